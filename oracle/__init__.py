@@ -1,0 +1,273 @@
+"""FP64 CPU oracle for the hierarchical pathwise CVA scheme (arXiv 2211.17005).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package's smoke check and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` use it; the product
+path never imports it. It shares no code with the CUDA library.
+
+* ``cva_oracle.c`` (built into ``_build/liboracle.so``) simulates the outer paths,
+  prices every swap with the three-case formula of App. B, draws the inner default
+  clocks of eq. (e:tau) and assembles the averaged target of eq. (eq:CVA_portfolio).
+* ``lsq`` solves the per-date least-squares problem of eq. (e:forw) by Householder
+  QR (numpy), on the standardised feature map.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Dict, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (binary64, no fast-math, OpenMP)."""
+    src = os.path.join(_HERE, "cva_oracle.c")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(src)):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-fno-fast-math", "-ffp-contract=off", src, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_int), ("C", ctypes.c_int)] + [
+        (n, ctypes.POINTER(ctypes.c_double)) for n in
+        ("a", "sigma_r", "f", "sigma_chi", "chi0", "kappa", "theta", "nu", "gamma0",
+         "recovery", "corr")]
+
+
+class _Portfolio(ctypes.Structure):
+    _fields_ = [("n_swaps", ctypes.c_int),
+                ("ccy", ctypes.POINTER(ctypes.c_int)), ("cpty", ctypes.POINTER(ctypes.c_int)),
+                ("omega", ctypes.POINTER(ctypes.c_int)),
+                ("n_periods", ctypes.POINTER(ctypes.c_int)),
+                ("notional", ctypes.POINTER(ctypes.c_double)), ("delta", ctypes.c_double)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("horizon", ctypes.c_double), ("n_steps", ctypes.c_int),
+                ("substeps", ctypes.c_int)]
+
+
+class _Out(ctypes.Structure):
+    _fields_ = [(n, ctypes.POINTER(ctypes.c_double)) for n in
+                ("features", "I0", "Lambda", "mtm", "swap_pv")] + [
+        ("idx", ctypes.POINTER(ctypes.c_uint16)),
+        ("xi_bar", ctypes.POINTER(ctypes.c_double)),
+        ("smooth", ctypes.POINTER(ctypes.c_double))]
+
+
+def _load(path: str):
+    L = ctypes.CDLL(path)
+    L.oracle_simulate.restype = ctypes.c_int
+    L.oracle_simulate.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Portfolio),
+                                  ctypes.POINTER(_Grid), ctypes.c_uint64, ctypes.c_uint64,
+                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                  ctypes.POINTER(_Out)]
+    L.oracle_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
+    L.oracle_uniform.restype = ctypes.c_double
+    L.oracle_uniform.argtypes = [ctypes.c_uint32]
+    L.oracle_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                 ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.oracle_exp_clock.restype = ctypes.c_double
+    L.oracle_exp_clock.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_int]
+    L.oracle_zc.restype = ctypes.c_double
+    L.oracle_zc.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_double]
+    L.oracle_par_rate.restype = ctypes.c_double
+    L.oracle_par_rate.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double]
+    L.oracle_n_factors.restype = ctypes.c_int
+    L.oracle_n_factors.argtypes = [ctypes.POINTER(_Model)]
+    return L
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _load(build())
+    return _lib
+
+
+class use_library:
+    """Context manager that points this module at another build of the oracle source
+    (used by the tests that plant a mistake in a copy of the source)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        lib()
+        self.saved = _lib
+        _lib = _load(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+class _Keep:
+    """Holds the numpy buffers a ctypes struct points into."""
+
+    def __init__(self):
+        self.refs = []
+
+    def d(self, x):
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        self.refs.append(a)
+        return _dp(a)
+
+    def i(self, x):
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+        self.refs.append(a)
+        return _ip(a)
+
+
+def _model_struct(model, keep: _Keep) -> _Model:
+    return _Model(model.E, model.C, keep.d(model.hw_a), keep.d(model.hw_sigma),
+                  keep.d(model.curve), keep.d(model.fx_vol), keep.d(model.fx0),
+                  keep.d(model.cir_kappa), keep.d(model.cir_theta), keep.d(model.cir_nu),
+                  keep.d(model.gamma0), keep.d(model.recovery), keep.d(model.corr))
+
+
+def _pf_struct(pf, keep: _Keep) -> _Portfolio:
+    return _Portfolio(pf.n_swaps, keep.i(pf.ccy), keep.i(pf.cpty), keep.i(pf.omega),
+                      keep.i(pf.n_periods), keep.d(pf.notional), float(pf.delta))
+
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block: ctr = 4 x uint32, key = 2 x uint32 -> 4 x uint32."""
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return [int(o[i]) for i in range(4)]
+
+
+def uniform(x: int) -> float:
+    return float(lib().oracle_uniform(int(x) & 0xFFFFFFFF))
+
+
+def normals(seed: int, k: int, q: int, F: int) -> np.ndarray:
+    z = np.zeros(F)
+    lib().oracle_normals(seed, k, q, F, _dp(z))
+    return z
+
+
+def exp_clock(seed: int, k: int, l: int, c: int) -> float:
+    return float(lib().oracle_exp_clock(seed, k, l, c))
+
+
+def zc(model, e: int, t: float, T: float, r: float) -> float:
+    keep = _Keep()
+    m = _model_struct(model, keep)
+    return float(lib().oracle_zc(ctypes.byref(m), e, t, T, r))
+
+
+def par_rate(model, e: int, n_periods: int, delta: float) -> float:
+    keep = _Keep()
+    m = _model_struct(model, keep)
+    return float(lib().oracle_par_rate(ctypes.byref(m), e, n_periods, delta))
+
+
+def n_factors(model) -> int:
+    keep = _Keep()
+    m = _model_struct(model, keep)
+    return int(lib().oracle_n_factors(ctypes.byref(m)))
+
+
+def simulate(model, pf, grid, k0: int, k1: int, N: int, seed: int,
+             want=("features", "I0", "Lambda", "mtm", "idx", "xi_bar"),
+             n_threads: int = 0) -> Dict[str, np.ndarray]:
+    """Run the oracle on outer paths [k0, k1); return the requested arrays.
+
+    Shapes: features [n+1, F, M], I0 [n+1, M], Lambda [n+1, C, M], mtm [n+1, C, M],
+    swap_pv [n+1, S, M], idx [M, N, C] (uint16; n+1 = no default), xi_bar [n, M],
+    smooth [n, M].
+    """
+    n, C, M = grid.n_steps, model.C, k1 - k0
+    F = n_factors(model)
+    shapes = {"features": (n + 1, F, M), "I0": (n + 1, M), "Lambda": (n + 1, C, M),
+              "mtm": (n + 1, C, M), "swap_pv": (n + 1, pf.n_swaps, M),
+              "idx": (M, N, C), "xi_bar": (n, M), "smooth": (n, M)}
+    res: Dict[str, np.ndarray] = {}
+    ptrs = {}
+    for key in ("features", "I0", "Lambda", "mtm", "swap_pv", "xi_bar", "smooth"):
+        if key in want:
+            res[key] = np.zeros(shapes[key])
+            ptrs[key] = _dp(res[key])
+        else:
+            ptrs[key] = ctypes.POINTER(ctypes.c_double)()
+    if "idx" in want:
+        res["idx"] = np.zeros(shapes["idx"], dtype=np.uint16)
+        idx_p = res["idx"].ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))
+    else:
+        idx_p = ctypes.POINTER(ctypes.c_uint16)()
+    out = _Out(ptrs["features"], ptrs["I0"], ptrs["Lambda"], ptrs["mtm"], ptrs["swap_pv"],
+               idx_p, ptrs["xi_bar"], ptrs["smooth"])
+    keep = _Keep()
+    m = _model_struct(model, keep)
+    p = _pf_struct(pf, keep)
+    g = _Grid(float(grid.horizon), int(grid.n_steps), int(grid.substeps))
+    rc = lib().oracle_simulate(ctypes.byref(m), ctypes.byref(p), ctypes.byref(g),
+                               k0, k1, N, seed, n_threads, ctypes.byref(out))
+    if rc != 0:
+        raise ValueError(f"oracle_simulate failed with code {rc}")
+    return res
+
+
+def cva0(xi_bar: np.ndarray):
+    """CVA_0 = mean over outer paths of the averaged target at t_0, and its standard error."""
+    x0 = np.asarray(xi_bar[0], dtype=np.float64)
+    return float(x0.mean()), float(x0.std(ddof=1) / np.sqrt(x0.size)) if x0.size > 1 else 0.0
+
+
+def poly2_features(y: np.ndarray) -> np.ndarray:
+    """[1, z, z^2] with z the standardised short rate (mean 0, variance 1 over paths)."""
+    sd = y.std()
+    z = (y - y.mean()) / (sd if sd > 0 else 1.0)
+    return np.stack([np.ones_like(z), z, z * z], axis=1)
+
+
+def linear_features(Y: np.ndarray) -> np.ndarray:
+    """[1, z_1, ..., z_F] with each factor standardised over paths. Y is [F, M]."""
+    mu = Y.mean(axis=1, keepdims=True)
+    sd = Y.std(axis=1, keepdims=True)
+    sd[sd == 0] = 1.0
+    Z = (Y - mu) / sd
+    return np.concatenate([np.ones((1, Y.shape[1])), Z], axis=0).T
+
+
+def lsq(phi: np.ndarray, xi: np.ndarray):
+    """Least squares of eq. (e:forw) by Householder QR: w = argmin ||xi - phi w||.
+
+    Returns (w, predictions phi w). phi is [M, m], xi is [M].
+    """
+    Q, R = np.linalg.qr(np.asarray(phi, dtype=np.float64), mode="reduced")
+    w = np.linalg.solve(R, Q.T @ np.asarray(xi, dtype=np.float64))
+    return w, phi @ w
