@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the hierarchical pathwise-CVA hot path on one GB300 (or N, one
+process per GPU under torchrun, each rank simulating its own range of outer paths).
+
+A step is one pass of the whole path over one batch: the outer-path kernel
+(factors, MtM, exposures), the inner-default kernel (N default draws per path,
+averaged targets), CVA_0, and the per-date regression of the targets on the state
+at every date 1..n-1. `value` is outer-path x inner-default x steps per second of
+whole steps (inputs resident on the device); `e2e` is the same metric through the
+public API with the model and portfolio handed over from host memory each step
+and the regression output copied back to host memory.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (the reference arm; there is no reference GPU code).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "outer-path·inner-default·steps/s and regression samples/s; adjoint/forward ratio"
+UNIT = "outer-path*inner-default*steps/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="paper")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def alu_peak_lane_instr_per_s(sm_mhz):
+    """Issue peak of the SM sub-partitions: 152 SMs x 4 schedulers x 32 lanes per clock."""
+    return 152 * 4 * 32 * sm_mhz * 1e6
+
+
+def outer_instr_per_path_step(wl):
+    """Algorithmic lane-instructions of the outer-path kernel per (path, pricing step),
+    counted from the method (not from the compiled code):
+      per Euler sub-step: Philox4x32-10 = 10 rounds x 8 integer ops + 4 counter ops per
+      block of four draws, 4 ops per uniform, 20 per Box-Muller pair, F(F+1)/2 FMA for
+      the correlation, 4 per rate and FX factor, 8 per CIR intensity, 4 per
+      integrated intensity (compensated sum), 1 for the FP64 discount integral;
+      per pricing date: 7 per (economy, reset date) for the bond prices, (2G+1) per
+      (portfolio, counterparty, economy) for the date-bucketed MtM, 12 per counterparty
+      (threshold) and 3 per (portfolio, counterparty) for the exposure."""
+    m = wl.model
+    E, C = m.E, m.C
+    CS = int(np.count_nonzero(m.cir_nu > 0))
+    F = 2 * E - 1 + CS
+    G = 10 if wl.name != "small" else 5
+    NPF = len(wl.portfolios)
+    S = wl.grid.substeps
+    blocks = (F + 3) // 4
+    sub = blocks * (84 + 16 + 40) + F * (F + 1) // 2 + 4 * E + 4 * (E - 1) + 8 * CS + 4 * C + 1
+    date = 7 * E * G + NPF * C * E * (2 * G + 1) + 12 * C + 3 * NPF * C
+    return S * sub + date
+
+
+def inner_bytes_per_path(wl):
+    """HBM bytes the inner-default kernel must move per outer path: thresholds and
+    exposures of dates 1..n (read), the discount integrals of dates 0..n-1 (read) and
+    the targets of dates 0..n-1 (written)."""
+    n, C, P = wl.grid.n_steps, wl.model.C, len(wl.portfolios)
+    return 4 * (n * C + P * n * C + n + P * n)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(wl, M_sample):
+    """Time the FP64 oracle (simulation + targets + per-date least squares) on the first
+    M_sample outer paths of the workload; returns (seconds, threads)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    o = oracle.simulate(wl.model, wl.portfolios[0], wl.grid, 0, M_sample, wl.N, wl.seed,
+                        want=("features", "xi_bar"))
+    for i in range(1, wl.grid.n_steps):
+        phi = oracle.linear_features(o["features"][i]) if wl.name != "small" else \
+            oracle.poly2_features(o["features"][i, 0])
+        oracle.lsq(phi, o["xi_bar"][i])
+    dt = time.perf_counter() - t0
+    return dt, os.cpu_count()
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2211_17005_gb300 import workload
+    wl = workload.make(args.workload)
+    M_sample = 1024 if wl.name != "small" else 4096
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, M_sample)
+    times = []
+    for _ in range(args.steps):
+        dt, cores = cpu_oracle_sample(wl, M_sample)
+        times.append(dt)
+    t = float(np.sum(times))
+    value = args.steps * M_sample * wl.N * wl.grid.n_steps / t
+    cb = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"first {M_sample} of {wl.M} outer paths per step, all {wl.N} inner draws, "
+                    f"{wl.grid.n_steps} dates, per-date least squares"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": describe(wl), "M_sample": M_sample},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}))
+
+
+def describe(wl):
+    m = wl.model
+    return (f"{wl.name}: E={m.E} economies, C={m.C} counterparties, F={m.F} factors, "
+            f"{sum(p.n_swaps for p in wl.portfolios)} swaps in {len(wl.portfolios)} portfolio(s), "
+            f"n={wl.grid.n_steps} steps over {wl.grid.horizon:g}y, S={wl.grid.substeps}, "
+            f"M={wl.M}, N={wl.N}")
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_2211_17005_gb300 import api, build, workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    build.build()
+    wl = workload.make(args.workload)
+    basis = "poly2" if wl.name == "small" else "linear"
+    k0 = rank * wl.M          # weak scaling: each rank owns its own outer paths
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N, profile=True)
+    stream = torch.cuda.current_stream()
+    n = wl.grid.n_steps
+
+    def step(seed):
+        sim.run(seed, k0=k0)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pred, _ = sim.regress_all(0, basis=basis, want_coef=False)
+        ev1.record(stream)
+        c0 = sim.cva0(0)
+        return c0, (ev0, ev1), pred
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    outer_ms, inner_ms, reg_ev = [], [], []
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for s in range(args.steps):
+            c0, evs, _ = step(s + 1)
+            o_ms, i_ms = sim.kernel_ms()
+            outer_ms.append(o_ms)
+            inner_ms.append(i_ms)
+            reg_ev.append(evs)
+        end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = start.elapsed_time(end)
+    reg_ms = [a.elapsed_time(b) for a, b in reg_ev]
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    units_per_step = wl.M * wl.N * n * world
+    value = units_per_step * args.steps / (t_max / 1e3)
+
+    # ---- end to end through the public API: host inputs in, host results out ----
+    pinned = torch.empty((n, wl.M), dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 5))
+    h2d = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        sim2 = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N)
+        sim2.run(s + 1, k0=k0)
+        pred, _ = sim2.regress_all(0, basis=basis, want_coef=False)
+        c0e = sim2.cva0(0)
+        pinned.copy_(pred, non_blocking=True)
+        torch.cuda.synchronize()
+        sim2.close()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    E, C, G = wl.model.E, wl.model.C, (10 if wl.name != "small" else 5)
+    h2d = 8 * (n + 1) * E * G + 8 * (n // 1 + 2) * E + 4 * (n + 1) + 4 * n * wl.grid.substeps * E
+    d2h = 4 * n * wl.M + 16
+    e2e_value = units_per_step / e2e_s
+
+    # ---- roofline of the dominant kernel (the outer-path kernel) ----
+    pk, src = peaks()
+    o_avg = float(np.mean(outer_ms))
+    i_avg = float(np.mean(inner_ms))
+    clk = clocks.summary()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    peak_alu = alu_peak_lane_instr_per_s(sm_mhz)
+    instr = outer_instr_per_path_step(wl) * wl.M * n
+    achieved = instr / (o_avg / 1e3)
+    roof = {"bound": "alu", "kernel": "outer_kernel", "achieved": achieved / 1e12, "peak": peak_alu / 1e12,
+            "unit": "T lane-instr/s", "frac": achieved / peak_alu, "traffic": None,
+            "peak_source": f"152 SMs x 128 lanes x {sm_mhz:g} MHz ({src} max SM clock)",
+            "algorithmic_instr_per_path_step": outer_instr_per_path_step(wl)}
+    hbm = pk.get("hbm_gbs", 6800.0)
+    inner_gbs = inner_bytes_per_path(wl) * wl.M / (i_avg / 1e3) / 1e9
+    reg_bytes = 4 * (n - 1) * wl.M * (wl.model.F + 1 + 1)
+    reg_gbs = reg_bytes / (np.mean(reg_ms) / 1e3) / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        M_sample = 2048 if wl.name != "small" else wl.M
+        dt, cores = cpu_oracle_sample(wl, M_sample)
+        cpu = {"value": M_sample * wl.N * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {M_sample} of {wl.M} outer paths, all {wl.N} inner draws, {n} dates, "
+                         f"per-date least squares ({dt:.1f} s)"}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": describe(wl), "regression": f"least squares, basis {basis}",
+                          "seed_per_step": "1..K", "l2": "working set > L2: 2.3 GB written per step",
+                          "parallelism": f"{world} rank(s), disjoint outer-path ranges"},
+               "sim_ms": o_avg + i_avg, "outer_kernel_ms": o_avg, "inner_kernel_ms": i_avg,
+               "regression_ms": float(np.mean(reg_ms)),
+               "sim_throughput": wl.M * wl.N * n / ((o_avg + i_avg) / 1e3),
+               "regression_samples_per_s": wl.M * (n - 1) / (np.mean(reg_ms) / 1e3),
+               "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
+               "cva0": c0[0], "cva0_se": c0[1],
+               "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h)},
+               "gpu_launches": 7 * args.steps}
+        print(json.dumps(out))
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

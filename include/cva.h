@@ -1,0 +1,197 @@
+/*
+ * cva.h -- C ABI of the GB300 (sm_103a) hierarchical pathwise-CVA library.
+ *
+ * The library implements the data-parallel hot path of Abbas-Turki, Crepey and
+ * Saadeddine, "Pathwise CVA Regressions With Oversimulated Defaults"
+ * (arXiv 2211.17005):
+ *
+ *   simulate  M outer paths Y^k of the market/credit factors (App. B: Hull-White
+ *             short rates eq. (e:sde1), lognormal FX, CIR intensities eq. (e:sde2)),
+ *             price the swap portfolio at every pricing date (App. B swap formula),
+ *             draw N inner default scenarios X^{k,l} per outer path (Sec. 3.2,
+ *             default clocks of eq. (e:tau)) and form the averaged pathwise CVA
+ *             target of eq. (eq:CVA_portfolio);
+ *   regress   the target on the state at each date by least squares (eq. (e:forw));
+ *   cva0      CVA_0 as the mean of the date-0 targets.
+ *
+ * Conventions (every entry point):
+ *  - all functions return a cva_status; nothing throws across the ABI; on error
+ *    cva_last_error() returns a message for the calling thread;
+ *  - "dev" pointers are CUDA device pointers on the current device, "host"
+ *    pointers are host memory; all work is enqueued on the caller's stream
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream) and is
+ *    asynchronous unless the comment says the call synchronises;
+ *  - arrays are row-major, the outer-path index k is always the fastest
+ *    (innermost) index of device arrays so that warps access consecutive paths;
+ *  - objects created by the library are owned by the library and released by
+ *    the matching _destroy call; pointers returned by cva_sim_view are borrowed
+ *    and valid until cva_sim_destroy.
+ */
+#ifndef CVA_H
+#define CVA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CVA_API __attribute__((visibility("default")))
+#else
+#define CVA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CVA_OK = 0,
+    CVA_EINVAL = 1,     /* bad argument (shape, range, non-SPD correlation, ...) */
+    CVA_ENOMEM = 2,     /* device or host allocation failed                      */
+    CVA_ECUDA = 3,      /* a CUDA runtime call failed                            */
+    CVA_ETIMEOUT = 4,   /* a bounded device-side wait gave up                    */
+    CVA_ENOTSUP = 5,    /* shape not supported by the compiled kernels           */
+    CVA_ENUMERIC = 6    /* numerical failure (e.g. singular normal equations)    */
+} cva_status;
+
+/* Market and credit model (Sec. 4.1 and App. B). E economies, economy 0 is the
+ * reference currency; C counterparties. The stochastic factors, in this order,
+ * are r^0..r^{E-1}, log chi^1..log chi^{E-1}, then gamma^c of every
+ * counterparty with cir_nu[c] > 0; F is their count and corr is their F x F
+ * correlation matrix (row-major, symmetric positive definite).
+ * Short rates are Hull-White fitted to a flat curve curve[e] (Vasicek is the
+ * constant-theta special case of eq. (e:sde1)); r^e for e >= 1 carries the
+ * quanto drift -rho_e fx_vol[e] hw_sigma[e] under the reference measure, rho_e
+ * being the correlation of r^e and log chi^e. cir_nu[c] = 0 makes gamma^c the
+ * constant gamma0[c]. All arrays are host memory, copied at creation. */
+typedef struct {
+    int E, C;
+    const double *hw_a, *hw_sigma, *curve;       /* [E] */
+    const double *fx_vol, *fx0;                  /* [E], entry 0 ignored */
+    const double *cir_kappa, *cir_theta, *cir_nu, *gamma0, *recovery; /* [C] */
+    const double *corr;                          /* [F*F] */
+} cva_model_desc;
+
+/* Spot-starting interest-rate swaps with regular resets every delta years
+ * (App. B): the bank pays delta*Sigma and receives the floating coupon at each
+ * reset date; omega = +1 (payer) or -1 (receiver) from the bank's point of
+ * view; the fixed rate Sigma is the par rate at t = 0 (computed by the
+ * library). delta must be a whole number of pricing steps. Host memory. */
+typedef struct {
+    int n_swaps;
+    const int32_t *ccy, *cpty, *omega, *n_periods;   /* [n_swaps] */
+    const double *notional;                          /* [n_swaps] */
+    double delta;
+} cva_portfolio_desc;
+
+/* Pricing grid t_j = j*horizon/n_steps, j = 0..n_steps, with `substeps`
+ * Euler-Maruyama sub-steps per pricing step (Remark rem:finecoarse). */
+typedef struct {
+    double horizon;
+    int n_steps, substeps;
+} cva_grid;
+
+typedef struct cva_sim cva_sim;   /* opaque: tables and device buffers of one run */
+
+/* flags of cva_sim_create */
+#define CVA_KEEP_DEFAULTS  1u   /* also keep default step indices (validation)     */
+#define CVA_KEEP_EXPOSURES 2u   /* also keep the MtM per counterparty and date     */
+#define CVA_PROFILE        4u   /* record CUDA events around each kernel launch    */
+
+/* Prepare a simulation of M outer paths x N inner default draws for n_pf
+ * portfolios sharing one model and grid. Validates every input (returns
+ * CVA_EINVAL on a bad one, CVA_ENOTSUP for model shapes the kernels are not
+ * compiled for), builds the host tables (correlation Cholesky factor, Hull-White
+ * drift and bond tables, date-bucketed portfolio weights, par rates) and
+ * allocates the device buffers on the current device (CVA_ENOMEM if that
+ * fails). Limits: 1 <= E <= 16, 1 <= C <= 16, n_steps <= 254, N <= 2^24,
+ * M <= 2^31. Synchronous. */
+CVA_API cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc *pfs,
+                          int n_pf, const cva_grid *grid, uint64_t M, uint32_t N,
+                          uint32_t flags, cva_sim **out);
+
+/* Run the hierarchical simulation for global outer paths [k0, k0 + M) with the
+ * Philox4x32-10 key `seed` (counters keyed by global path, step and inner
+ * index, so a path range gives the same paths as a full run). Enqueues the
+ * outer-path kernel (factors, MtM, exposures, features) and the inner-default
+ * kernel (default steps, averaged targets) on `stream`. */
+CVA_API cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *stream);
+
+/* What cva_sim_view can return; shapes use n = n_steps, F factors, C
+ * counterparties, P = n_pf portfolios:
+ *   CVA_VIEW_FEATURES  float [n+1][F][M]   state Y_j (r^e, log chi^e, gamma^c)
+ *   CVA_VIEW_TARGETS   float [P][n][M]     averaged target xi_bar_i, i = 0..n-1
+ *   CVA_VIEW_DISCOUNT  float [n+1][M]      int_0^{t_j} r^0 (beta_j = exp(-value))
+ *   CVA_VIEW_THRESHOLD float [n+1][C][M]   1 - exp(-Lambda_c(t_j))
+ *   CVA_VIEW_EXPOSURE  float [P][n+1][C][M] (1-R_c) beta_j MtM_c(t_j)^+
+ *   CVA_VIEW_MTM       float [P][n+1][C][M] MtM_c(t_j), reference ccy  (KEEP_EXPOSURES)
+ *   CVA_VIEW_DEFAULTS  uint8 [M][N][C]     default step in 1..n, n+1 = none (KEEP_DEFAULTS)
+ * The pointer is borrowed (owned by sim). Returns CVA_EINVAL if the view was
+ * not requested at creation. */
+#define CVA_VIEW_FEATURES  0
+#define CVA_VIEW_TARGETS   1
+#define CVA_VIEW_DISCOUNT  2
+#define CVA_VIEW_THRESHOLD 3
+#define CVA_VIEW_EXPOSURE  4
+#define CVA_VIEW_MTM       5
+#define CVA_VIEW_DEFAULTS  6
+CVA_API cva_status cva_sim_view(const cva_sim *sim, int what, void **dev_ptr, size_t *bytes);
+
+/* Device durations (milliseconds, CUDA events on the launching stream) of the
+ * last cva_simulate of a sim created with CVA_PROFILE: out_ms[0] = outer-path
+ * kernel, out_ms[1] = inner-default kernel. Waits for those events. */
+CVA_API cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[2]);
+
+/* Shape of a simulation: out[0..5] = M, N, n_steps, F, C, n_pf. */
+CVA_API cva_status cva_sim_shape(const cva_sim *sim, int64_t out[6]);
+
+CVA_API void cva_sim_destroy(cva_sim *sim);
+
+/* CVA_0 of eq. (eq:CVA_portfolio) at i = 0: the mean over the M outer paths of
+ * the date-0 averaged targets xi0_dev[M] (float, device), accumulated in FP64 in
+ * a fixed order (bit-reproducible). Writes host out2[0] = CVA_0 and
+ * out2[1] = its Monte Carlo standard error. Synchronises `stream`. */
+CVA_API cva_status cva_cva0(const float *xi0_dev, uint64_t M, double *out2_host, void *stream);
+
+/* Least-squares regression of eq. (e:forw) at one date:
+ *   w = argmin_w sum_k (targets[k] - w^T phi(Y[:, k]))^2
+ * features_dev: float [F][M] (state at the date, path index fastest);
+ * targets_dev:  float [M];
+ * basis: CVA_BASIS_LINEAR  phi = [1, Y_1, ..., Y_F]        (m = F + 1)
+ *        CVA_BASIS_POLY2   phi = [1, y, y^2] of factor 0     (m = 3)
+ * The normal equations are accumulated in FP64 on the centred, scaled basis and
+ * solved by Cholesky in FP64. pred_dev (float [M], nullable) receives
+ * phi(Y_k)^T w; coef_host (double [m], nullable) receives w in the raw basis
+ * (w_0 + w_1 y + ... ). Synchronises `stream` when coef_host is not NULL.
+ * CVA_ENUMERIC if the normal matrix is singular. */
+#define CVA_BASIS_LINEAR 0
+#define CVA_BASIS_POLY2  1
+CVA_API cva_status cva_regress(const float *targets_dev, const float *features_dev, int F,
+                       uint64_t M, int basis, float *pred_dev, double *coef_host,
+                       void *stream);
+
+/* The same regression for every date i = 1..n-1 of a simulation and portfolio
+ * pf, all dates in one grouped launch: features of date i, targets of date i.
+ * pred_dev: float [n][M] (row 0 left untouched), nullable; coef_host: double
+ * [n][m] (row 0 left untouched), nullable. Synchronises when coef_host != NULL. */
+CVA_API cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float *pred_dev,
+                           double *coef_host, void *stream);
+
+/* The counter-based generator the kernels draw from: Philox4x32-10 (Salmon,
+ * Moraes, Dror, Shaw, SC'11) with key (seed low 32 bits, seed high 32 bits).
+ * For i < n: out_dev[4i..4i+3] = Philox4x32-10(ctr_dev[4i..4i+3], key). Both
+ * arrays are device memory (uint32). The simulation uses the counters
+ * (path k, fine step q, 0, 1 << 24 | block) for its normals and
+ * (path k, inner draw l, 0, 2 << 24 | block) for its default clocks. */
+CVA_API cva_status cva_philox4x32_10(const uint32_t *ctr_dev, uint32_t *out_dev, uint64_t n,
+                                     uint64_t seed, void *stream);
+
+/* Thread-local message describing the last error of this thread. */
+CVA_API const char *cva_last_error(void);
+
+/* Library build information: "sm_103a <version>". */
+CVA_API const char *cva_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CVA_H */

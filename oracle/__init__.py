@@ -84,6 +84,8 @@ def _load(path: str):
     L.oracle_exp_clock.restype = ctypes.c_double
     L.oracle_exp_clock.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_int]
+    L.oracle_exp_clocks.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                    ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.oracle_zc.restype = ctypes.c_double
     L.oracle_zc.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, ctypes.c_double,
                             ctypes.c_double, ctypes.c_double]
@@ -181,6 +183,13 @@ def normals(seed: int, k: int, q: int, F: int) -> np.ndarray:
 
 def exp_clock(seed: int, k: int, l: int, c: int) -> float:
     return float(lib().oracle_exp_clock(seed, k, l, c))
+
+
+def exp_clocks(seed: int, k0: int, k1: int, N: int, C: int) -> np.ndarray:
+    """Standard exponential clocks epsilon of every inner draw: [k1-k0, N, C]."""
+    out = np.zeros((k1 - k0, N, C))
+    lib().oracle_exp_clocks(seed, k0, k1, N, C, _dp(out))
+    return out
 
 
 def zc(model, e: int, t: float, T: float, r: float) -> float:

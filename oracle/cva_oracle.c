@@ -112,6 +112,15 @@ double oracle_exp_clock(uint64_t seed, uint32_t k, uint32_t l, int c)
     return -log1p(-w);
 }
 
+/* All default clocks of paths [k0, k1): out[(k-k0)][l][c], for tie accounting. */
+void oracle_exp_clocks(uint64_t seed, uint64_t k0, uint64_t k1, uint32_t N, int C, double *out)
+{
+    for (uint64_t k = k0; k < k1; ++k)
+        for (uint32_t l = 0; l < N; ++l)
+            for (int c = 0; c < C; ++c)
+                out[((k - k0) * N + l) * (uint64_t)C + c] = oracle_exp_clock(seed, (uint32_t)k, l, c);
+}
+
 /* ---------------- model, portfolio, grid --------------------------------- */
 
 typedef struct {

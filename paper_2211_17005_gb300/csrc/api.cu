@@ -1,0 +1,429 @@
+// C ABI of the library (include/cva.h): input validation, host-side tables
+// and device buffers of a simulation, and the entry points.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "cva_internal.h"
+
+namespace cva {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+cva_status fail(cva_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+cva_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? CVA_ENOMEM : CVA_ECUDA;
+}
+
+namespace {
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+// Hull-White bond ZC_t(T) = exp(lnA(t,T) - B(t,T) r_t) for a flat initial curve f:
+// B = (1 - e^{-a(T-t)})/a, lnA = -f (T-t) + B f - sigma^2/(4a) (1 - e^{-2at}) B^2.
+struct HW {
+    double a, s, f;
+    double B(double t, double T) const { return (1.0 - std::exp(-a * (T - t))) / a; }
+    double lnA(double t, double T) const
+    {
+        const double b = B(t, T);
+        return -f * (T - t) + b * f - s * s / (4.0 * a) * (1.0 - std::exp(-2.0 * a * t)) * b * b;
+    }
+    // theta(t) of the fit to the flat curve: a f + sigma^2/(2a) (1 - e^{-2at})
+    double theta(double t) const { return a * f + s * s / (2.0 * a) * (1.0 - std::exp(-2.0 * a * t)); }
+};
+
+// Lower Cholesky factor of an SPD matrix (FP64); false if not positive definite.
+bool cholesky(int F, const double *A, std::vector<double> &L)
+{
+    L.assign((size_t)F * F, 0.0);
+    for (int i = 0; i < F; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i * F + j];
+            for (int p = 0; p < j; ++p) s -= L[i * F + p] * L[j * F + p];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i * F + i] = std::sqrt(s);
+            } else {
+                L[i * F + j] = s / L[j * F + j];
+            }
+        }
+    return true;
+}
+
+template <class T>
+cva_status dev_alloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) return CVA_OK;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(CVA_ENOMEM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    return CVA_OK;
+}
+
+void free_sim(Sim *s)
+{
+    if (!s) return;
+    forget_const_owner(s);
+    cudaFree(s->d_zc);
+    cudaFree(s->d_fix);
+    cudaFree(s->d_date_p);
+    cudaFree(s->d_drift);
+    cudaFree(s->d_features);
+    cudaFree(s->d_disc);
+    cudaFree(s->d_thr);
+    cudaFree(s->d_expo);
+    cudaFree(s->d_mtm);
+    cudaFree(s->d_targets);
+    cudaFree(s->d_idx);
+    for (cudaEvent_t &e : s->ev)
+        if (e) cudaEventDestroy(e);
+    delete s;
+}
+
+cva_status validate_model(const cva_model_desc *m, int *F_out, int *CS_out, std::vector<double> &L)
+{
+    if (!m) return fail(CVA_EINVAL, "model is NULL");
+    if (m->E < 1 || m->E > kMaxE) return fail(CVA_EINVAL, "model: E must be in [1, 16]");
+    if (m->C < 1 || m->C > kMaxC) return fail(CVA_EINVAL, "model: C must be in [1, 16]");
+    if (!m->hw_a || !m->hw_sigma || !m->curve || !m->fx_vol || !m->fx0 || !m->cir_kappa ||
+        !m->cir_theta || !m->cir_nu || !m->gamma0 || !m->recovery || !m->corr)
+        return fail(CVA_EINVAL, "model: NULL parameter array");
+    for (int e = 0; e < m->E; ++e) {
+        if (!(m->hw_a[e] > 0.0) || !is_fin(m->hw_a[e])) return fail(CVA_EINVAL, "model: hw_a must be > 0");
+        if (!(m->hw_sigma[e] >= 0.0) || !is_fin(m->hw_sigma[e])) return fail(CVA_EINVAL, "model: hw_sigma must be >= 0");
+        if (!is_fin(m->curve[e])) return fail(CVA_EINVAL, "model: curve must be finite");
+        if (e > 0 && (!(m->fx_vol[e] >= 0.0) || !is_fin(m->fx_vol[e])))
+            return fail(CVA_EINVAL, "model: fx_vol must be >= 0");
+        if (e > 0 && (!(m->fx0[e] > 0.0) || !is_fin(m->fx0[e]))) return fail(CVA_EINVAL, "model: fx0 must be > 0");
+    }
+    int CS = 0;
+    for (int c = 0; c < m->C; ++c) {
+        if (!(m->cir_kappa[c] >= 0.0) || !(m->cir_theta[c] >= 0.0) || !(m->cir_nu[c] >= 0.0) ||
+            !(m->gamma0[c] >= 0.0) || !is_fin(m->cir_kappa[c]) || !is_fin(m->cir_theta[c]) ||
+            !is_fin(m->cir_nu[c]) || !is_fin(m->gamma0[c]))
+            return fail(CVA_EINVAL, "model: CIR parameters must be finite and >= 0");
+        if (!(m->recovery[c] >= 0.0 && m->recovery[c] <= 1.0)) return fail(CVA_EINVAL, "model: recovery must be in [0, 1]");
+        if (m->cir_nu[c] > 0.0) ++CS;
+    }
+    const int F = m->E + (m->E - 1) + CS;
+    for (int i = 0; i < F; ++i) {
+        if (std::fabs(m->corr[i * F + i] - 1.0) > 1e-12) return fail(CVA_EINVAL, "model: corr diagonal must be 1");
+        for (int j = 0; j < F; ++j) {
+            const double v = m->corr[i * F + j];
+            if (!is_fin(v) || std::fabs(v - m->corr[j * F + i]) > 1e-12 || std::fabs(v) > 1.0)
+                return fail(CVA_EINVAL, "model: corr must be a symmetric correlation matrix");
+        }
+    }
+    if (!cholesky(F, m->corr, L)) return fail(CVA_EINVAL, "model: corr is not positive definite");
+    *F_out = F;
+    *CS_out = CS;
+    return CVA_OK;
+}
+
+}  // namespace
+}  // namespace cva
+
+using namespace cva;
+
+extern "C" {
+
+const char *cva_last_error(void) { return g_err.c_str(); }
+
+const char *cva_version(void) { return "sm_103a 0.1.0"; }
+
+cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc *pfs, int n_pf,
+                          const cva_grid *grid, uint64_t M, uint32_t N, uint32_t flags, cva_sim **out)
+{
+    if (!out) return fail(CVA_EINVAL, "out is NULL");
+    *out = nullptr;
+    int F = 0, CS = 0;
+    std::vector<double> L;
+    cva_status st = validate_model(model, &F, &CS, L);
+    if (st != CVA_OK) return st;
+    if (!pfs || n_pf < 1 || n_pf > kMaxPF) return fail(CVA_EINVAL, "n_pf must be in [1, 6]");
+    if (!grid || !(grid->horizon > 0.0) || !is_fin(grid->horizon) || grid->n_steps < 1 || grid->n_steps > 254 ||
+        grid->substeps < 1 || (int64_t)grid->n_steps * grid->substeps > (1 << 24))
+        return fail(CVA_EINVAL, "grid: need horizon > 0, 1 <= n_steps <= 254, substeps >= 1");
+    if (M < 1 || M > 0x7fffffffull) return fail(CVA_EINVAL, "M must be in [1, 2^31)");
+    if (N < 1 || N > (1u << 24)) return fail(CVA_EINVAL, "N must be in [1, 2^24]");
+    const int E = model->E, C = model->C, n = grid->n_steps, S = grid->substeps;
+    const double Delta = grid->horizon / n;
+    const double delta = pfs[0].delta;
+    if (!(delta > 0.0)) return fail(CVA_EINVAL, "portfolio: delta must be > 0");
+    const double pr = delta / Delta;
+    const long ppp = std::lround(pr);
+    if (ppp < 1 || std::fabs(pr - (double)ppp) > 1e-9 * pr)
+        return fail(CVA_EINVAL, "portfolio: delta must be a whole number of pricing steps");
+    int G = 1;
+    for (int p = 0; p < n_pf; ++p) {
+        const cva_portfolio_desc &d = pfs[p];
+        if (d.n_swaps < 0) return fail(CVA_EINVAL, "portfolio: n_swaps < 0");
+        if (d.n_swaps > 0 && (!d.ccy || !d.cpty || !d.omega || !d.n_periods || !d.notional))
+            return fail(CVA_EINVAL, "portfolio: NULL swap array");
+        if (std::fabs(d.delta - delta) > 1e-12) return fail(CVA_EINVAL, "portfolios must share delta");
+        for (int s = 0; s < d.n_swaps; ++s) {
+            if (d.ccy[s] < 0 || d.ccy[s] >= E) return fail(CVA_EINVAL, "swap: currency out of range");
+            if (d.cpty[s] < 0 || d.cpty[s] >= C) return fail(CVA_EINVAL, "swap: counterparty out of range");
+            if (d.omega[s] != 1 && d.omega[s] != -1) return fail(CVA_EINVAL, "swap: omega must be +1 or -1");
+            if (d.n_periods[s] < 1 || d.n_periods[s] > kMaxG)
+                return fail(CVA_EINVAL, "swap: n_periods must be in [1, 10]");
+            if (!is_fin(d.notional[s])) return fail(CVA_EINVAL, "swap: notional must be finite");
+            G = std::max(G, (int)d.n_periods[s]);
+        }
+    }
+    int Ginst = 0;
+    if (!outer_supported(E, C, CS, G, n_pf, &Ginst))
+        return fail(CVA_ENOTSUP, "no compiled outer kernel for E=" + std::to_string(E) + " C=" +
+                                     std::to_string(C) + " stochastic C=" + std::to_string(CS) +
+                                     " portfolios=" + std::to_string(n_pf));
+    if ((size_t)n_pf * C * E * Ginst > (size_t)kMaxW) return fail(CVA_ENOTSUP, "portfolio weights exceed constant memory");
+
+    Sim *s = new Sim();
+    s->E = E; s->C = C; s->CS = CS; s->F = F; s->G = G; s->Ginst = Ginst; s->NPF = n_pf;
+    s->n = n; s->S = S; s->ppp = (int)ppp; s->M = M; s->N = N; s->flags = flags;
+    s->horizon = grid->horizon; s->delta = delta;
+
+    // ---- constants ----
+    SimConsts &k = s->consts;
+    memset(&k, 0, sizeof(k));
+    k.E = E; k.C = C; k.CS = CS; k.F = F; k.G = Ginst; k.NPF = n_pf; k.n = n; k.S = S; k.ppp = (int)ppp;
+    const double ds = Delta / S;
+    k.ds_d = ds;
+    k.ds = (float)ds;
+    k.sqds = (float)std::sqrt(ds);
+    for (int i = 0; i < F; ++i)
+        for (int j = 0; j <= i; ++j) k.L[i * (i + 1) / 2 + j] = (float)L[i * F + j];
+    std::vector<HW> hw(E);
+    for (int e = 0; e < E; ++e) {
+        hw[e] = HW{model->hw_a[e], model->hw_sigma[e], model->curve[e]};
+        k.hw_a_ds[e] = (float)(model->hw_a[e] * ds);
+        k.hw_sig_sqds[e] = (float)(model->hw_sigma[e] * std::sqrt(ds));
+        k.fx_drift_ds[e] = e ? (float)(-0.5 * model->fx_vol[e] * model->fx_vol[e] * ds) : 0.f;
+        k.fx_sig_sqds[e] = e ? (float)(model->fx_vol[e] * std::sqrt(ds)) : 0.f;
+        k.r0[e] = (float)model->curve[e];
+        k.lchi0[e] = e ? (float)std::log(model->fx0[e]) : 0.f;
+        k.fix0_m1[e] = (float)std::expm1(model->curve[e] * delta);   // 1/ZC_0(delta) - 1
+    }
+    for (int c = 0; c < C; ++c) {
+        const bool stoch = model->cir_nu[c] > 0.0;
+        k.cir_kds[c] = stoch ? (float)(model->cir_kappa[c] * ds) : 0.f;
+        k.cir_ktds[c] = stoch ? (float)(model->cir_kappa[c] * model->cir_theta[c] * ds) : 0.f;
+        k.cir_nu_sqds[c] = stoch ? (float)(model->cir_nu[c] * std::sqrt(ds)) : 0.f;
+        k.gamma0[c] = (float)model->gamma0[c];
+        k.lgd[c] = (float)(1.0 - model->recovery[c]);
+    }
+    // quanto drift of r^e under the reference measure: -rho_e sigma^chi_e sigma^r_e
+    std::vector<double> quanto(E, 0.0);
+    for (int e = 1; e < E; ++e) {
+        const int pr_ = e, px = E - 1 + e;
+        quanto[e] = model->corr[pr_ * F + px] * model->fx_vol[e] * model->hw_sigma[e];
+    }
+
+    // ---- tables ----
+    std::vector<float> drift((size_t)n * S * E);
+    for (int q = 0; q < n * S; ++q)
+        for (int e = 0; e < E; ++e)
+            drift[(size_t)q * E + e] = (float)((hw[e].theta(q * ds) - quanto[e]) * ds);
+    std::vector<float2> zc((size_t)(n + 1) * E * Ginst, make_float2(0.f, 0.f));
+    std::vector<int> date_p(n + 1, 0);
+    for (int j = 1; j <= n; ++j) date_p[j] = (j - 1) / (int)ppp;
+    for (int j = 0; j <= n; ++j) {
+        const double t = j * Delta;
+        for (int e = 0; e < E; ++e)
+            for (int g = 0; g < Ginst; ++g) {
+                const double T = (g + 1) * delta;
+                if (T + 1e-12 < t) continue;
+                zc[((size_t)j * E + e) * Ginst + g] = make_float2((float)hw[e].lnA(t, T), (float)hw[e].B(t, T));
+            }
+    }
+    const int n_periods = n / (int)ppp + 1;
+    std::vector<float2> fix((size_t)(n_periods + 1) * E);
+    for (int p = 0; p <= n_periods; ++p)
+        for (int e = 0; e < E; ++e)
+            fix[(size_t)p * E + e] = make_float2((float)hw[e].lnA(p * delta, (p + 1) * delta),
+                                                 (float)hw[e].B(p * delta, (p + 1) * delta));
+    // date-bucketed weights, App. B formula regrouped by (counterparty, currency, reset date)
+    memset(&s->weights, 0, sizeof(SimWeights));
+    {
+        // accumulate in FP64, then round once
+        std::vector<double> wA((size_t)n_pf * C * E * Ginst, 0.0), wK(wA.size(), 0.0);
+        for (int p = 0; p < n_pf; ++p) {
+            const cva_portfolio_desc &d = pfs[p];
+            for (int sw = 0; sw < d.n_swaps; ++sw) {
+                const int e = d.ccy[sw], c = d.cpty[sw], m = d.n_periods[sw];
+                double ann = 0.0;
+                for (int g = 1; g <= m; ++g) ann += std::exp(-model->curve[e] * g * delta);
+                const double Sigma = (1.0 - std::exp(-model->curve[e] * m * delta)) / (delta * ann);
+                const double wN = d.omega[sw] * d.notional[sw];
+                const size_t base = (((size_t)p * C + c) * E + e) * Ginst;
+                for (int h = 0; h < m; ++h) wA[base + h] += wN;                  // float notional, period h
+                for (int g = 1; g <= m; ++g) wK[base + g - 1] += delta * wN * Sigma;   // fixed coupon at g
+            }
+        }
+        for (size_t i = 0; i < wA.size(); ++i) {
+            s->weights.wA[i] = (float)wA[i];
+            s->weights.wK[i] = (float)wK[i];
+        }
+    }
+    s->recovery.assign(model->recovery, model->recovery + C);
+
+    // ---- device buffers ----
+    const size_t Mz = (size_t)M;
+#define TRY_ALLOC(p, n_)                           \
+    do {                                           \
+        cva_status _s = dev_alloc(&(p), (n_));     \
+        if (_s != CVA_OK) {                        \
+            free_sim(s);                           \
+            return _s;                             \
+        }                                          \
+    } while (0)
+    TRY_ALLOC(s->d_zc, zc.size());
+    TRY_ALLOC(s->d_fix, fix.size());
+    TRY_ALLOC(s->d_date_p, date_p.size());
+    TRY_ALLOC(s->d_drift, drift.size());
+    TRY_ALLOC(s->d_features, (size_t)(n + 1) * F * Mz);
+    TRY_ALLOC(s->d_disc, (size_t)(n + 1) * Mz);
+    TRY_ALLOC(s->d_thr, (size_t)(n + 1) * C * Mz);
+    TRY_ALLOC(s->d_expo, (size_t)n_pf * (n + 1) * C * Mz);
+    if (flags & CVA_KEEP_EXPOSURES) TRY_ALLOC(s->d_mtm, (size_t)n_pf * (n + 1) * C * Mz);
+    TRY_ALLOC(s->d_targets, (size_t)n_pf * n * Mz);
+    if (flags & CVA_KEEP_DEFAULTS) TRY_ALLOC(s->d_idx, Mz * N * C);
+#undef TRY_ALLOC
+    cudaError_t e1 = cudaMemcpy(s->d_zc, zc.data(), zc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaError_t e2 = cudaMemcpy(s->d_fix, fix.data(), fix.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaError_t e3 = cudaMemcpy(s->d_date_p, date_p.data(), date_p.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaError_t e4 = cudaMemcpy(s->d_drift, drift.data(), drift.size() * sizeof(float), cudaMemcpyHostToDevice);
+    for (cudaError_t e : {e1, e2, e3, e4})
+        if (e != cudaSuccess) {
+            free_sim(s);
+            return cuda_fail(e, "table upload");
+        }
+    if (flags & CVA_PROFILE)
+        for (cudaEvent_t &ev : s->ev)
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                free_sim(s);
+                return fail(CVA_ECUDA, "event creation failed");
+            }
+    *out = reinterpret_cast<cva_sim *>(s);
+    return CVA_OK;
+}
+
+cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *stream)
+{
+    if (!sim) return fail(CVA_EINVAL, "sim is NULL");
+    Sim &s = *reinterpret_cast<Sim *>(sim);
+    if (k0 + s.M > 0xffffffffull) return fail(CVA_EINVAL, "k0 + M must fit in 32 bits");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (s.ev[0]) CVA_CUDA_TRY(cudaEventRecord(s.ev[0], st));
+    cva_status r = launch_outer(s, seed, k0, st);
+    if (r != CVA_OK) return r;
+    if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
+    r = launch_inner(s, seed, k0, st);
+    if (r != CVA_OK) return r;
+    if (s.ev[2]) CVA_CUDA_TRY(cudaEventRecord(s.ev[2], st));
+    return CVA_OK;
+}
+
+cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[2])
+{
+    if (!sim || !out_ms) return fail(CVA_EINVAL, "NULL argument");
+    const Sim &s = *reinterpret_cast<const Sim *>(sim);
+    if (!s.ev[0]) return fail(CVA_EINVAL, "sim was not created with CVA_PROFILE");
+    CVA_CUDA_TRY(cudaEventSynchronize(s.ev[2]));
+    CVA_CUDA_TRY(cudaEventElapsedTime(&out_ms[0], s.ev[0], s.ev[1]));
+    CVA_CUDA_TRY(cudaEventElapsedTime(&out_ms[1], s.ev[1], s.ev[2]));
+    return CVA_OK;
+}
+
+cva_status cva_sim_view(const cva_sim *sim, int what, void **dev_ptr, size_t *bytes)
+{
+    if (!sim || !dev_ptr || !bytes) return fail(CVA_EINVAL, "NULL argument");
+    const Sim &s = *reinterpret_cast<const Sim *>(sim);
+    const size_t M = s.M, n = s.n;
+    void *p = nullptr;
+    size_t b = 0;
+    switch (what) {
+    case CVA_VIEW_FEATURES: p = s.d_features; b = (n + 1) * s.F * M * 4; break;
+    case CVA_VIEW_TARGETS: p = s.d_targets; b = (size_t)s.NPF * n * M * 4; break;
+    case CVA_VIEW_DISCOUNT: p = s.d_disc; b = (n + 1) * M * 4; break;
+    case CVA_VIEW_THRESHOLD: p = s.d_thr; b = (n + 1) * s.C * M * 4; break;
+    case CVA_VIEW_EXPOSURE: p = s.d_expo; b = (size_t)s.NPF * (n + 1) * s.C * M * 4; break;
+    case CVA_VIEW_MTM: p = s.d_mtm; b = (size_t)s.NPF * (n + 1) * s.C * M * 4; break;
+    case CVA_VIEW_DEFAULTS: p = s.d_idx; b = M * s.N * s.C; break;
+    default: return fail(CVA_EINVAL, "unknown view");
+    }
+    if (!p) return fail(CVA_EINVAL, "view not kept (see the flags of cva_sim_create)");
+    *dev_ptr = p;
+    *bytes = b;
+    return CVA_OK;
+}
+
+cva_status cva_sim_shape(const cva_sim *sim, int64_t out[6])
+{
+    if (!sim || !out) return fail(CVA_EINVAL, "NULL argument");
+    const Sim &s = *reinterpret_cast<const Sim *>(sim);
+    out[0] = (int64_t)s.M;
+    out[1] = s.N;
+    out[2] = s.n;
+    out[3] = s.F;
+    out[4] = s.C;
+    out[5] = s.NPF;
+    return CVA_OK;
+}
+
+void cva_sim_destroy(cva_sim *sim) { free_sim(reinterpret_cast<Sim *>(sim)); }
+
+cva_status cva_cva0(const float *xi0_dev, uint64_t M, double *out2_host, void *stream)
+{
+    return mean_fp64(xi0_dev, M, out2_host, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_regress(const float *targets_dev, const float *features_dev, int F, uint64_t M, int basis,
+                       float *pred_dev, double *coef_host, void *stream)
+{
+    return lsq_grouped_strided(features_dev, 0, targets_dev, 0, pred_dev, 0, F, M, basis, 1, coef_host,
+                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float *pred_dev, double *coef_host,
+                           void *stream)
+{
+    if (!sim) return fail(CVA_EINVAL, "sim is NULL");
+    const Sim &s = *reinterpret_cast<const Sim *>(sim);
+    if (pf < 0 || pf >= s.NPF) return fail(CVA_EINVAL, "portfolio index out of range");
+    if (s.n < 2) return fail(CVA_EINVAL, "need at least two pricing steps");
+    const size_t M = s.M;
+    const int m = (basis == CVA_BASIS_POLY2) ? 3 : s.F + 1;
+    const float *feat1 = s.d_features + (size_t)s.F * M;                 // date 1
+    const float *targ1 = s.d_targets + ((size_t)pf * s.n + 1) * M;        // date 1
+    float *pred1 = pred_dev ? pred_dev + M : nullptr;
+    return lsq_grouped_strided(feat1, (size_t)s.F * M, targ1, M, pred1, M, s.F, M, basis, s.n - 1,
+                               coef_host ? coef_host + m : nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_philox4x32_10(const uint32_t *ctr_dev, uint32_t *out_dev, uint64_t n, uint64_t seed,
+                             void *stream)
+{
+    return philox_blocks(ctr_dev, out_dev, n, seed, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

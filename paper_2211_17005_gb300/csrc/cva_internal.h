@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cva.h"
+
+namespace cva {
+
+constexpr int kMaxE = 16;
+constexpr int kMaxC = 16;
+constexpr int kMaxF = 2 * kMaxE - 1 + kMaxC;
+constexpr int kMaxG = 10;        // reset dates per swap schedule (periods)
+constexpr int kMaxPF = 6;        // portfolios simulated together
+constexpr int kMaxW = 5120;     // NPF*C*E*G weights of each kind held in constant memory
+
+// Per-thread error message of the C ABI.
+void set_error(const std::string &msg);
+cva_status fail(cva_status st, const std::string &msg);
+cva_status cuda_fail(cudaError_t e, const char *what);
+
+#define CVA_CUDA_TRY(expr)                                                   \
+    do {                                                                     \
+        cudaError_t _e = (expr);                                             \
+        if (_e != cudaSuccess) return ::cva::cuda_fail(_e, #expr);           \
+    } while (0)
+
+// Scalars and small tables of a simulation, uploaded to __constant__ memory
+// before each launch of the outer-path kernel.
+struct SimConsts {
+    int E, C, CS, F, G, NPF, n, S, ppp;
+    double ds_d;                           // sub-step length in FP64 (discount integral)
+    float ds, sqds;
+    float L[kMaxF * (kMaxF + 1) / 2];      // packed lower Cholesky factor, row-major
+    float hw_a_ds[kMaxE];                  // a_e * ds
+    float hw_sig_sqds[kMaxE];              // sigma^r_e * sqrt(ds)
+    float fx_drift_ds[kMaxE];              // -sigma^chi_e^2 / 2 * ds
+    float fx_sig_sqds[kMaxE];              // sigma^chi_e * sqrt(ds)
+    float r0[kMaxE], lchi0[kMaxE];         // initial state
+    float fix0_m1[kMaxE];                  // 1/ZC_0(delta) - 1 (first fixing)
+    float cir_kds[kMaxC], cir_ktds[kMaxC], cir_nu_sqds[kMaxC];
+    float gamma0[kMaxC], lgd[kMaxC];
+};
+
+// Date-bucketed portfolio weights, [pf][c][e][g] with compile-time strides
+// (C, E, G of the kernel instantiation):
+//   wA[..][h]  = sum over live swaps of (c, e) with n_periods >= h+1 of omega*N
+//                (floating notional of period h, h = 0..G-1)
+//   wK[..][g-1] = delta * sum over swaps of (c, e) with n_periods >= g of omega*N*Sigma
+//                (fixed coupon paid at reset g, g = 1..G)
+struct SimWeights {
+    float wA[kMaxW];
+    float wK[kMaxW];
+};
+
+struct Sim {
+    // shape
+    int E, C, CS, F, G, NPF, n, S, ppp, Ginst;
+    uint64_t M;
+    uint32_t N;
+    uint32_t flags;
+    double horizon, delta;
+    // host tables
+    SimConsts consts;
+    SimWeights weights;
+    std::vector<double> recovery;
+    // device tables
+    float2 *d_zc = nullptr;        // [n+1][E][Ginst]  (lnA, B)
+    float2 *d_fix = nullptr;       // [n_periods+1][E] (lnA, B) of ZC_{p delta}((p+1) delta)
+    int *d_date_p = nullptr;       // [n+1] period index of t_j
+    float *d_drift = nullptr;      // [n*S][E] (theta_e(t_q) - quanto_e) * ds
+    // device outputs / scratch
+    float *d_features = nullptr;   // [n+1][F][M]
+    float *d_disc = nullptr;       // [n+1][M]
+    float *d_thr = nullptr;        // [n+1][C][M]
+    float *d_expo = nullptr;       // [NPF][n+1][C][M]
+    float *d_mtm = nullptr;        // [NPF][n+1][C][M] (optional)
+    float *d_targets = nullptr;    // [NPF][n][M]
+    uint8_t *d_idx = nullptr;      // [M][N][C] (optional)
+    // profiling events: before outer, between, after inner
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+// Kernel launchers (sim.cu).
+cva_status launch_outer(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);
+cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);
+void forget_const_owner(const Sim *s);
+bool outer_supported(int E, int C, int CS, int G, int NPF, int *Ginst);
+
+// Regression (lsq.cu): least squares for `groups` dates at once; group g reads
+// features feat0 + g*feat_stride ([F][M]) and targets targ0 + g*targ_stride.
+cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const float *targ0,
+                               size_t targ_stride, float *pred0, size_t pred_stride, int F,
+                               uint64_t M, int basis, int groups, double *coef_host, cudaStream_t st);
+
+// CVA_0 reduction (reduce.cu).
+cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);
+cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st);
+
+}  // namespace cva

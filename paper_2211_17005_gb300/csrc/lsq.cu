@@ -1,0 +1,344 @@
+// Grouped least-squares regression of eq. (e:forw), one group per pricing date:
+//   w = argmin_w sum_k (xi_k - w^T phi(Y_k))^2.
+// The augmented Gram matrix [phi, xi]^T [phi, xi] of the basis centred on path
+// 0's state is accumulated from FP32 products in FP32 runs of >= 64 rows, then
+// in FP64 (per thread, per block, then across blocks in a fixed order), and
+// solved by a Jacobi-scaled Cholesky factorisation in FP64. The pass over the
+// features and targets is the only HBM traffic: every byte is read once.
+#include <math.h>
+
+#include <mutex>
+
+#include "cva_internal.h"
+
+namespace cva {
+
+namespace {
+
+constexpr int kGramThreads = 256;
+
+struct LsqArgs {
+    const float *feat0;
+    size_t feat_stride;   // floats between groups' feature blocks ([F][M] each)
+    const float *targ0;
+    size_t targ_stride;   // floats between groups' targets
+    float *pred0;
+    size_t pred_stride;
+    int F, m, basis, chunks;
+    uint32_t M, rows_per_chunk;
+    double *part;         // [groups][chunks][NUT*16]
+    double *coef;         // [groups][m] centred basis
+    double *coef_raw;     // [groups][m] raw basis
+    int *status;          // [groups] dropped columns
+};
+
+// value of augmented column `col` at row k (col == m is the target)
+__device__ __forceinline__ float basis_value(const LsqArgs &a, const float *feat, const float *targ,
+                                            int col, uint32_t k)
+{
+    if (col == a.m) return __ldg(targ + k);
+    if (col == 0) return 1.f;
+    if (a.basis == CVA_BASIS_POLY2) {
+        const float d = __ldg(feat + k) - __ldg(feat);
+        return col == 1 ? d : d * d;
+    }
+    const float *f = feat + (size_t)(col - 1) * a.M;
+    return __ldg(f + k) - __ldg(f);
+}
+
+template <int MP, int TR>
+__global__ void __launch_bounds__(kGramThreads) lsq_gram(LsqArgs a)
+{
+    constexpr int NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2, RS = MP + 4;
+    constexpr int NRG = kGramThreads / NUT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *tile = reinterpret_cast<float *>(smem);          // [TR][RS]
+    const int g = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    const float *feat = a.feat0 + (size_t)g * a.feat_stride;
+    const float *targ = a.targ0 + (size_t)g * a.targ_stride;
+    const uint32_t r_begin = (uint32_t)chunk * a.rows_per_chunk;
+    const uint32_t r_end = min(a.M, r_begin + a.rows_per_chunk);
+    const int mA = a.m + 1;
+
+    // this thread's 4x4 block (bi <= bj) and row group
+    const int b = tid % NUT, rg = tid / NUT;
+    int bi = 0, bj = 0;
+    {
+        int t = b;
+        for (int i = 0; i < NBLK; ++i) {
+            if (t < NBLK - i) {
+                bi = i;
+                bj = i + t;
+                break;
+            }
+            t -= NBLK - i;
+        }
+    }
+    double dacc[16];
+    float acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        dacc[i] = 0.0;
+        acc[i] = 0.f;
+    }
+    int since_flush = 0;
+
+    for (uint32_t r0 = r_begin; r0 < r_end; r0 += TR) {
+        __syncthreads();
+        for (int i = tid; i < MP * TR; i += kGramThreads) {
+            const int col = i / TR, r = i % TR;
+            const uint32_t k = r0 + r;
+            float v = 0.f;
+            if (col < mA && k < r_end) v = basis_value(a, feat, targ, col, k);
+            tile[r * RS + col] = v;
+        }
+        __syncthreads();
+        if (rg < NRG) {
+            for (int r = rg; r < TR; r += NRG) {
+                const float4 x = *reinterpret_cast<const float4 *>(tile + r * RS + 4 * bi);
+                const float4 y = *reinterpret_cast<const float4 *>(tile + r * RS + 4 * bj);
+                const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(xv[u], yv[v], acc[u * 4 + v]);
+                if (++since_flush == 64) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        dacc[i] += (double)acc[i];
+                        acc[i] = 0.f;
+                    }
+                    since_flush = 0;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dacc[i] += (double)acc[i];
+
+    // reduce the row groups in a fixed order
+    __syncthreads();
+    double *red = reinterpret_cast<double *>(smem);        // [NRG][NUT*16]
+    if (rg < NRG)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) red[(size_t)rg * NUT * 16 + b * 16 + i] = dacc[i];
+    __syncthreads();
+    double *out = a.part + ((size_t)g * a.chunks + chunk) * NUT * 16;
+    for (int e = tid; e < NUT * 16; e += kGramThreads) {
+        double s = 0.0;
+        for (int q = 0; q < NRG; ++q) s += red[(size_t)q * NUT * 16 + e];
+        out[e] = s;
+    }
+}
+
+template <int MP>
+__global__ void __launch_bounds__(256) lsq_solve(LsqArgs a)
+{
+    constexpr int NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2;
+    __shared__ double blocks[NUT * 16];
+    __shared__ double A[MP * MP];
+    const int g = blockIdx.x, tid = threadIdx.x, m = a.m, mA = m + 1;
+    for (int e = tid; e < NUT * 16; e += blockDim.x) {
+        double s = 0.0;
+        const double *p = a.part + (size_t)g * a.chunks * NUT * 16 + e;
+        for (int c = 0; c < a.chunks; ++c) s += p[(size_t)c * NUT * 16];
+        blocks[e] = s;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    // unpack upper-triangular 4x4 blocks into the dense augmented matrix
+    int b = 0;
+    for (int bi = 0; bi < NBLK; ++bi)
+        for (int bj = bi; bj < NBLK; ++bj, ++b)
+            for (int u = 0; u < 4; ++u)
+                for (int v = 0; v < 4; ++v) {
+                    const int i = 4 * bi + u, j = 4 * bj + v;
+                    if (i < mA && j < mA) {
+                        A[i * MP + j] = blocks[b * 16 + u * 4 + v];
+                        A[j * MP + i] = blocks[b * 16 + u * 4 + v];
+                    }
+                }
+    // Jacobi scaling, Cholesky of the scaled normal matrix, rank-deficient columns dropped
+    double sc[MP], L[MP * MP], y[MP];
+    bool drop[MP];
+    for (int i = 0; i < m; ++i) {
+        const double d = A[i * MP + i];
+        drop[i] = !(d > 0.0);
+        sc[i] = drop[i] ? 0.0 : 1.0 / sqrt(d);
+    }
+    int dropped = 0;
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = (drop[i] || drop[j]) ? 0.0 : A[i * MP + j] * sc[i] * sc[j];
+            for (int p = 0; p < j; ++p) s -= L[i * MP + p] * L[j * MP + p];
+            if (i == j) {
+                if (drop[i] || !(s > 1e-12)) {
+                    drop[i] = true;
+                    L[i * MP + i] = 1.0;
+                    for (int p = 0; p < i; ++p) L[i * MP + p] = 0.0;
+                    ++dropped;
+                } else {
+                    L[i * MP + i] = sqrt(s);
+                }
+            } else {
+                L[i * MP + j] = drop[i] ? 0.0 : s / L[j * MP + j];
+            }
+        }
+    }
+    for (int i = 0; i < m; ++i) {           // L y = D^{-1/2} b
+        double s = drop[i] ? 0.0 : A[i * MP + m] * sc[i];
+        for (int p = 0; p < i; ++p) s -= L[i * MP + p] * y[p];
+        y[i] = drop[i] ? 0.0 : s / L[i * MP + i];
+    }
+    double w[MP];
+    for (int i = m - 1; i >= 0; --i) {     // L^T z = y, w = D^{-1/2} z
+        double s = y[i];
+        for (int p = i + 1; p < m; ++p) s -= L[p * MP + i] * w[p];
+        w[i] = drop[i] ? 0.0 : s / L[i * MP + i];
+    }
+    for (int i = 0; i < m; ++i) w[i] *= sc[i];
+    double *co = a.coef + (size_t)g * m, *cr = a.coef_raw + (size_t)g * m;
+    for (int i = 0; i < m; ++i) co[i] = w[i];
+    const float *feat = a.feat0 + (size_t)g * a.feat_stride;
+    if (a.basis == CVA_BASIS_POLY2) {
+        const double c = (double)feat[0];
+        cr[0] = w[0] - w[1] * c + w[2] * c * c;
+        cr[1] = w[1] - 2.0 * w[2] * c;
+        cr[2] = w[2];
+    } else {
+        double w0 = w[0];
+        for (int f = 0; f < a.F; ++f) {
+            const double c = (double)feat[(size_t)f * a.M];
+            w0 -= w[1 + f] * c;
+            cr[1 + f] = w[1 + f];
+        }
+        cr[0] = w0;
+    }
+    a.status[g] = dropped;
+}
+
+__global__ void __launch_bounds__(256) lsq_predict(LsqArgs a)
+{
+    const int g = blockIdx.y;
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.M) return;
+    const double *co = a.coef + (size_t)g * a.m;
+    const float *feat = a.feat0 + (size_t)g * a.feat_stride;
+    float acc = (float)co[0];
+    if (a.basis == CVA_BASIS_POLY2) {
+        const float d = __ldg(feat + k) - __ldg(feat);
+        acc = fmaf((float)co[1], d, acc);
+        acc = fmaf((float)co[2], d * d, acc);
+    } else {
+        for (int f = 0; f < a.F; ++f) {
+            const float *fr = feat + (size_t)f * a.M;
+            acc = fmaf((float)co[1 + f], __ldg(fr + k) - __ldg(fr), acc);
+        }
+    }
+    a.pred0[(size_t)g * a.pred_stride + k] = acc;
+}
+
+// Library-owned scratch for the Gram partials and coefficients, per device.
+// Reuse is ordered by an event: a call waits for the previous call's kernels.
+struct LsqScratch {
+    double *buf = nullptr;
+    size_t cap = 0;   // doubles
+    cudaEvent_t done = nullptr;
+};
+std::mutex g_lsq_mu;
+LsqScratch g_lsq[64];
+
+}  // namespace
+
+cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const float *targ0,
+                               size_t targ_stride, float *pred0, size_t pred_stride, int F,
+                               uint64_t M, int basis, int groups, double *coef_host, cudaStream_t st)
+{
+    if (!feat0 || !targ0 || M == 0 || groups <= 0) return fail(CVA_EINVAL, "regress: bad arguments");
+    if (M > 0x7fffffffull) return fail(CVA_EINVAL, "regress: M too large");
+    if (basis != CVA_BASIS_LINEAR && basis != CVA_BASIS_POLY2) return fail(CVA_EINVAL, "regress: unknown basis");
+    const int m = (basis == CVA_BASIS_POLY2) ? 3 : F + 1;
+    if (basis == CVA_BASIS_LINEAR && (F < 1 || m + 1 > 32))
+        return fail(CVA_ENOTSUP, "regress: linear basis supports 1 <= F <= 30");
+    if (basis == CVA_BASIS_POLY2 && F < 1) return fail(CVA_EINVAL, "regress: need one factor");
+    const int MP = (m + 1 <= 4) ? 4 : 32;
+    const int NUT = (MP / 4) * (MP / 4 + 1) / 2;
+    const uint64_t max_chunks = (M + 1023) / 1024;
+    uint64_t chunks = (2432 + groups - 1) / groups;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    const uint32_t rows_per_chunk = (uint32_t)((M + chunks - 1) / chunks);
+
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_lsq_mu);
+    LsqScratch &sc = g_lsq[dev];
+    const size_t need = (size_t)groups * chunks * NUT * 16 + 2 * (size_t)groups * m + groups;
+    if (!sc.done) CVA_CUDA_TRY(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming));
+    else CVA_CUDA_TRY(cudaStreamWaitEvent(st, sc.done, 0));
+    if (sc.cap < need) {
+        if (sc.buf) {
+            CVA_CUDA_TRY(cudaEventSynchronize(sc.done));
+            cudaFree(sc.buf);
+            sc.buf = nullptr;
+            sc.cap = 0;
+        }
+        if (cudaMalloc(&sc.buf, need * sizeof(double)) != cudaSuccess)
+            return fail(CVA_ENOMEM, "regress: scratch allocation failed");
+        sc.cap = need;
+    }
+    LsqArgs a;
+    a.feat0 = feat0;
+    a.feat_stride = feat_stride;
+    a.targ0 = targ0;
+    a.targ_stride = targ_stride;
+    a.pred0 = pred0;
+    a.pred_stride = pred_stride;
+    a.F = F;
+    a.m = m;
+    a.basis = basis;
+    a.chunks = (int)chunks;
+    a.M = (uint32_t)M;
+    a.rows_per_chunk = rows_per_chunk;
+    a.part = sc.buf;
+    a.coef = a.part + (size_t)groups * chunks * NUT * 16;
+    a.coef_raw = a.coef + (size_t)groups * m;
+    a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)groups * m);
+
+    const dim3 ggrid((unsigned)chunks, (unsigned)groups);
+    if (MP == 4) {
+        constexpr int TR = 1024;
+        const size_t sm = (size_t)TR * 8 * sizeof(float);
+        lsq_gram<4, TR><<<ggrid, kGramThreads, sm, st>>>(a);
+        CVA_CUDA_TRY(cudaGetLastError());
+        lsq_solve<4><<<groups, 256, 0, st>>>(a);
+    } else {
+        constexpr int TR = 256;
+        const size_t sm = (size_t)TR * 36 * sizeof(float);
+        lsq_gram<32, TR><<<ggrid, kGramThreads, sm, st>>>(a);
+        CVA_CUDA_TRY(cudaGetLastError());
+        lsq_solve<32><<<groups, 256, 0, st>>>(a);
+    }
+    CVA_CUDA_TRY(cudaGetLastError());
+    if (pred0) {
+        lsq_predict<<<dim3((unsigned)((M + 255) / 256), (unsigned)groups), 256, 0, st>>>(a);
+        CVA_CUDA_TRY(cudaGetLastError());
+    }
+    if (coef_host) {
+        CVA_CUDA_TRY(cudaMemcpyAsync(coef_host, a.coef_raw, sizeof(double) * groups * m,
+                                     cudaMemcpyDeviceToHost, st));
+        std::vector<int> status(groups);
+        CVA_CUDA_TRY(cudaMemcpyAsync(status.data(), a.status, sizeof(int) * groups,
+                                     cudaMemcpyDeviceToHost, st));
+        CVA_CUDA_TRY(cudaEventRecord(sc.done, st));
+        CVA_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int g = 0; g < groups; ++g)
+            if (status[g] != 0) return fail(CVA_ENUMERIC, "regress: rank-deficient normal equations");
+        return CVA_OK;
+    }
+    CVA_CUDA_TRY(cudaEventRecord(sc.done, st));
+    return CVA_OK;
+}
+
+}  // namespace cva

@@ -1,0 +1,115 @@
+// CVA_0 = mean over outer paths of the date-0 averaged targets (eq.
+// (eq:CVA_portfolio) at i = 0), with its Monte Carlo standard error. Two-stage
+// FP64 reduction with a fixed grid and a fixed tree, so the result does not
+// depend on scheduling.
+#include <math.h>
+
+#include <mutex>
+
+#include "cva_internal.h"
+#include "rng.cuh"
+
+namespace cva {
+
+namespace {
+
+constexpr int kRedBlocks = 304;    // 2 x 152 SMs
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ void block_sum2(double &a, double &b, double2 *sh)
+{
+    const int tid = threadIdx.x;
+    sh[tid] = make_double2(a, b);
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (tid < s) {
+            sh[tid].x += sh[tid + s].x;
+            sh[tid].y += sh[tid + s].y;
+        }
+        __syncthreads();
+    }
+    a = sh[0].x;
+    b = sh[0].y;
+}
+
+__global__ void __launch_bounds__(kRedThreads) sum_stage1(const float *__restrict__ x, uint64_t M,
+                                                          double2 *__restrict__ part)
+{
+    __shared__ double2 sh[kRedThreads];
+    double s = 0.0, q = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const double v = (double)__ldg(x + i);
+        s += v;
+        q = fma(v, v, q);
+    }
+    block_sum2(s, q, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(s, q);
+}
+
+__global__ void __launch_bounds__(kRedThreads) sum_stage2(const double2 *__restrict__ part, int nparts,
+                                                          double2 *__restrict__ out)
+{
+    __shared__ double2 sh[kRedThreads];
+    double s = 0.0, q = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
+        s += part[i].x;
+        q += part[i].y;
+    }
+    block_sum2(s, q, sh);
+    if (threadIdx.x == 0) out[0] = make_double2(s, q);
+}
+
+__global__ void philox_fill(const uint4 *__restrict__ ctr, uint4 *__restrict__ out, uint64_t n,
+                            uint32_t k0, uint32_t k1)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+std::mutex g_red_mu;
+double2 *g_red_buf[64] = {};
+
+}  // namespace
+
+cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st)
+{
+    if (!ctr || !out) return fail(CVA_EINVAL, "philox: NULL pointer");
+    if (n == 0) return CVA_OK;
+    if (((uintptr_t)ctr | (uintptr_t)out) & 15) return fail(CVA_EINVAL, "philox: arrays must be 16-byte aligned");
+    const uint64_t blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffull) return fail(CVA_EINVAL, "philox: n too large");
+    philox_fill<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const uint4 *>(ctr), reinterpret_cast<uint4 *>(out),
+                                                  n, (uint32_t)seed, (uint32_t)(seed >> 32));
+    CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
+}
+
+cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st)
+{
+    if (!x || !out2 || M == 0) return fail(CVA_EINVAL, "cva0: null pointer or M == 0");
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_red_mu);
+    if (!g_red_buf[dev]) {
+        cudaError_t e = cudaMalloc(&g_red_buf[dev], sizeof(double2) * (kRedBlocks + 1));
+        if (e != cudaSuccess) return fail(CVA_ENOMEM, "cva0: scratch allocation failed");
+    }
+    double2 *part = g_red_buf[dev];
+    sum_stage1<<<kRedBlocks, kRedThreads, 0, st>>>(x, M, part);
+    CVA_CUDA_TRY(cudaGetLastError());
+    sum_stage2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, part + kRedBlocks);
+    CVA_CUDA_TRY(cudaGetLastError());
+    double2 h;
+    CVA_CUDA_TRY(cudaMemcpyAsync(&h, part + kRedBlocks, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CVA_CUDA_TRY(cudaStreamSynchronize(st));
+    const double mean = h.x / (double)M;
+    double var = (M > 1) ? (h.y - (double)M * mean * mean) / (double)(M - 1) : 0.0;
+    if (var < 0.0) var = 0.0;
+    out2[0] = mean;
+    out2[1] = sqrt(var / (double)M);
+    return CVA_OK;
+}
+
+}  // namespace cva
