@@ -93,8 +93,14 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, device_index):
+        import torch
+        self.index = str(device_index)
+        try:   # address the GPU by UUID: CUDA_VISIBLE_DEVICES may renumber devices
+            u = str(torch.cuda.get_device_properties(device_index).uuid)
+            self.index = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
         self.proc = None
         self.lines = []
 

@@ -13,7 +13,7 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 import torch
 
-from . import _native as N
+from . import _native as nat
 
 _F32, _U8 = "<f4", "|u1"
 
@@ -33,15 +33,15 @@ class _Keep:
         return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
 
-def model_desc(model, keep: _Keep) -> N.ModelDesc:
-    return N.ModelDesc(model.E, model.C, keep.d(model.hw_a), keep.d(model.hw_sigma), keep.d(model.curve),
+def model_desc(model, keep: _Keep) -> nat.ModelDesc:
+    return nat.ModelDesc(model.E, model.C, keep.d(model.hw_a), keep.d(model.hw_sigma), keep.d(model.curve),
                        keep.d(model.fx_vol), keep.d(model.fx0), keep.d(model.cir_kappa),
                        keep.d(model.cir_theta), keep.d(model.cir_nu), keep.d(model.gamma0),
                        keep.d(model.recovery), keep.d(model.corr))
 
 
-def portfolio_desc(pf, keep: _Keep) -> N.PortfolioDesc:
-    return N.PortfolioDesc(pf.n_swaps, keep.i(pf.ccy), keep.i(pf.cpty), keep.i(pf.omega),
+def portfolio_desc(pf, keep: _Keep) -> nat.PortfolioDesc:
+    return nat.PortfolioDesc(pf.n_swaps, keep.i(pf.ccy), keep.i(pf.cpty), keep.i(pf.omega),
                            keep.i(pf.n_periods), keep.d(pf.notional), float(pf.delta))
 
 
@@ -68,16 +68,16 @@ class Simulation:
         L = N_lib()
         keep = _Keep()
         md = model_desc(model, keep)
-        pds = (N.PortfolioDesc * len(portfolios))(*[portfolio_desc(p, keep) for p in portfolios])
-        gd = N.GridDesc(float(grid.horizon), int(grid.n_steps), int(grid.substeps))
-        flags = ((N.KEEP_DEFAULTS if keep_defaults else 0) | (N.KEEP_EXPOSURES if keep_exposures else 0)
-                 | (N.PROFILE if profile else 0))
+        pds = (nat.PortfolioDesc * len(portfolios))(*[portfolio_desc(p, keep) for p in portfolios])
+        gd = nat.GridDesc(float(grid.horizon), int(grid.n_steps), int(grid.substeps))
+        flags = ((nat.KEEP_DEFAULTS if keep_defaults else 0) | (nat.KEEP_EXPOSURES if keep_exposures else 0)
+                 | (nat.PROFILE if profile else 0))
         h = ctypes.c_void_p()
-        N.check(L.cva_sim_create(ctypes.byref(md), pds, len(portfolios), ctypes.byref(gd), int(M), int(N),
+        nat.check(L.cva_sim_create(ctypes.byref(md), pds, len(portfolios), ctypes.byref(gd), int(M), int(N),
                                  flags, ctypes.byref(h)), "cva_sim_create")
         self._h = h
         shp = (ctypes.c_int64 * 6)()
-        N.check(L.cva_sim_shape(h, shp), "cva_sim_shape")
+        nat.check(L.cva_sim_shape(h, shp), "cva_sim_shape")
         self.M, self.N, self.n, self.F, self.C, self.n_pf = (int(x) for x in shp)
         self.device = torch.device("cuda", torch.cuda.current_device())
 
@@ -94,43 +94,43 @@ class Simulation:
 
     def run(self, seed: int, k0: int = 0, stream: Optional[torch.cuda.Stream] = None):
         """Enqueue the outer-path and inner-default kernels for paths [k0, k0+M)."""
-        N.check(N_lib().cva_simulate(self._h, int(seed), int(k0), _stream_handle(stream)), "cva_simulate")
+        nat.check(N_lib().cva_simulate(self._h, int(seed), int(k0), _stream_handle(stream)), "cva_simulate")
         return self
 
     def kernel_ms(self) -> Tuple[float, float]:
         """(outer-path kernel, inner-default kernel) device milliseconds of the last run."""
         out = (ctypes.c_float * 2)()
-        N.check(N_lib().cva_sim_kernel_ms(self._h, out), "cva_sim_kernel_ms")
+        nat.check(N_lib().cva_sim_kernel_ms(self._h, out), "cva_sim_kernel_ms")
         return float(out[0]), float(out[1])
 
     def _view(self, what: int, shape, typestr=_F32) -> torch.Tensor:
         p = ctypes.c_void_p()
         b = ctypes.c_size_t()
-        N.check(N_lib().cva_sim_view(self._h, what, ctypes.byref(p), ctypes.byref(b)), "cva_sim_view")
+        nat.check(N_lib().cva_sim_view(self._h, what, ctypes.byref(p), ctypes.byref(b)), "cva_sim_view")
         t = torch.as_tensor(_DevArray(p.value, shape, typestr), device=self.device)
         t._cva_owner = self          # keep the simulation alive while the view is
         return t
 
     def features(self):
-        return self._view(N.VIEW_FEATURES, (self.n + 1, self.F, self.M))
+        return self._view(nat.VIEW_FEATURES, (self.n + 1, self.F, self.M))
 
     def targets(self):
-        return self._view(N.VIEW_TARGETS, (self.n_pf, self.n, self.M))
+        return self._view(nat.VIEW_TARGETS, (self.n_pf, self.n, self.M))
 
     def discount_integral(self):
-        return self._view(N.VIEW_DISCOUNT, (self.n + 1, self.M))
+        return self._view(nat.VIEW_DISCOUNT, (self.n + 1, self.M))
 
     def thresholds(self):
-        return self._view(N.VIEW_THRESHOLD, (self.n + 1, self.C, self.M))
+        return self._view(nat.VIEW_THRESHOLD, (self.n + 1, self.C, self.M))
 
     def exposures(self):
-        return self._view(N.VIEW_EXPOSURE, (self.n_pf, self.n + 1, self.C, self.M))
+        return self._view(nat.VIEW_EXPOSURE, (self.n_pf, self.n + 1, self.C, self.M))
 
     def mtm(self):
-        return self._view(N.VIEW_MTM, (self.n_pf, self.n + 1, self.C, self.M))
+        return self._view(nat.VIEW_MTM, (self.n_pf, self.n + 1, self.C, self.M))
 
     def defaults(self):
-        return self._view(N.VIEW_DEFAULTS, (self.M, self.N, self.C), _U8)
+        return self._view(nat.VIEW_DEFAULTS, (self.M, self.N, self.C), _U8)
 
     def cva0(self, pf: int = 0, stream=None) -> Tuple[float, float]:
         return cva0(self.targets()[pf, 0], stream=stream)
@@ -138,25 +138,25 @@ class Simulation:
     def regress_all(self, pf: int = 0, basis: str = "poly2", stream=None, want_coef: bool = True):
         """Least squares at every date 1..n-1 in one grouped launch; returns
         (predictions [n, M] on the device, coefficients [n, m] numpy or None)."""
-        b = N.BASIS_POLY2 if basis == "poly2" else N.BASIS_LINEAR
-        m = 3 if b == N.BASIS_POLY2 else self.F + 1
+        b = nat.BASIS_POLY2 if basis == "poly2" else nat.BASIS_LINEAR
+        m = 3 if b == nat.BASIS_POLY2 else self.F + 1
         pred = torch.zeros((self.n, self.M), dtype=torch.float32, device=self.device)
         coef = np.zeros((self.n, m)) if want_coef else None
         cp = coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_coef else None
-        N.check(N_lib().cva_regress_all(self._h, pf, b, ctypes.c_void_p(pred.data_ptr()), cp,
+        nat.check(N_lib().cva_regress_all(self._h, pf, b, ctypes.c_void_p(pred.data_ptr()), cp,
                                         _stream_handle(stream)), "cva_regress_all")
         return pred, coef
 
 
 def N_lib():
-    return N.lib()
+    return nat.lib()
 
 
 def cva0(xi0: torch.Tensor, stream=None) -> Tuple[float, float]:
     """CVA_0 and its standard error from the date-0 targets (device float tensor [M])."""
     assert xi0.is_cuda and xi0.dtype == torch.float32 and xi0.is_contiguous()
     out = np.zeros(2)
-    N.check(N_lib().cva_cva0(ctypes.c_void_p(xi0.data_ptr()), xi0.numel(),
+    nat.check(N_lib().cva_cva0(ctypes.c_void_p(xi0.data_ptr()), xi0.numel(),
                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)),
             "cva_cva0")
     return float(out[0]), float(out[1])
@@ -171,11 +171,11 @@ def regress(targets: torch.Tensor, features: torch.Tensor, basis: str = "linear"
     targets = targets.contiguous()
     features = features.contiguous()
     F, M = features.shape
-    b = N.BASIS_POLY2 if basis == "poly2" else N.BASIS_LINEAR
-    m = 3 if b == N.BASIS_POLY2 else F + 1
+    b = nat.BASIS_POLY2 if basis == "poly2" else nat.BASIS_LINEAR
+    m = 3 if b == nat.BASIS_POLY2 else F + 1
     pred = torch.empty(M, dtype=torch.float32, device=targets.device) if want_pred else None
     coef = np.zeros(m) if want_coef else None
-    N.check(N_lib().cva_regress(ctypes.c_void_p(targets.data_ptr()), ctypes.c_void_p(features.data_ptr()), F, M,
+    nat.check(N_lib().cva_regress(ctypes.c_void_p(targets.data_ptr()), ctypes.c_void_p(features.data_ptr()), F, M,
                                 b, ctypes.c_void_p(pred.data_ptr()) if want_pred else None,
                                 coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_coef else None,
                                 _stream_handle(stream)), "cva_regress")
@@ -187,6 +187,6 @@ def philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
     assert ctr.is_cuda and ctr.shape[-1] == 4 and ctr.element_size() == 4
     ctr = ctr.contiguous()
     out = torch.empty_like(ctr)
-    N.check(N_lib().cva_philox4x32_10(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+    nat.check(N_lib().cva_philox4x32_10(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       ctr.numel() // 4, int(seed), _stream_handle(stream)), "cva_philox4x32_10")
     return out

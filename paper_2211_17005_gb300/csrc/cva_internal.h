@@ -85,6 +85,13 @@ struct Sim {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
 
+// One compiled shape of the outer-path kernel (outer_*.cu).
+struct OuterInst {
+    int E, C, CS, G, NPF;
+    cva_status (*launch)(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);
+    void (*forget)(const Sim *s);
+};
+
 // Kernel launchers (sim.cu).
 cva_status launch_outer(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);
 cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);

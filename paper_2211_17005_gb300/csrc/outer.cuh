@@ -1,0 +1,252 @@
+// Outer-path kernel of the hierarchical CVA simulation (one thread per outer
+// path k, Sec. 3.2), templated on the model shape. Each translation unit that
+// includes this header gets its own copy of the constant-memory tables and of
+// their ownership state, so instantiations compile in parallel.
+//
+// Per Euler sub-step (Remark rem:finecoarse): Philox normals, correlation by the
+// Cholesky factor, Hull-White rates with the quanto drift, lognormal FX, CIR
+// intensities with full truncation (App. B), and the left-point integrals
+// int r^0 (FP64) and Lambda^c (compensated FP32). At each pricing date: bond
+// prices ZC_t(g delta) of every live reset date, the portfolio MtM per
+// counterparty from the App. B swap formula regrouped by (counterparty,
+// currency, reset date), the exposure (1-R_c) beta_j MtM^+ and the threshold
+// 1 - exp(-Lambda_c(t_j)). Outputs are structure-of-arrays with the path index
+// fastest.
+#pragma once
+#include <mutex>
+
+#include "cva_internal.h"
+#include "rng.cuh"
+
+namespace cva {
+namespace {
+
+static __constant__ SimConsts c_sim;
+static __constant__ SimWeights c_w;
+
+struct OuterArgs {
+    uint32_t M, k0, seed_lo, seed_hi;
+    const float2 *__restrict__ zc;     // [n+1][E][G] (lnA, B)
+    const float2 *__restrict__ fix;    // [periods+1][E] (lnA, B)
+    const int *__restrict__ date_p;    // [n+1]
+    const float *__restrict__ drift;   // [n*S][E]
+    float *features, *disc, *thr, *expo, *mtm;
+};
+
+template <int E, int C, int CS, int G, int NPF>
+__global__ void __launch_bounds__(128) outer_kernel(OuterArgs a)
+{
+    constexpr int F = 2 * E - 1 + CS;
+    constexpr int NB = (F + 3) / 4;
+    const uint32_t kl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kl >= a.M) return;
+    const uint32_t k = a.k0 + kl;
+    const size_t M = a.M;
+    const int n = c_sim.n, S = c_sim.S, ppp = c_sim.ppp;
+    const float ds = c_sim.ds;
+    const double ds_d = (double)c_sim.ds_d;
+
+    float r[E], lchi[E], fixm1[E];
+    float gam[C], lam[C], lamc[C], thr_prev[C];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        r[e] = c_sim.r0[e];
+        lchi[e] = c_sim.lchi0[e];
+        fixm1[e] = c_sim.fix0_m1[e];
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        gam[c] = c_sim.gamma0[c];
+        lam[c] = 0.f;
+        lamc[c] = 0.f;
+        thr_prev[c] = 0.f;
+    }
+    double I0 = 0.0;
+
+    // date 0
+    {
+#pragma unroll
+        for (int e = 0; e < E; ++e) a.features[(size_t)e * M + kl] = r[e];
+#pragma unroll
+        for (int e = 1; e < E; ++e) a.features[(size_t)(E - 1 + e) * M + kl] = lchi[e];
+#pragma unroll
+        for (int c = 0; c < CS; ++c) a.features[(size_t)(2 * E - 1 + c) * M + kl] = gam[c];
+        a.disc[kl] = 0.f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) a.thr[(size_t)c * M + kl] = 0.f;
+#pragma unroll
+        for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                a.expo[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
+                if (a.mtm) a.mtm[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
+            }
+    }
+
+    for (int j = 1; j <= n; ++j) {
+        for (int s = 0; s < S; ++s) {
+            const uint32_t q = (uint32_t)((j - 1) * S + s);
+            float z[4 * NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const uint4 x = philox4x32_10(make_uint4(k, q, 0u, (kStreamOuter << 24) | (uint32_t)b),
+                                              a.seed_lo, a.seed_hi);
+                box_muller(x.x, x.y, z[4 * b], z[4 * b + 1]);
+                box_muller(x.z, x.w, z[4 * b + 2], z[4 * b + 3]);
+            }
+            float W[F];
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                float acc = 0.f;
+#pragma unroll
+                for (int b = 0; b <= i; ++b) acc = fmaf(c_sim.L[i * (i + 1) / 2 + b], z[b], acc);
+                W[i] = acc;
+            }
+            const float r0 = r[0];
+            // left-point integrals: int r^0 in FP64, Lambda^c compensated FP32
+            I0 = fma((double)r0, ds_d, I0);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float gp = fmaxf(gam[c], 0.f);
+                const float y = fmaf(gp, ds, -lamc[c]);
+                const float t = lam[c] + y;
+                lamc[c] = (t - lam[c]) - y;
+                lam[c] = t;
+                if (c < CS) {
+                    constexpr int w0 = (CS > 0) ? 2 * E - 1 : 0;
+                    gam[c] += c_sim.cir_ktds[c] - c_sim.cir_kds[c] * gp
+                              + c_sim.cir_nu_sqds[c] * sqrtf(gp) * W[w0 + (c < CS ? c : 0)];
+                }
+            }
+            const float *drow = a.drift + (size_t)q * E;
+#pragma unroll
+            for (int e = 1; e < E; ++e)
+                lchi[e] += fmaf(r0 - r[e], ds, c_sim.fx_drift_ds[e]) + c_sim.fx_sig_sqds[e] * W[E - 1 + e];
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                r[e] += (__ldg(drow + e) - c_sim.hw_a_ds[e] * r[e]) + c_sim.hw_sig_sqds[e] * W[e];
+        }
+
+        // ---- pricing date t_j ----
+        const float I0f = (float)I0;
+        const float beta = expf(-I0f);
+        const int p = __ldg(a.date_p + j);
+        float mt[NPF][C];
+#pragma unroll
+        for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+            for (int c = 0; c < C; ++c) mt[pf][c] = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float re = r[e];
+            const float2 *tab = a.zc + ((size_t)j * E + e) * G;
+            float Z[G], D[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float2 t2 = __ldg(tab + g);
+                Z[g] = (g >= p) ? expf(fmaf(-t2.y, re, t2.x)) : 0.f;   // ZC_t((g+1) delta)
+            }
+            // D[h]: h == p -> ZC_t(t_+) (1/ZC_{t_-}(t_+) - 1); h > p -> ZC_t(h delta) - ZC_t((h+1) delta)
+#pragma unroll
+            for (int h = 0; h < G; ++h)
+                D[h] = (h == p) ? Z[h] * fixm1[e] : ((h > p) ? Z[h - 1 >= 0 ? h - 1 : 0] - Z[h] : 0.f);
+            const float chi = (e == 0) ? 1.f : expf(lchi[e]);
+#pragma unroll
+            for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int base = ((pf * C + c) * E + e) * G;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int h = 0; h < G; ++h) acc = fmaf(c_w.wA[base + h], D[h], acc);
+#pragma unroll
+                    for (int g = 0; g < G; ++g) acc = fmaf(-c_w.wK[base + g], Z[g], acc);
+                    mt[pf][c] = fmaf(chi, acc, mt[pf][c]);
+                }
+        }
+        if (j % ppp == 0) {   // reset date: fix the next floating coupon at today's rate
+            const float2 *fx = a.fix + (size_t)(j / ppp) * E;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const float2 f2 = __ldg(fx + e);
+                fixm1[e] = expm1f(fmaf(f2.y, r[e], -f2.x));
+            }
+        }
+
+        float *fe = a.features + (size_t)j * F * M + kl;
+#pragma unroll
+        for (int e = 0; e < E; ++e) fe[(size_t)e * M] = r[e];
+#pragma unroll
+        for (int e = 1; e < E; ++e) fe[(size_t)(E - 1 + e) * M] = lchi[e];
+#pragma unroll
+        for (int c = 0; c < CS; ++c) fe[(size_t)(2 * E - 1 + c) * M] = gam[c];
+        a.disc[(size_t)j * M + kl] = I0f;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float T = fmaxf(-expm1f(-lam[c]), thr_prev[c]);
+            thr_prev[c] = T;
+            a.thr[((size_t)j * C + c) * M + kl] = T;
+        }
+#pragma unroll
+        for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const size_t o = ((size_t)(pf * (n + 1) + j) * C + c) * M + kl;
+                a.expo[o] = c_sim.lgd[c] * beta * fmaxf(mt[pf][c], 0.f);
+                if (a.mtm) a.mtm[o] = mt[pf][c];
+            }
+    }
+}
+
+
+// Constant-memory ownership of this translation unit: a launch for another
+// simulation re-uploads the tables, and every launch first waits for the
+// previous one (on whichever stream) before constant memory can change.
+static std::mutex t_const_mu;
+static const Sim *t_owner[64] = {};
+static cudaEvent_t t_last[64] = {};
+
+static void outer_forget(const Sim *s)
+{
+    std::lock_guard<std::mutex> lk(t_const_mu);
+    for (auto &o : t_owner)
+        if (o == s) o = nullptr;
+}
+
+template <int E, int C, int CS, int G, int NPF>
+cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
+{
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    OuterArgs args;
+    args.M = (uint32_t)s.M;
+    args.k0 = (uint32_t)k0;
+    args.seed_lo = (uint32_t)seed;
+    args.seed_hi = (uint32_t)(seed >> 32);
+    args.zc = s.d_zc;
+    args.fix = s.d_fix;
+    args.date_p = s.d_date_p;
+    args.drift = s.d_drift;
+    args.features = s.d_features;
+    args.disc = s.d_disc;
+    args.thr = s.d_thr;
+    args.expo = s.d_expo;
+    args.mtm = s.d_mtm;
+    std::lock_guard<std::mutex> lk(t_const_mu);
+    if (!t_last[dev]) CVA_CUDA_TRY(cudaEventCreateWithFlags(&t_last[dev], cudaEventDisableTiming));
+    else CVA_CUDA_TRY(cudaStreamWaitEvent(st, t_last[dev], 0));
+    if (t_owner[dev] != &s) {
+        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_sim, &s.consts, sizeof(SimConsts), 0, cudaMemcpyHostToDevice, st));
+        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_w, &s.weights, sizeof(SimWeights), 0, cudaMemcpyHostToDevice, st));
+        t_owner[dev] = &s;
+    }
+    const unsigned blocks = (args.M + 127u) / 128u;
+    outer_kernel<E, C, CS, G, NPF><<<blocks, 128, 0, st>>>(args);
+    CVA_CUDA_TRY(cudaGetLastError());
+    CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
+    return CVA_OK;
+}
+
+}  // namespace
+}  // namespace cva

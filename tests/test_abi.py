@@ -72,3 +72,16 @@ def test_invalid_inputs_are_rejected_on_the_host(libcva):
     # regress / cva0 argument checks
     assert L.cva_cva0(None, 0, None, None) == N.CVA_EINVAL
     assert L.cva_regress(None, None, 1, 0, 0, None, None, None) == N.CVA_EINVAL
+
+
+def test_python_binding_marshals_and_reports_errors(libcva):
+    """The torch-facing binding builds the C structs and surfaces a host-side
+    validation error as CvaError (no device call is reached)."""
+    from paper_2211_17005_gb300 import api, workload as W
+    from paper_2211_17005_gb300._native import CvaError, CVA_EINVAL
+    wl = W.make("paper", M=64)
+    with pytest.raises(CvaError) as ei:
+        api.Simulation(wl.model, wl.portfolios, W.Grid(10.0, 300, 1), 64, 8)
+    assert ei.value.status == CVA_EINVAL
+    with pytest.raises(CvaError):
+        api.Simulation(wl.model, wl.portfolios, wl.grid, 64, 0)
