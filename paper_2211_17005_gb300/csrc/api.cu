@@ -243,7 +243,10 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
     for (int q = 0; q < n * S; ++q)
         for (int e = 0; e < E; ++e)
             drift[(size_t)q * E + e] = (float)((hw[e].theta(q * ds) - quanto[e]) * ds);
-    std::vector<float2> zc((size_t)(n + 1) * E * Ginst, make_float2(0.f, 0.f));
+    // bond tables: for T = (g+1) delta >= t_j, (lnA(t_j, T), B(t_j, T)) and the
+    // increments from T - delta (log-ratio of consecutive bond prices is
+    // dlnA - dB r), all in FP64 before rounding
+    std::vector<float4> zc((size_t)(n + 1) * E * Ginst, make_float4(0.f, 0.f, 0.f, 0.f));
     std::vector<int> date_p(n + 1, 0);
     for (int j = 1; j <= n; ++j) date_p[j] = (j - 1) / (int)ppp;
     for (int j = 0; j <= n; ++j) {
@@ -252,7 +255,13 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
             for (int g = 0; g < Ginst; ++g) {
                 const double T = (g + 1) * delta;
                 if (T + 1e-12 < t) continue;
-                zc[((size_t)j * E + e) * Ginst + g] = make_float2((float)hw[e].lnA(t, T), (float)hw[e].B(t, T));
+                const double lnA = hw[e].lnA(t, T), B = hw[e].B(t, T);
+                double dlnA = 0.0, dB = 0.0;
+                if (T - delta + 1e-12 >= t) {
+                    dlnA = lnA - hw[e].lnA(t, T - delta);
+                    dB = B - hw[e].B(t, T - delta);
+                }
+                zc[((size_t)j * E + e) * Ginst + g] = make_float4((float)lnA, (float)B, (float)dlnA, (float)dB);
             }
     }
     const int n_periods = n / (int)ppp + 1;
@@ -308,7 +317,7 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
     TRY_ALLOC(s->d_targets, (size_t)n_pf * n * Mz);
     if (flags & CVA_KEEP_DEFAULTS) TRY_ALLOC(s->d_idx, Mz * N * C);
 #undef TRY_ALLOC
-    cudaError_t e1 = cudaMemcpy(s->d_zc, zc.data(), zc.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    cudaError_t e1 = cudaMemcpy(s->d_zc, zc.data(), zc.size() * sizeof(float4), cudaMemcpyHostToDevice);
     cudaError_t e2 = cudaMemcpy(s->d_fix, fix.data(), fix.size() * sizeof(float2), cudaMemcpyHostToDevice);
     cudaError_t e3 = cudaMemcpy(s->d_date_p, date_p.data(), date_p.size() * sizeof(int), cudaMemcpyHostToDevice);
     cudaError_t e4 = cudaMemcpy(s->d_drift, drift.data(), drift.size() * sizeof(float), cudaMemcpyHostToDevice);

@@ -69,7 +69,7 @@ struct Sim {
     SimWeights weights;
     std::vector<double> recovery;
     // device tables
-    float2 *d_zc = nullptr;        // [n+1][E][Ginst]  (lnA, B)
+    float4 *d_zc = nullptr;        // [n+1][E][Ginst]  (lnA, B, dlnA, dB) of ZC_{t_j}((g+1) delta)
     float2 *d_fix = nullptr;       // [n_periods+1][E] (lnA, B) of ZC_{p delta}((p+1) delta)
     int *d_date_p = nullptr;       // [n+1] period index of t_j
     float *d_drift = nullptr;      // [n*S][E] (theta_e(t_q) - quanto_e) * ds
