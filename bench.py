@@ -39,6 +39,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--paths", type=int, default=None,
+                   help="override the number of outer paths (small cases for profiling captures)")
     return p.parse_args()
 
 
@@ -217,7 +219,7 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     build.build()
-    wl = workload.make(args.workload)
+    wl = workload.make(args.workload, M=args.paths)
     basis = "poly2" if wl.name == "small" else "linear"
     k0 = rank * wl.M          # weak scaling: each rank owns its own outer paths
     sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N, profile=True)

@@ -161,13 +161,8 @@ __global__ void __launch_bounds__(128) outer_kernel(OuterArgs a)
             // ln ZC_t(g delta). D[h] = ZC_t(h delta) - ZC_t((h+1) delta) = -Z[h-1] expm1(x_h)
             // keeps full relative accuracy of each bond-price difference; D[p] carries the
             // running floating coupon ZC_t(t_+) (1/ZC_{t_-}(t_+) - 1).
-            float lnz_first = 0.f;
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const float4 t4 = __ldg(tab + g);
-                if (g == p) lnz_first = fmaf(-t4.y, re, t4.x);
-            }
-            const float z_first = expf(lnz_first);
+            const float4 tp = __ldg(tab + (p < G ? p : G - 1));   // p >= G: every swap has matured
+            const float z_first = expf(fmaf(-tp.y, re, tp.x));
             float Z[G], D[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
