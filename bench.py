@@ -58,27 +58,36 @@ def alu_peak_lane_instr_per_s(sm_mhz):
     return 152 * 4 * 32 * sm_mhz * 1e6
 
 
-def outer_instr_per_path_step(wl):
-    """Algorithmic lane-instructions of the outer-path kernel per (path, pricing step),
-    counted from the method (not from the compiled code):
-      per Euler sub-step: Philox4x32-10 = 10 rounds x 8 integer ops + 4 counter ops per
-      block of four draws, 4 ops per uniform, 20 per Box-Muller pair, F(F+1)/2 FMA for
-      the correlation, 4 per rate and FX factor, 8 per CIR intensity, 4 per
-      integrated intensity (compensated sum), 1 for the FP64 discount integral;
-      per pricing date: 7 per (economy, reset date) for the bond prices, (2G+1) per
-      (portfolio, counterparty, economy) for the date-bucketed MtM, 12 per counterparty
-      (threshold) and 3 per (portfolio, counterparty) for the exposure."""
+def _shape(wl):
     m = wl.model
-    E, C = m.E, m.C
     CS = int(np.count_nonzero(m.cir_nu > 0))
-    F = 2 * E - 1 + CS
+    F = 2 * m.E - 1 + CS
     G = 10 if wl.name != "small" else 5
-    NPF = len(wl.portfolios)
-    S = wl.grid.substeps
+    return m.E, m.C, CS, F, G, len(wl.portfolios), wl.grid.substeps
+
+
+def sim_instr_per_path_step(wl):
+    """Algorithmic lane-instructions of the path-simulation kernel per (path, pricing
+    step), counted from the method (not from the compiled code): per Euler sub-step,
+    Philox4x32-10 = 10 rounds x 8 integer ops + 4 counter ops per block of four draws,
+    4 ops per uniform, 20 per Box-Muller pair, F(F+1)/2 FMA for the correlation, 4 per
+    rate and FX factor, 8 per CIR intensity, 5 per integrated intensity (compensated,
+    non-decreasing sum), 1 for the FP64 discount integral; per pricing date 12 per
+    counterparty for the threshold 1 - exp(-Lambda)."""
+    E, C, CS, F, G, NPF, S = _shape(wl)
     blocks = (F + 3) // 4
-    sub = blocks * (84 + 16 + 40) + F * (F + 1) // 2 + 4 * E + 4 * (E - 1) + 8 * CS + 4 * C + 1
-    date = 7 * E * G + NPF * C * E * (2 * G + 1) + 12 * C + 3 * NPF * C
-    return S * sub + date
+    sub = blocks * (84 + 16 + 40) + F * (F + 1) // 2 + 4 * E + 4 * (E - 1) + 8 * CS + 5 * C + 1
+    return S * sub + 12 * C
+
+
+def price_instr_per_path_date(wl):
+    """Algorithmic lane-instructions of the pricing kernel per (path, pricing date):
+    20 per economy for the first live bond and the running fixing, 12 per (economy,
+    reset date) for the chained bond prices and their differences (degree-8 series),
+    (2G+1) per (portfolio, counterparty, economy) for the date-bucketed MtM, 3 per
+    (portfolio, counterparty) for the exposure and 6 for the discount factor."""
+    E, C, CS, F, G, NPF, S = _shape(wl)
+    return 20 * E + 12 * E * G + NPF * C * E * (2 * G + 1) + 3 * NPF * C + 6
 
 
 def inner_bytes_per_path(wl):
@@ -241,7 +250,7 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    outer_ms, inner_ms, reg_ev = [], [], []
+    sim_ms, price_ms, inner_ms, reg_ev = [], [], [], []
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
@@ -249,8 +258,9 @@ def main():
         start.record(stream)
         for s in range(args.steps):
             c0, evs, _ = step(s + 1)
-            o_ms, i_ms = sim.kernel_ms()
-            outer_ms.append(o_ms)
+            a_ms, p_ms, i_ms = sim.kernel_ms()
+            sim_ms.append(a_ms)
+            price_ms.append(p_ms)
             inner_ms.append(i_ms)
             reg_ev.append(evs)
         end.record(stream)
@@ -287,19 +297,23 @@ def main():
     d2h = 4 * n * wl.M + 16
     e2e_value = units_per_step / e2e_s
 
-    # ---- roofline of the dominant kernel (the outer-path kernel) ----
+    # ---- roofline of the dominant kernel ----
     pk, src = peaks()
-    o_avg = float(np.mean(outer_ms))
-    i_avg = float(np.mean(inner_ms))
+    s_avg, p_avg, i_avg = float(np.mean(sim_ms)), float(np.mean(price_ms)), float(np.mean(inner_ms))
     clk = clocks.summary()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     peak_alu = alu_peak_lane_instr_per_s(sm_mhz)
-    instr = outer_instr_per_path_step(wl) * wl.M * n
-    achieved = instr / (o_avg / 1e3)
-    roof = {"bound": "alu", "kernel": "outer_kernel", "achieved": achieved / 1e12, "peak": peak_alu / 1e12,
-            "unit": "T lane-instr/s", "frac": achieved / peak_alu, "traffic": None,
-            "peak_source": f"152 SMs x 128 lanes x {sm_mhz:g} MHz ({src} max SM clock)",
-            "algorithmic_instr_per_path_step": outer_instr_per_path_step(wl)}
+    kern = {"sim_kernel": (sim_instr_per_path_step(wl), s_avg, "path-step"),
+            "price_kernel": (price_instr_per_path_date(wl), p_avg, "path-date")}
+    alu = {}
+    for name, (per_unit, ms, unit) in kern.items():
+        ach = per_unit * wl.M * n / (ms / 1e3)
+        alu[name] = {"bound": "alu", "kernel": name, "achieved": ach / 1e12, "peak": peak_alu / 1e12,
+                     "unit": "T lane-instr/s", "frac": ach / peak_alu, "traffic": None,
+                     "algorithmic_instr_per_unit": per_unit, "unit_of_work": unit, "ms": ms}
+    dom = max(alu, key=lambda k: alu[k]["ms"])
+    roof = dict(alu[dom])
+    roof["peak_source"] = f"152 SMs x 128 lanes x {sm_mhz:g} MHz ({src} max SM clock)"
     hbm = pk.get("hbm_gbs", 6800.0)
     inner_gbs = inner_bytes_per_path(wl) * wl.M / (i_avg / 1e3) / 1e9
     reg_bytes = 4 * (n - 1) * wl.M * (wl.model.F + 1 + 1)
@@ -319,16 +333,17 @@ def main():
                "config": {"workload": describe(wl), "regression": f"least squares, basis {basis}",
                           "seed_per_step": "1..K", "l2": "working set > L2: 2.3 GB written per step",
                           "parallelism": f"{world} rank(s), disjoint outer-path ranges"},
-               "sim_ms": o_avg + i_avg, "outer_kernel_ms": o_avg, "inner_kernel_ms": i_avg,
-               "regression_ms": float(np.mean(reg_ms)),
-               "sim_throughput": wl.M * wl.N * n / ((o_avg + i_avg) / 1e3),
+               "sim_ms": s_avg + p_avg + i_avg, "sim_kernel_ms": s_avg, "price_kernel_ms": p_avg,
+               "inner_kernel_ms": i_avg, "regression_ms": float(np.mean(reg_ms)),
+               "sim_throughput": wl.M * wl.N * n / ((s_avg + p_avg + i_avg) / 1e3),
+               "alu_kernels": alu,
                "regression_samples_per_s": wl.M * (n - 1) / (np.mean(reg_ms) / 1e3),
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
-               "gpu_launches": 7 * args.steps}
+               "gpu_launches": 8 * args.steps}
         print(json.dumps(out))
     sim.close()
     if world > 1:

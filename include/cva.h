@@ -112,7 +112,8 @@ CVA_API cva_status cva_sim_create(const cva_model_desc *model, const cva_portfol
 /* Run the hierarchical simulation for global outer paths [k0, k0 + M) with the
  * Philox4x32-10 key `seed` (counters keyed by global path, step and inner
  * index, so a path range gives the same paths as a full run). Enqueues the
- * outer-path kernel (factors, MtM, exposures, features) and the inner-default
+ * path-simulation kernel (factors, integrals, thresholds, features), the
+ * pricing kernel (MtM and exposures per path and date) and the inner-default
  * kernel (default steps, averaged targets) on `stream`. */
 CVA_API cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *stream);
 
@@ -137,9 +138,10 @@ CVA_API cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *
 CVA_API cva_status cva_sim_view(const cva_sim *sim, int what, void **dev_ptr, size_t *bytes);
 
 /* Device durations (milliseconds, CUDA events on the launching stream) of the
- * last cva_simulate of a sim created with CVA_PROFILE: out_ms[0] = outer-path
- * kernel, out_ms[1] = inner-default kernel. Waits for those events. */
-CVA_API cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[2]);
+ * last cva_simulate of a sim created with CVA_PROFILE: out_ms[0] = path
+ * simulation kernel, out_ms[1] = pricing kernel (MtM and exposures),
+ * out_ms[2] = inner-default kernel. Waits for those events. */
+CVA_API cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[3]);
 
 /* Shape of a simulation: out[0..5] = M, N, n_steps, F, C, n_pf. */
 CVA_API cva_status cva_sim_shape(const cva_sim *sim, int64_t out[6]);

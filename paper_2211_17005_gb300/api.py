@@ -97,11 +97,11 @@ class Simulation:
         nat.check(N_lib().cva_simulate(self._h, int(seed), int(k0), _stream_handle(stream)), "cva_simulate")
         return self
 
-    def kernel_ms(self) -> Tuple[float, float]:
-        """(outer-path kernel, inner-default kernel) device milliseconds of the last run."""
-        out = (ctypes.c_float * 2)()
+    def kernel_ms(self) -> Tuple[float, float, float]:
+        """(path simulation, pricing, inner defaults) device milliseconds of the last run."""
+        out = (ctypes.c_float * 3)()
         nat.check(N_lib().cva_sim_kernel_ms(self._h, out), "cva_sim_kernel_ms")
-        return float(out[0]), float(out[1])
+        return float(out[0]), float(out[1]), float(out[2])
 
     def _view(self, what: int, shape, typestr=_F32) -> torch.Tensor:
         p = ctypes.c_void_p()

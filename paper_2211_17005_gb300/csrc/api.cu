@@ -343,23 +343,24 @@ cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *stream)
     if (k0 + s.M > 0xffffffffull) return fail(CVA_EINVAL, "k0 + M must fit in 32 bits");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (s.ev[0]) CVA_CUDA_TRY(cudaEventRecord(s.ev[0], st));
-    cva_status r = launch_outer(s, seed, k0, st);
-    if (r != CVA_OK) return r;
-    if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
-    r = launch_inner(s, seed, k0, st);
+    cva_status r = launch_outer(s, seed, k0, st);   // records ev[1] between its two kernels
     if (r != CVA_OK) return r;
     if (s.ev[2]) CVA_CUDA_TRY(cudaEventRecord(s.ev[2], st));
+    r = launch_inner(s, seed, k0, st);
+    if (r != CVA_OK) return r;
+    if (s.ev[3]) CVA_CUDA_TRY(cudaEventRecord(s.ev[3], st));
     return CVA_OK;
 }
 
-cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[2])
+cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[3])
 {
     if (!sim || !out_ms) return fail(CVA_EINVAL, "NULL argument");
     const Sim &s = *reinterpret_cast<const Sim *>(sim);
     if (!s.ev[0]) return fail(CVA_EINVAL, "sim was not created with CVA_PROFILE");
-    CVA_CUDA_TRY(cudaEventSynchronize(s.ev[2]));
+    CVA_CUDA_TRY(cudaEventSynchronize(s.ev[3]));
     CVA_CUDA_TRY(cudaEventElapsedTime(&out_ms[0], s.ev[0], s.ev[1]));
     CVA_CUDA_TRY(cudaEventElapsedTime(&out_ms[1], s.ev[1], s.ev[2]));
+    CVA_CUDA_TRY(cudaEventElapsedTime(&out_ms[2], s.ev[2], s.ev[3]));
     return CVA_OK;
 }
 

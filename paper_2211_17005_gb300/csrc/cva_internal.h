@@ -81,8 +81,9 @@ struct Sim {
     float *d_mtm = nullptr;        // [NPF][n+1][C][M] (optional)
     float *d_targets = nullptr;    // [NPF][n][M]
     uint8_t *d_idx = nullptr;      // [M][N][C] (optional)
-    // profiling events: before outer, between, after inner
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // profiling events: before the simulation kernel, after it, after the pricing
+    // kernel, after the inner-default kernel
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // One compiled shape of the outer-path kernel (outer_*.cu).

@@ -1,17 +1,23 @@
-// Outer-path kernel of the hierarchical CVA simulation (one thread per outer
-// path k, Sec. 3.2), templated on the model shape. Each translation unit that
-// includes this header gets its own copy of the constant-memory tables and of
-// their ownership state, so instantiations compile in parallel.
+// Outer-path kernels of the hierarchical CVA simulation, templated on the model
+// shape. Each translation unit that includes this header gets its own copy of
+// the constant-memory tables and of their ownership state, so instantiations
+// compile in parallel.
 //
-// Per Euler sub-step (Remark rem:finecoarse): Philox normals, correlation by the
-// Cholesky factor, Hull-White rates with the quanto drift, lognormal FX, CIR
-// intensities with full truncation (App. B), and the left-point integrals
-// int r^0 (FP64) and Lambda^c (compensated FP32). At each pricing date: bond
-// prices ZC_t(g delta) of every live reset date, the portfolio MtM per
-// counterparty from the App. B swap formula regrouped by (counterparty,
-// currency, reset date), the exposure (1-R_c) beta_j MtM^+ and the threshold
-// 1 - exp(-Lambda_c(t_j)). Outputs are structure-of-arrays with the path index
-// fastest.
+// sim_kernel (one thread per outer path k, Sec. 3.2): the time loop. Per
+// Euler-Maruyama sub-step (Remark rem:finecoarse): Philox normals, correlation
+// by the Cholesky factor, Hull-White rates with the quanto drift, lognormal FX,
+// CIR intensities with full truncation (App. B), and the left-point integrals
+// int r^0 (FP64) and Lambda^c (compensated FP32). At each pricing date it
+// stores the state Y_j, int r^0 and the threshold 1 - exp(-Lambda_c(t_j)).
+//
+// price_kernel (one thread per outer path and pricing date): the portfolio MtM
+// per counterparty from the App. B swap formula, regrouped exactly by
+// (counterparty, currency, reset date), and the exposure (1-R_c) beta_j MtM^+.
+// It reads the state of date j and the short rates of the last reset date
+// (Remark rem:pathdep) from the stored states; every (path, date) is
+// independent, so the pricing runs at full occupancy.
+//
+// Outputs are structure-of-arrays with the path index fastest.
 #pragma once
 #include <mutex>
 
@@ -49,8 +55,8 @@ struct OuterArgs {
     float *features, *disc, *thr, *expo, *mtm;
 };
 
-template <int E, int C, int CS, int G, int NPF>
-__global__ void __launch_bounds__(128) outer_kernel(OuterArgs a)
+template <int E, int C, int CS>
+__global__ void __launch_bounds__(128) sim_kernel(OuterArgs a)
 {
     constexpr int F = 2 * E - 1 + CS;
     constexpr int NB = (F + 3) / 4;
@@ -58,68 +64,63 @@ __global__ void __launch_bounds__(128) outer_kernel(OuterArgs a)
     if (kl >= a.M) return;
     const uint32_t k = a.k0 + kl;
     const size_t M = a.M;
-    const int n = c_sim.n, S = c_sim.S, ppp = c_sim.ppp;
+    const int n = c_sim.n, S = c_sim.S;
     const float ds = c_sim.ds;
-    const double ds_d = (double)c_sim.ds_d;
+    const double ds_d = c_sim.ds_d;
 
-    float r[E], lchi[E], fixm1[E];
-    float gam[C], lam[C], lamc[C], thr_prev[C];
+    float r[E], lchi[E];
+    float gam[C], lam[C], lamc[C];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         r[e] = c_sim.r0[e];
         lchi[e] = c_sim.lchi0[e];
-        fixm1[e] = c_sim.fix0_m1[e];
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         gam[c] = c_sim.gamma0[c];
         lam[c] = 0.f;
         lamc[c] = 0.f;
-        thr_prev[c] = 0.f;
     }
     double I0 = 0.0;
 
     // date 0
-    {
 #pragma unroll
-        for (int e = 0; e < E; ++e) a.features[(size_t)e * M + kl] = r[e];
+    for (int e = 0; e < E; ++e) a.features[(size_t)e * M + kl] = r[e];
 #pragma unroll
-        for (int e = 1; e < E; ++e) a.features[(size_t)(E - 1 + e) * M + kl] = lchi[e];
+    for (int e = 1; e < E; ++e) a.features[(size_t)(E - 1 + e) * M + kl] = lchi[e];
 #pragma unroll
-        for (int c = 0; c < CS; ++c) a.features[(size_t)(2 * E - 1 + c) * M + kl] = gam[c];
-        a.disc[kl] = 0.f;
+    for (int c = 0; c < CS; ++c) a.features[(size_t)(2 * E - 1 + c) * M + kl] = gam[c];
+    a.disc[kl] = 0.f;
 #pragma unroll
-        for (int c = 0; c < C; ++c) a.thr[(size_t)c * M + kl] = 0.f;
-#pragma unroll
-        for (int pf = 0; pf < NPF; ++pf)
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                a.expo[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
-                if (a.mtm) a.mtm[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
-            }
-    }
+    for (int c = 0; c < C; ++c) a.thr[(size_t)c * M + kl] = 0.f;
 
     for (int j = 1; j <= n; ++j) {
         for (int s = 0; s < S; ++s) {
             const uint32_t q = (uint32_t)((j - 1) * S + s);
-            float z[4 * NB];
+            // correlated increments W = L z, accumulated one Philox block (four
+            // normals) at a time
+            float W[F];
+#pragma unroll
+            for (int i = 0; i < F; ++i) W[i] = 0.f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const uint4 x = philox4x32_10(make_uint4(k, q, 0u, (kStreamOuter << 24) | (uint32_t)b),
                                               a.seed_lo, a.seed_hi);
-                box_muller(x.x, x.y, z[4 * b], z[4 * b + 1]);
-                box_muller(x.z, x.w, z[4 * b + 2], z[4 * b + 3]);
-            }
-            float W[F];
+                float z[4];
+                box_muller(x.x, x.y, z[0], z[1]);
+                box_muller(x.z, x.w, z[2], z[3]);
 #pragma unroll
-            for (int i = 0; i < F; ++i) {
-                float acc = 0.f;
+                for (int t = 0; t < 4; ++t) {
+                    const int col = 4 * b + t;
+                    if (col < F) {
 #pragma unroll
-                for (int b = 0; b <= i; ++b) acc = fmaf(c_sim.L[i * (i + 1) / 2 + b], z[b], acc);
-                W[i] = acc;
+                        for (int i = col; i < F; ++i) W[i] = fmaf(c_sim.L[i * (i + 1) / 2 + col], z[t], W[i]);
+                    }
+                }
             }
             const float r0 = r[0];
-            // left-point integrals: int r^0 in FP64, Lambda^c compensated FP32
+            // left-point integrals: int r^0 in FP64, Lambda^c compensated FP32 and
+            // kept non-decreasing
             I0 = fma((double)r0, ds_d, I0);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(128) outer_kernel(OuterArgs a)
                 const float y = fmaf(gp, ds, -lamc[c]);
                 const float t = lam[c] + y;
                 lamc[c] = (t - lam[c]) - y;
-                lam[c] = t;
+                lam[c] = fmaxf(t, lam[c]);
                 if (c < CS) {
                     constexpr int w0 = (CS > 0) ? 2 * E - 1 : 0;
                     gam[c] += c_sim.cir_ktds[c] - c_sim.cir_kds[c] * gp
@@ -143,66 +144,6 @@ __global__ void __launch_bounds__(128) outer_kernel(OuterArgs a)
                 r[e] += (__ldg(drow + e) - c_sim.hw_a_ds[e] * r[e]) + c_sim.hw_sig_sqds[e] * W[e];
         }
 
-        // ---- pricing date t_j ----
-        const float I0f = (float)I0;
-        const float beta = expf(-I0f);
-        const int p = __ldg(a.date_p + j);
-        float mt[NPF][C];
-#pragma unroll
-        for (int pf = 0; pf < NPF; ++pf)
-#pragma unroll
-            for (int c = 0; c < C; ++c) mt[pf][c] = 0.f;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float re = r[e];
-            const float4 *tab = a.zc + ((size_t)j * E + e) * G;
-            // Z[g] = ZC_t((g+1) delta) for live reset dates (g >= p), chained from the
-            // first one: Z[g] = Z[g-1] (1 + expm1(x_g)), x_g = ln ZC_t((g+1) delta) -
-            // ln ZC_t(g delta). D[h] = ZC_t(h delta) - ZC_t((h+1) delta) = -Z[h-1] expm1(x_h)
-            // keeps full relative accuracy of each bond-price difference; D[p] carries the
-            // running floating coupon ZC_t(t_+) (1/ZC_{t_-}(t_+) - 1).
-            const float4 tp = __ldg(tab + (p < G ? p : G - 1));   // p >= G: every swap has matured
-            const float z_first = expf(fmaf(-tp.y, re, tp.x));
-            float Z[G], D[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const float4 t4 = __ldg(tab + g);
-                if (g < p) {
-                    Z[g] = 0.f;
-                    D[g] = 0.f;
-                } else if (g == p) {
-                    Z[g] = z_first;
-                    D[g] = z_first * fixm1[e];
-                } else {
-                    const float zp = Z[g > 0 ? g - 1 : 0];
-                    const float em = expm1_small(fmaf(-t4.w, re, t4.z));
-                    D[g] = -zp * em;
-                    Z[g] = fmaf(zp, em, zp);
-                }
-            }
-            const float chi = (e == 0) ? 1.f : expf(lchi[e]);
-#pragma unroll
-            for (int pf = 0; pf < NPF; ++pf)
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const int base = ((pf * C + c) * E + e) * G;
-                    float acc = 0.f;
-#pragma unroll
-                    for (int h = 0; h < G; ++h) acc = fmaf(c_w.wA[base + h], D[h], acc);
-#pragma unroll
-                    for (int g = 0; g < G; ++g) acc = fmaf(-c_w.wK[base + g], Z[g], acc);
-                    mt[pf][c] = fmaf(chi, acc, mt[pf][c]);
-                }
-        }
-        if (j % ppp == 0) {   // reset date: fix the next floating coupon at today's rate
-            const float2 *fx = a.fix + (size_t)(j / ppp) * E;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const float2 f2 = __ldg(fx + e);
-                fixm1[e] = expm1f(fmaf(f2.y, r[e], -f2.x));
-            }
-        }
-
         float *fe = a.features + (size_t)j * F * M + kl;
 #pragma unroll
         for (int e = 0; e < E; ++e) fe[(size_t)e * M] = r[e];
@@ -210,24 +151,96 @@ __global__ void __launch_bounds__(128) outer_kernel(OuterArgs a)
         for (int e = 1; e < E; ++e) fe[(size_t)(E - 1 + e) * M] = lchi[e];
 #pragma unroll
         for (int c = 0; c < CS; ++c) fe[(size_t)(2 * E - 1 + c) * M] = gam[c];
-        a.disc[(size_t)j * M + kl] = I0f;
+        a.disc[(size_t)j * M + kl] = (float)I0;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const float T = fmaxf(-expm1f(-lam[c]), thr_prev[c]);
-            thr_prev[c] = T;
-            a.thr[((size_t)j * C + c) * M + kl] = T;
-        }
+        for (int c = 0; c < C; ++c) a.thr[((size_t)j * C + c) * M + kl] = -expm1f(-lam[c]);
+    }
+}
+
+template <int E, int C, int CS, int G, int NPF>
+__global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
+{
+    constexpr int F = 2 * E - 1 + CS;
+    const uint32_t kl = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (kl >= a.M) return;
+    const size_t M = a.M;
+    const int n = c_sim.n, ppp = c_sim.ppp;
+    if (j == 0) {   // no default at t_0: exposures of date 0 are never used
 #pragma unroll
         for (int pf = 0; pf < NPF; ++pf)
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const size_t o = ((size_t)(pf * (n + 1) + j) * C + c) * M + kl;
-                a.expo[o] = c_sim.lgd[c] * beta * fmaxf(mt[pf][c], 0.f);
-                if (a.mtm) a.mtm[o] = mt[pf][c];
+                a.expo[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
+                if (a.mtm) a.mtm[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
+            }
+        return;
+    }
+    const int p = __ldg(a.date_p + j);          // t_j in (p delta, (p+1) delta]
+    const float *fe = a.features + (size_t)j * F * M + kl;
+    const float *ffix = a.features + (size_t)(p * ppp) * F * M + kl;   // state at the last reset
+    const float2 *fx = a.fix + (size_t)p * E;
+    const float beta = expf(-__ldg(a.disc + (size_t)j * M + kl));
+
+    float mt[NPF][C];
+#pragma unroll
+    for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+        for (int c = 0; c < C; ++c) mt[pf][c] = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const float re = __ldg(fe + (size_t)e * M);
+        // running floating coupon fixed at t_- = p delta: 1/ZC_{t_-}(t_+) - 1
+        const float2 f2 = __ldg(fx + e);
+        const float fixm1 = expm1f(fmaf(f2.y, __ldg(ffix + (size_t)e * M), -f2.x));
+        const float4 *tab = a.zc + ((size_t)j * E + e) * G;
+        // Z[g] = ZC_t((g+1) delta) for live reset dates (g >= p), chained from the
+        // first one: Z[g] = Z[g-1] (1 + expm1(x_g)), x_g = ln ZC_t((g+1) delta) -
+        // ln ZC_t(g delta). D[h] = ZC_t(h delta) - ZC_t((h+1) delta) = -Z[h-1] expm1(x_h)
+        // keeps full relative accuracy of each bond-price difference; D[p] carries the
+        // running floating coupon ZC_t(t_+) (1/ZC_{t_-}(t_+) - 1).
+        const float4 tp = __ldg(tab + (p < G ? p : G - 1));   // p >= G: every swap has matured
+        const float z_first = expf(fmaf(-tp.y, re, tp.x));
+        float Z[G], D[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (g < p) {
+                Z[g] = 0.f;
+                D[g] = 0.f;
+            } else if (g == p) {
+                Z[g] = z_first;
+                D[g] = z_first * fixm1;
+            } else {
+                const float4 t4 = __ldg(tab + g);
+                const float zp = Z[g > 0 ? g - 1 : 0];
+                const float em = expm1_small(fmaf(-t4.w, re, t4.z));
+                D[g] = -zp * em;
+                Z[g] = fmaf(zp, em, zp);
+            }
+        }
+        const float chi = (e == 0) ? 1.f : expf(__ldg(fe + (size_t)(E - 1 + (e > 0 ? e : 1)) * M));
+#pragma unroll
+        for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int base = ((pf * C + c) * E + e) * G;
+                float acc = 0.f;
+#pragma unroll
+                for (int h = 0; h < G; ++h) acc = fmaf(c_w.wA[base + h], D[h], acc);
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc = fmaf(-c_w.wK[base + g], Z[g], acc);
+                mt[pf][c] = fmaf(chi, acc, mt[pf][c]);
             }
     }
+#pragma unroll
+    for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const size_t o = ((size_t)(pf * (n + 1) + j) * C + c) * M + kl;
+            a.expo[o] = c_sim.lgd[c] * beta * fmaxf(mt[pf][c], 0.f);
+            if (a.mtm) a.mtm[o] = mt[pf][c];
+        }
 }
-
 
 // Constant-memory ownership of this translation unit: a launch for another
 // simulation re-uploads the tables, and every launch first waits for the
@@ -271,8 +284,10 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
         CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_w, &s.weights, sizeof(SimWeights), 0, cudaMemcpyHostToDevice, st));
         t_owner[dev] = &s;
     }
-    const unsigned blocks = (args.M + 127u) / 128u;
-    outer_kernel<E, C, CS, G, NPF><<<blocks, 128, 0, st>>>(args);
+    sim_kernel<E, C, CS><<<(args.M + 127u) / 128u, 128, 0, st>>>(args);
+    CVA_CUDA_TRY(cudaGetLastError());
+    if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
+    price_kernel<E, C, CS, G, NPF><<<dim3((args.M + 255u) / 256u, (unsigned)s.n + 1u), 256, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
     return CVA_OK;

@@ -196,3 +196,17 @@ def single_swap_model(gammas=(0.02, 0.05), recovery=0.4) -> Model:
     m.cir_nu = np.zeros(m.C)
     m.recovery = np.full(m.C, recovery)
     return m
+
+
+def mlp_init(d: int, u: int, seed: int = GENERATOR_SEED + 7):
+    """Initial parameters of the NN+ regressor (two hidden layers of width u on d
+    inputs): weights and biases U(-1/sqrt(fan_in), 1/sqrt(fan_in)), mu = 0. They are
+    an input of the training, shared by the CUDA path and the oracle."""
+    rng = np.random.default_rng(seed)
+
+    def unif(fan_in, *shape):
+        b = 1.0 / np.sqrt(fan_in)
+        return rng.uniform(-b, b, size=shape)
+
+    return {"W1": unif(d, u, d), "b1": unif(d, u), "W2": unif(u, u, u), "b2": unif(u, u),
+            "w3": unif(u, u), "b3": np.array(unif(u, 1)[0]), "mu": np.array(0.0)}
