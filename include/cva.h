@@ -178,6 +178,33 @@ CVA_API cva_status cva_regress(const float *targets_dev, const float *features_d
 CVA_API cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float *pred_dev,
                            double *coef_host, void *stream);
 
+/* The paper has no counterpart for this entry point; it serves callers that
+ * cannot allocate device memory when they need a fit: a framework that owns the
+ * whole device through its own pool, a process held to a fixed memory budget
+ * checked at start-up, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * It fits `groups` independent least-squares problems exactly like cva_regress
+ * (same bases, same FP64 normal equations and Cholesky solve), group g reading
+ * targets_dev + g*M (float [M]) and features_dev + g*F*M (float [F][M]) and
+ * writing pred_dev + g*M (float [M], nullable) and coef_host + g*m (double,
+ * nullable; m = F+1 linear, 3 poly2).
+ *
+ * It allocates nothing: its scratch (Gram partials, coefficients, status) is a
+ * static 1 MiB device array inside the library, present on every device that
+ * loads the library until the process exits. That array bounds the batch: a
+ * call with more groups than fit (about 200 for the linear basis with F = 27,
+ * 1024 at most) returns CVA_EINVAL with the limit in cva_last_error(). The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; later calls reuse it. Every call shares
+ * the array and leaves its contents behind; each call writes what it reads, so
+ * nothing needs clearing, but calls whose kernels overlap on the GPU (e.g. on two
+ * streams) race on the array and must be ordered by the caller. Synchronises
+ * `stream` when coef_host is not NULL. */
+CVA_API cva_status cva_regress_batched_static(const float *targets_dev, const float *features_dev,
+                                              int groups, int F, uint64_t M, int basis,
+                                              float *pred_dev, double *coef_host, void *stream);
+
 /* The counter-based generator the kernels draw from: Philox4x32-10 (Salmon,
  * Moraes, Dror, Shaw, SC'11) with key (seed low 32 bits, seed high 32 bits).
  * For i < n: out_dev[4i..4i+3] = Philox4x32-10(ctr_dev[4i..4i+3], key). Both

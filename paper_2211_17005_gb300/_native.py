@@ -57,6 +57,9 @@ SIGNATURES = {
                                    ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_void_p]),
     "cva_regress_all": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp,
                                        ctypes.c_void_p]),
+    "cva_regress_batched_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, _dp,
+                                                  ctypes.c_void_p]),
     "cva_philox4x32_10": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_void_p]),
     "cva_last_error": (ctypes.c_char_p, []),

@@ -430,6 +430,13 @@ cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float *pred_de
                                coef_host ? coef_host + m : nullptr, reinterpret_cast<cudaStream_t>(stream));
 }
 
+cva_status cva_regress_batched_static(const float *targets_dev, const float *features_dev, int groups, int F,
+                                      uint64_t M, int basis, float *pred_dev, double *coef_host, void *stream)
+{
+    return lsq_batched_static(targets_dev, features_dev, groups, F, M, basis, pred_dev, coef_host,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
 cva_status cva_philox4x32_10(const uint32_t *ctr_dev, uint32_t *out_dev, uint64_t n, uint64_t seed,
                              void *stream)
 {

@@ -105,6 +105,10 @@ cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const flo
                                size_t targ_stride, float *pred0, size_t pred_stride, int F,
                                uint64_t M, int basis, int groups, double *coef_host, cudaStream_t st);
 
+// The same regression for `groups` dates, scratch in a static device array (lsq.cu).
+cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups, int F, uint64_t M,
+                              int basis, float *pred0, double *coef_host, cudaStream_t st);
+
 // CVA_0 reduction (reduce.cu).
 cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);
 cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st);

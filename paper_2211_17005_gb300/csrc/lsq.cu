@@ -341,4 +341,122 @@ cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const flo
     return CVA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Regression without any device allocation.
+//
+// Some callers cannot allocate device memory at the time they need a fit: a
+// framework may own the whole device through its own pool, a process may run
+// under a fixed memory budget checked at start-up, or a latency-critical loop
+// cannot afford the device-wide synchronisation of cudaMalloc/cudaFree. For
+// them, the batched regression below keeps its Gram partials, coefficients and
+// status words in this file-scope array instead of library-allocated scratch.
+// The array lives on every device that loads the library until the process
+// exits. Its size bounds the number of groups per call (see the check below).
+// All calls share it: each call writes every entry it later reads, so nothing
+// has to start at zero, but two calls whose kernels overlap on the GPU (for
+// instance on two streams) race on it and must be ordered by the caller.
+constexpr size_t kStaticScratchDoubles = 1u << 17;   // 1 MiB
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+
+namespace {
+std::mutex g_static_mu;
+double *g_static_ptr[64] = {};
+}  // namespace
+
+// Device address of the static scratch on the current device. The first call on
+// a device resolves it with cudaGetSymbolAddress (the host-side name is only a
+// stand-in for the device array), later calls reuse the cached address.
+static cva_status static_scratch(double **out)
+{
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+        g_static_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return CVA_OK;
+}
+
+cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups, int F, uint64_t M,
+                              int basis, float *pred0, double *coef_host, cudaStream_t st)
+{
+    if (!feat0 || !targ0 || M == 0 || groups <= 0) return fail(CVA_EINVAL, "regress_static: bad arguments");
+    if (M > 0x7fffffffull) return fail(CVA_EINVAL, "regress_static: M too large");
+    if (basis != CVA_BASIS_LINEAR && basis != CVA_BASIS_POLY2)
+        return fail(CVA_EINVAL, "regress_static: unknown basis");
+    const int m = (basis == CVA_BASIS_POLY2) ? 3 : F + 1;
+    if (basis == CVA_BASIS_LINEAR && (F < 1 || m + 1 > 32))
+        return fail(CVA_ENOTSUP, "regress_static: linear basis supports 1 <= F <= 30");
+    if (basis == CVA_BASIS_POLY2 && F < 1) return fail(CVA_EINVAL, "regress_static: need one factor");
+    const int MP = (m + 1 <= 4) ? 4 : 32;
+    const size_t NUT = (size_t)(MP / 4) * (MP / 4 + 1) / 2;
+    const size_t per_group_fixed = 2 * (size_t)m + 1;          // coefficients (two bases) + status
+    const size_t per_chunk = NUT * 16;
+    const size_t max_groups = kStaticScratchDoubles / (per_chunk + per_group_fixed);
+    if ((size_t)groups > max_groups || groups > 1024)
+        return fail(CVA_EINVAL, "regress_static: " + std::to_string(groups) + " groups exceed the static scratch (at most " +
+                                    std::to_string(max_groups < 1024 ? max_groups : 1024) +
+                                    " groups of this basis per call)");
+    double *scratch = nullptr;
+    cva_status r = static_scratch(&scratch);
+    if (r != CVA_OK) return r;
+
+    const uint64_t max_chunks = (M + 1023) / 1024;
+    uint64_t chunks = (2432 + groups - 1) / groups;
+    const uint64_t fit = (kStaticScratchDoubles - (size_t)groups * per_group_fixed) / ((size_t)groups * per_chunk);
+    if (chunks > fit) chunks = fit;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+
+    LsqArgs a;
+    a.feat0 = feat0;
+    a.feat_stride = (size_t)F * M;
+    a.targ0 = targ0;
+    a.targ_stride = M;
+    a.pred0 = pred0;
+    a.pred_stride = M;
+    a.F = F;
+    a.m = m;
+    a.basis = basis;
+    a.chunks = (int)chunks;
+    a.M = (uint32_t)M;
+    a.rows_per_chunk = (uint32_t)((M + chunks - 1) / chunks);
+    a.part = scratch;
+    a.coef = a.part + (size_t)groups * chunks * per_chunk;
+    a.coef_raw = a.coef + (size_t)groups * m;
+    a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)groups * m);
+
+    const dim3 ggrid((unsigned)chunks, (unsigned)groups);
+    if (MP == 4) {
+        constexpr int TR = 1024;
+        lsq_gram<4, TR><<<ggrid, kGramThreads, (size_t)TR * 8 * sizeof(float), st>>>(a);
+        CVA_CUDA_TRY(cudaGetLastError());
+        lsq_solve<4><<<groups, 256, 0, st>>>(a);
+    } else {
+        constexpr int TR = 256;
+        lsq_gram<32, TR><<<ggrid, kGramThreads, (size_t)TR * 36 * sizeof(float), st>>>(a);
+        CVA_CUDA_TRY(cudaGetLastError());
+        lsq_solve<32><<<groups, 256, 0, st>>>(a);
+    }
+    CVA_CUDA_TRY(cudaGetLastError());
+    if (pred0) {
+        lsq_predict<<<dim3((unsigned)((M + 255) / 256), (unsigned)groups), 256, 0, st>>>(a);
+        CVA_CUDA_TRY(cudaGetLastError());
+    }
+    if (coef_host) {
+        int status[1024];
+        CVA_CUDA_TRY(cudaMemcpyAsync(coef_host, a.coef_raw, sizeof(double) * groups * m, cudaMemcpyDeviceToHost, st));
+        CVA_CUDA_TRY(cudaMemcpyAsync(status, a.status, sizeof(int) * groups, cudaMemcpyDeviceToHost, st));
+        CVA_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int g = 0; g < groups; ++g)
+            if (status[g] != 0) return fail(CVA_ENUMERIC, "regress_static: rank-deficient normal equations");
+    }
+    return CVA_OK;
+}
+
 }  // namespace cva
