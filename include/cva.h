@@ -178,6 +178,44 @@ CVA_API cva_status cva_regress(const float *targets_dev, const float *features_d
 CVA_API cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float *pred_dev,
                            double *coef_host, void *stream);
 
+/* Neural regression of Sec. 2 (eq. (e:regrkappo)) at one date: the NN+ network of
+ * eq. (e:nnp) with two hidden ReLU layers of width `hidden` (64 is compiled) on
+ * the F <= 32 standardised factors, trained by Algorithm 1 (BaseAlg): mini-batch
+ * Adam (beta = 0.9, 0.999, eps = 1e-8, step size lr) over n_batches contiguous
+ * path ranges for `epochs` epochs, no output ReLU for the first floor(epochs/2)
+ * epochs, then a closed-form least-squares refit of the output layer (FP64
+ * normal equations) and the output ReLU; after every epoch the full-sample loss
+ * decides whether the parameters are the best so far. GEMMs run on tcgen05 tensor
+ * cores (BF16 operands, FP32 accumulation); the rest in FP32.
+ * params_dev (device float, cva_mlp_num_params(hidden) entries) holds the
+ * initial parameters and receives the best ones; layout: W1 [hidden][32]
+ * (columns >= F zero), b1 [hidden], W2 [hidden][hidden], b2 [hidden],
+ * w3 [hidden], b3, mu. pred_dev (float [M], nullable) receives the best
+ * network's predictions, loss_dev (float [epochs], nullable) the loss after each
+ * epoch. M must be a multiple of 128 * n_batches. Synchronises `stream`.
+ * CVA_ETIMEOUT if a bounded device-side wait gave up. */
+CVA_API cva_status cva_mlp_fit(const float *targets_dev, const float *features_dev, int F, uint64_t M,
+                               int hidden, int n_batches, int epochs, float lr, float *params_dev,
+                               float *pred_dev, float *loss_dev, void *stream);
+
+/* Number of parameters of the network of cva_mlp_fit. */
+CVA_API int cva_mlp_num_params(int hidden);
+
+/* Validation hook of cva_mlp_fit: one Adam step on the first batch; grad_dev
+ * (float [cva_mlp_num_params]) receives that batch's gradient, params_dev the
+ * updated parameters. */
+CVA_API cva_status cva_mlp_first_gradient(const float *targets_dev, const float *features_dev, int F,
+                                          uint64_t M, int hidden, int n_batches, float lr,
+                                          float *params_dev, float *grad_dev, void *stream);
+
+/* Algorithm 2 (backward learning) over a simulation: dates n-1 down to 1, each
+ * fitted by cva_mlp_fit on the state and targets of portfolio pf at that date,
+ * starting from the previous date's best parameters (params_dev holds the
+ * initial parameters and receives date 1's). pred_dev: float [n][M] (row 0 and
+ * row n untouched). Synchronises `stream`. */
+CVA_API cva_status cva_mlp_regress_all(const cva_sim *sim, int pf, int hidden, int n_batches, int epochs,
+                                       float lr, float *params_dev, float *pred_dev, void *stream);
+
 /* The paper has no counterpart for this entry point; it serves callers that
  * cannot allocate device memory when they need a fit: a framework that owns the
  * whole device through its own pool, a process held to a fixed memory budget

@@ -129,3 +129,35 @@ def backward_alg(p_init, features: Sequence[np.ndarray], targets: Sequence[np.nd
         p, best = base_alg(p, Z, y, **kw)
         out[i] = (p, best, forward(p, Z, 1)[0])
     return out
+
+
+def bf16(x):
+    """Round to bfloat16 (8-bit significand), round-to-nearest-even, returned as float64."""
+    u = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def grads_bf16(p, Z, y, pos):
+    """The gradient of `grads`, with the operands of the four matrix products rounded to
+    bfloat16 where a tensor-core implementation feeds them (inputs, W1, W2, the first
+    hidden layer, dH2 and dH1); every sum and every other operation in binary64."""
+    B = Z.shape[0]
+    Zb, W1b, W2b = bf16(Z), bf16(p["W1"]), bf16(p["W2"])
+    a1 = Zb @ W1b.T + p["b1"]
+    h1 = np.maximum(a1, 0.0)
+    h1b = bf16(h1)
+    a2 = h1b @ W2b.T + p["b2"]
+    h2 = np.maximum(a2, 0.0)
+    out = h2 @ p["w3"] + p["b3"]
+    pred = (np.maximum(out, 0.0) if pos else out) + p["mu"]
+    dpred = 2.0 * (pred - y) / B
+    dout = dpred * ((out > 0).astype(np.float64) if pos else 1.0)
+    g = {"mu": np.array(dpred.sum()), "b3": np.array(dout.sum()), "w3": h2.T @ dout}
+    dh2b = bf16(np.outer(dout, p["w3"]) * (h2 > 0))
+    g["W2"] = dh2b.T @ h1b
+    g["b2"] = dh2b.sum(axis=0)
+    dh1b = bf16((dh2b @ W2b) * (h1 > 0))
+    g["W1"] = dh1b.T @ Zb
+    g["b1"] = dh1b.sum(axis=0)
+    return g

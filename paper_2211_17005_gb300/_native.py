@@ -57,6 +57,15 @@ SIGNATURES = {
                                    ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_void_p]),
     "cva_regress_all": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp,
                                        ctypes.c_void_p]),
+    "cva_mlp_fit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "cva_mlp_num_params": (ctypes.c_int, [ctypes.c_int]),
+    "cva_mlp_first_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
+    "cva_mlp_regress_all": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cva_regress_batched_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, _dp,
                                                   ctypes.c_void_p]),

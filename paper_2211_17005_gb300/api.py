@@ -190,3 +190,69 @@ def philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
     nat.check(N_lib().cva_philox4x32_10(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       ctr.numel() // 4, int(seed), _stream_handle(stream)), "cva_philox4x32_10")
     return out
+
+
+# ---------------------------------------------------------------- MLP ------
+
+MLP_IN = 32
+
+
+def mlp_num_params(hidden: int) -> int:
+    return int(N_lib().cva_mlp_num_params(hidden))
+
+
+def mlp_pack(p, hidden: int) -> torch.Tensor:
+    """Flat device parameter vector from a dict (W1 [u, d<=32], b1, W2, b2, w3, b3, mu)."""
+    W1 = np.zeros((hidden, MLP_IN))
+    W1[:, :p["W1"].shape[1]] = p["W1"]
+    flat = np.concatenate([W1.ravel(), np.ravel(p["b1"]), np.ravel(p["W2"]), np.ravel(p["b2"]),
+                           np.ravel(p["w3"]), [float(p["b3"])], [float(p["mu"])]]).astype(np.float32)
+    assert flat.size == mlp_num_params(hidden)
+    return torch.from_numpy(flat).cuda()
+
+
+def mlp_unpack(flat: torch.Tensor, hidden: int, d: int):
+    v = flat.detach().cpu().numpy().astype(np.float64)
+    u = hidden
+    o = 0
+    W1 = v[o:o + u * MLP_IN].reshape(u, MLP_IN)[:, :d]; o += u * MLP_IN
+    b1 = v[o:o + u]; o += u
+    W2 = v[o:o + u * u].reshape(u, u); o += u * u
+    b2 = v[o:o + u]; o += u
+    w3 = v[o:o + u]; o += u
+    return {"W1": W1, "b1": b1, "W2": W2, "b2": b2, "w3": w3, "b3": np.array(v[o]), "mu": np.array(v[o + 1])}
+
+
+def mlp_fit(targets: torch.Tensor, features: torch.Tensor, params: torch.Tensor, hidden: int = 64,
+            n_batches: int = 32, epochs: int = 8, lr: float = 1e-3, want_pred: bool = True, stream=None):
+    """Algorithm 1 at one date on device tensors (targets [M], features [F, M]); params is
+    updated in place to the best parameters. Returns (predictions [M] or None, losses [epochs])."""
+    F, M = features.shape
+    pred = torch.empty(M, dtype=torch.float32, device=targets.device) if want_pred else None
+    losses = torch.empty(epochs, dtype=torch.float32, device=targets.device)
+    nat.check(N_lib().cva_mlp_fit(ctypes.c_void_p(targets.data_ptr()), ctypes.c_void_p(features.data_ptr()), F, M,
+                                  hidden, n_batches, epochs, float(lr), ctypes.c_void_p(params.data_ptr()),
+                                  ctypes.c_void_p(pred.data_ptr()) if want_pred else None,
+                                  ctypes.c_void_p(losses.data_ptr()), _stream_handle(stream)), "cva_mlp_fit")
+    return pred, losses.cpu().numpy()
+
+
+def mlp_first_gradient(targets, features, params, hidden=64, n_batches=32, lr=1e-3, stream=None):
+    F, M = features.shape
+    grad = torch.empty_like(params)
+    nat.check(N_lib().cva_mlp_first_gradient(ctypes.c_void_p(targets.data_ptr()),
+                                             ctypes.c_void_p(features.data_ptr()), F, M, hidden, n_batches,
+                                             float(lr), ctypes.c_void_p(params.data_ptr()),
+                                             ctypes.c_void_p(grad.data_ptr()), _stream_handle(stream)),
+              "cva_mlp_first_gradient")
+    return grad
+
+
+def mlp_regress_all(sim: "Simulation", params: torch.Tensor, pf: int = 0, hidden: int = 64, n_batches: int = 32,
+                    epochs: int = 8, lr: float = 1e-3, stream=None) -> torch.Tensor:
+    """Algorithm 2 over every date n-1..1 of a simulation; returns predictions [n, M]."""
+    pred = torch.zeros((sim.n, sim.M), dtype=torch.float32, device=sim.device)
+    nat.check(N_lib().cva_mlp_regress_all(sim._h, pf, hidden, n_batches, epochs, float(lr),
+                                          ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(pred.data_ptr()),
+                                          _stream_handle(stream)), "cva_mlp_regress_all")
+    return pred

@@ -437,6 +437,44 @@ cva_status cva_regress_batched_static(const float *targets_dev, const float *fea
                               reinterpret_cast<cudaStream_t>(stream));
 }
 
+int cva_mlp_num_params(int hidden) { return mlp_num_params(hidden); }
+
+cva_status cva_mlp_fit(const float *targets_dev, const float *features_dev, int F, uint64_t M, int hidden,
+                       int n_batches, int epochs, float lr, float *params_dev, float *pred_dev, float *loss_dev,
+                       void *stream)
+{
+    if (!targets_dev || !features_dev || !params_dev) return fail(CVA_EINVAL, "mlp: NULL pointer");
+    return mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, epochs, lr, 0, params_dev, pred_dev,
+                          nullptr, loss_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_mlp_first_gradient(const float *targets_dev, const float *features_dev, int F, uint64_t M,
+                                  int hidden, int n_batches, float lr, float *params_dev, float *grad_dev,
+                                  void *stream)
+{
+    if (!targets_dev || !features_dev || !params_dev || !grad_dev) return fail(CVA_EINVAL, "mlp: NULL pointer");
+    return mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, 1, lr, 1, params_dev, nullptr,
+                          grad_dev, nullptr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_mlp_regress_all(const cva_sim *sim, int pf, int hidden, int n_batches, int epochs, float lr,
+                               float *params_dev, float *pred_dev, void *stream)
+{
+    if (!sim || !params_dev) return fail(CVA_EINVAL, "mlp: NULL pointer");
+    const Sim &s = *reinterpret_cast<const Sim *>(sim);
+    if (pf < 0 || pf >= s.NPF) return fail(CVA_EINVAL, "portfolio index out of range");
+    const size_t M = s.M;
+    for (int i = s.n - 1; i >= 1; --i) {
+        const float *feat = s.d_features + (size_t)i * s.F * M;
+        const float *targ = s.d_targets + ((size_t)pf * s.n + i) * M;
+        cva_status r = mlp_train_date(feat, s.F, targ, M, hidden, n_batches, epochs, lr, 0, params_dev,
+                                      pred_dev ? pred_dev + (size_t)i * M : nullptr, nullptr, nullptr,
+                                      reinterpret_cast<cudaStream_t>(stream));
+        if (r != CVA_OK) return r;
+    }
+    return CVA_OK;
+}
+
 cva_status cva_philox4x32_10(const uint32_t *ctr_dev, uint32_t *out_dev, uint64_t n, uint64_t seed,
                              void *stream)
 {

@@ -109,6 +109,12 @@ cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const flo
 cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups, int F, uint64_t M,
                               int basis, float *pred0, double *coef_host, cudaStream_t st);
 
+// Neural regression (mlp.cu).
+int mlp_num_params(int U);
+cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t M, int U, int n_batches,
+                          int epochs, float lr, int max_steps, float *params_dev, float *pred_dev,
+                          float *grad_out_dev, float *loss_out_dev, cudaStream_t st);
+
 // CVA_0 reduction (reduce.cu).
 cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);
 cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st);

@@ -1,0 +1,95 @@
+"""The tcgen05 MLP regression (NN+ of eq. (e:nnp), Algorithms 1 and 2) against the
+FP64 oracle of the same algorithms. The GEMM operands are BF16, so the comparison
+is at BF16 accuracy: gradients of one step to a few 1e-3 relative in norm, trained
+losses and predictions to a few percent."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp as omlp
+from paper_2211_17005_gb300 import workload as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2211_17005_gb300 import api as A, build
+    build.build()
+    oracle.build()
+    return A
+
+
+def _problem(M, d=27, seed=0):
+    rng = np.random.default_rng(seed)
+    Y = (0.02 + 0.01 * rng.normal(size=(d, M))).astype(np.float32)
+    z = (Y - Y.mean(axis=1, keepdims=True)) / Y.std(axis=1, keepdims=True)
+    xi = (0.05 * np.maximum(z[:4].sum(axis=0), 0) + 0.01 + 0.002 * rng.normal(size=M)).astype(np.float32)
+    return Y, xi
+
+
+def test_first_step_gradient_matches_oracle(api):
+    M, nb, u = 4096 * 4, 32, 64
+    Y, xi = _problem(M)
+    p0 = W.mlp_init(27, u, seed=11)
+    flat = api.mlp_pack(p0, u)
+    g = api.mlp_first_gradient(torch.from_numpy(xi).cuda(), torch.from_numpy(Y).cuda(), flat, hidden=u,
+                               n_batches=nb).cpu().numpy()
+    gd = api.mlp_unpack(torch.from_numpy(g), u, 27)
+    Z, _, _ = omlp.standardize(Y.astype(np.float64).T)
+    sl = omlp.batches(M, nb)[0]
+    ref = omlp.grads(p0, Z[sl], xi[sl].astype(np.float64), 0)
+    ref16 = omlp.grads_bf16(p0, Z[sl], xi[sl].astype(np.float64), 0)
+    for k in omlp.NAMES:
+        a, b, b16 = np.ravel(gd[k]), np.ravel(ref[k]), np.ravel(ref16[k])
+        # same rounding points as the tensor-core path: only FP32 accumulation order differs
+        rel16 = np.linalg.norm(a - b16) / max(np.linalg.norm(b16), 1e-30)
+        assert rel16 < 1e-3, (k, rel16)
+        # against the exact FP64 gradient: the BF16 operand rounding itself
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel < 0.1, (k, rel)
+    # padded input columns of W1 receive nothing
+    assert np.all(g[:u * 32].reshape(u, 32)[:, 27:] == 0)
+
+
+def test_base_alg_trains_like_the_oracle(api):
+    M, nb, u, E = 4096 * 4, 32, 64, 8
+    Y, xi = _problem(M, seed=1)
+    p0 = W.mlp_init(27, u, seed=12)
+    flat = api.mlp_pack(p0, u)
+    pred, losses = api.mlp_fit(torch.from_numpy(xi).cuda(), torch.from_numpy(Y).cuda(), flat, hidden=u,
+                               n_batches=nb, epochs=E, lr=1e-3)
+    Z, _, _ = omlp.standardize(Y.astype(np.float64).T)
+    trace = []
+    best_p, best = omlp.base_alg(p0, Z, xi.astype(np.float64), n_batches=nb, epochs=E, lr=1e-3, trace=trace)
+    gpu_best = float(np.min(losses))
+    assert np.all(np.isfinite(losses))
+    assert gpu_best == pytest.approx(best, rel=0.1), (losses, trace)
+    p_or = omlp.forward(best_p, Z, 1)[0]
+    pg = pred.cpu().numpy()
+    assert np.sqrt(np.mean((pg - p_or) ** 2)) < 0.1 * np.sqrt(np.mean(xi.astype(np.float64) ** 2))
+    # the kept parameters are the best ones: their loss is the minimum of the trace
+    assert float(np.mean((pg - xi) ** 2)) == pytest.approx(gpu_best, rel=2e-2)
+
+
+def test_backward_learning_on_simulated_targets(api):
+    """Algorithm 2 over the dates of a small paper-shaped simulation."""
+    wl = W.make("paper", M=8192, N=16, n_steps=10)
+    u, nb, E = 64, 8, 8
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N)
+    sim.run(wl.seed)
+    p0 = W.mlp_init(27, u, seed=13)
+    flat = api.mlp_pack(p0, u)
+    pred = api.mlp_regress_all(sim, flat, hidden=u, n_batches=nb, epochs=E).cpu().numpy()
+    feats = sim.features().cpu().numpy().astype(np.float64)
+    targs = sim.targets()[0].cpu().numpy().astype(np.float64)
+    res = omlp.backward_alg(p0, feats, targs, dates=range(1, wl.grid.n_steps), n_batches=nb, epochs=E, lr=1e-3)
+    for i in range(1, wl.grid.n_steps):
+        scale = np.sqrt(np.mean(targs[i] ** 2))
+        gap = np.sqrt(np.mean((pred[i] - res[i][2]) ** 2))
+        assert gap < 0.15 * scale, (i, gap, scale)
+        # the regressed conditional CVA keeps the level of the targets
+        assert abs(pred[i].mean() - targs[i].mean()) < 0.05 * abs(targs[i].mean()) + 1e-6
+    sim.close()

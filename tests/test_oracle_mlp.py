@@ -73,3 +73,17 @@ def test_batches_partition_the_paths():
     sl = mlp.batches(1000, 32)
     idx = np.concatenate([np.arange(1000)[s] for s in sl])
     np.testing.assert_array_equal(idx, np.arange(1000))
+
+
+def test_bf16_rounding_and_rounded_gradient():
+    # bfloat16 keeps 8 significand bits, ties to even
+    assert mlp.bf16(1.0) == 1.0
+    assert mlp.bf16(1.0 + 2 ** -8) == 1.0            # tie -> even
+    assert mlp.bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6
+    x = np.random.default_rng(0).normal(size=1000)
+    assert np.max(np.abs(mlp.bf16(x) - x) / np.abs(x)) <= 2 ** -8
+    Z, y = _data()
+    p = W.mlp_init(5, 8, seed=3)
+    g, g16 = mlp.grads(p, Z, y, 0), mlp.grads_bf16(p, Z, y, 0)
+    for k in mlp.NAMES:
+        assert np.linalg.norm(g[k] - g16[k]) <= 0.05 * np.linalg.norm(g[k]) + 1e-12
