@@ -39,6 +39,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--lsq", action="store_true", help="least-squares regression instead of the workload's MLP")
     p.add_argument("--paths", type=int, default=None,
                    help="override the number of outer paths (small cases for profiling captures)")
     return p.parse_args()
@@ -159,18 +160,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(wl, M_sample):
-    """Time the FP64 oracle (simulation + targets + per-date least squares) on the first
-    M_sample outer paths of the workload; returns (seconds, threads)."""
+def cpu_oracle_sample(wl, M_sample, use_mlp=None):
+    """Time the FP64 oracle on the first M_sample outer paths of the workload: simulation,
+    targets and the per-date regression (Algorithm 2 with the NN+ network for the MLP
+    workloads, least squares otherwise). Returns (seconds, threads)."""
     import oracle
+    from oracle import mlp as omlp
+    from paper_2211_17005_gb300 import workload
     oracle.build()
+    if use_mlp is None:
+        use_mlp = wl.regression == "mlp"
     t0 = time.perf_counter()
     o = oracle.simulate(wl.model, wl.portfolios[0], wl.grid, 0, M_sample, wl.N, wl.seed,
                         want=("features", "xi_bar"))
-    for i in range(1, wl.grid.n_steps):
-        phi = oracle.linear_features(o["features"][i]) if wl.name != "small" else \
-            oracle.poly2_features(o["features"][i, 0])
-        oracle.lsq(phi, o["xi_bar"][i])
+    dates = range(1, wl.grid.n_steps)
+    if use_mlp:
+        p0 = workload.mlp_init(wl.model.F, wl.hidden or 64)
+        omlp.backward_alg(p0, o["features"], o["xi_bar"], dates, n_batches=32, epochs=8, lr=1e-3)
+    else:
+        for i in dates:
+            phi = oracle.linear_features(o["features"][i]) if wl.name != "small" else \
+                oracle.poly2_features(o["features"][i, 0])
+            oracle.lsq(phi, o["xi_bar"][i])
     dt = time.perf_counter() - t0
     return dt, os.cpu_count()
 
@@ -230,6 +241,19 @@ def main():
     build.build()
     wl = workload.make(args.workload, M=args.paths)
     basis = "poly2" if wl.name == "small" else "linear"
+    use_mlp = wl.regression == "mlp" and not args.lsq
+    hidden, n_batches, epochs, lr = (wl.hidden or 64), 32, 8, 1e-3
+    if use_mlp:
+        p_init = api.mlp_pack(workload.mlp_init(wl.model.F, hidden), hidden)
+        p_work = p_init.clone()
+
+    def regress(s):
+        """Regression at every date 1..n-1: Algorithm 2 with the NN+ network for the
+        MLP workloads, one grouped least-squares launch otherwise."""
+        if use_mlp:
+            p_work.copy_(p_init)      # every step starts Algorithm 2 from the same initial network
+            return api.mlp_regress_all(s, p_work, hidden=hidden, n_batches=n_batches, epochs=epochs, lr=lr)
+        return s.regress_all(0, basis=basis, want_coef=False)[0]
     k0 = rank * wl.M          # weak scaling: each rank owns its own outer paths
     sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N, profile=True)
     stream = torch.cuda.current_stream()
@@ -240,7 +264,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        pred, _ = sim.regress_all(0, basis=basis, want_coef=False)
+        pred = regress(sim)
         ev1.record(stream)
         c0 = sim.cva0(0)
         return c0, (ev0, ev1), pred
@@ -286,7 +310,7 @@ def main():
     for s in range(e2e_steps):
         sim2 = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N)
         sim2.run(s + 1, k0=k0)
-        pred, _ = sim2.regress_all(0, basis=basis, want_coef=False)
+        pred = regress(sim2)
         c0e = sim2.cva0(0)
         pinned.copy_(pred, non_blocking=True)
         torch.cuda.synchronize()
@@ -318,19 +342,35 @@ def main():
     inner_gbs = inner_bytes_per_path(wl) * wl.M / (i_avg / 1e3) / 1e9
     reg_bytes = 4 * (n - 1) * wl.M * (wl.model.F + 1 + 1)
     reg_gbs = reg_bytes / (np.mean(reg_ms) / 1e3) / 1e9
+    mlp_roof = None
+    if use_mlp:
+        d, u = wl.model.F, hidden
+        fwd = 2 * (d * u + u * u)                 # forward GEMM flops per sample
+        bwd = 2 * (u * u + u * u + d * u)         # dH1, dW2, dW1 GEMM flops per sample
+        per_date = wl.M * (epochs * (fwd + bwd) + (epochs + 2) * fwd)   # training + loss, refit, predict sweeps
+        flops = per_date * (n - 1)
+        tf = flops / (np.mean(reg_ms) / 1e3) / 1e12
+        peak_tf = pk.get("bf16_tflops_sustained", 1720.9)
+        mlp_roof = {"bound": "tensor", "kernel": "mlp_train_kernel", "achieved": tf, "peak": peak_tf,
+                    "unit": "TFLOP/s", "frac": tf / peak_tf, "traffic": None,
+                    "algorithmic_flops_per_date": per_date, "dates": n - 1,
+                    "peak_source": "measured bf16 cuBLAS, sustained", "ms": float(np.mean(reg_ms))}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         M_sample = 2048 if wl.name != "small" else wl.M
-        dt, cores = cpu_oracle_sample(wl, M_sample)
+        dt, cores = cpu_oracle_sample(wl, M_sample, use_mlp)
         cpu = {"value": M_sample * wl.N * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {M_sample} of {wl.M} outer paths, all {wl.N} inner draws, {n} dates, "
-                         f"per-date least squares ({dt:.1f} s)"}
+                         f"per-date {'NN+ Algorithm 2' if use_mlp else 'least squares'} ({dt:.1f} s)"}
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": describe(wl), "regression": f"least squares, basis {basis}",
+               "config": {"workload": describe(wl),
+                          "regression": (f"NN+ {wl.model.F}->{hidden}->{hidden}->1, Algorithm 2 over {n - 1} dates, "
+                                         f"E={epochs}, |B|={n_batches}, Adam lr={lr}, tcgen05 BF16 GEMMs")
+                          if use_mlp else f"least squares, basis {basis}",
                           "seed_per_step": "1..K", "l2": "working set > L2: 2.3 GB written per step",
                           "parallelism": f"{world} rank(s), disjoint outer-path ranges"},
                "sim_ms": s_avg + p_avg + i_avg, "sim_kernel_ms": s_avg, "price_kernel_ms": p_avg,
@@ -340,7 +380,8 @@ def main():
                "regression_samples_per_s": wl.M * (n - 1) / (np.mean(reg_ms) / 1e3),
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
-               "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+               "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
+               "mlp_roofline": mlp_roof, "cpu_baseline": cpu, "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
                "gpu_launches": 8 * args.steps}
