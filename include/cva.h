@@ -74,13 +74,15 @@ typedef struct {
 /* Spot-starting interest-rate swaps with regular resets every delta years
  * (App. B): the bank pays delta*Sigma and receives the floating coupon at each
  * reset date; omega = +1 (payer) or -1 (receiver) from the bank's point of
- * view; the fixed rate Sigma is the par rate at t = 0 (computed by the
- * library). delta must be a whole number of pricing steps. Host memory. */
+ * view. fixed_rate gives Sigma per swap; when it is NULL every swap is at par
+ * at t = 0 (P^sw_0 = 0, computed by the library from the model's curve).
+ * delta must be a whole number of pricing steps. Host memory. */
 typedef struct {
     int n_swaps;
     const int32_t *ccy, *cpty, *omega, *n_periods;   /* [n_swaps] */
     const double *notional;                          /* [n_swaps] */
     double delta;
+    const double *fixed_rate;                        /* [n_swaps] or NULL (par) */
 } cva_portfolio_desc;
 
 /* Pricing grid t_j = j*horizon/n_steps, j = 0..n_steps, with `substeps`
@@ -177,6 +179,35 @@ CVA_API cva_status cva_regress(const float *targets_dev, const float *features_d
  * [n][m] (row 0 left untouched), nullable. Synchronises when coef_host != NULL. */
 CVA_API cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float *pred_dev,
                            double *coef_host, void *stream);
+
+/* Sensitivities of CVA_0 by a hand-written adjoint (reverse-mode) sweep. The
+ * sampled default indicators have zero pathwise derivative, so the function
+ * differentiated is the smooth CVA_0 that the oversimulated average estimates,
+ * the exact discrete form of the intensity formula eq. (eq:CVAint) at i = 0:
+ *   CVA_0 = (1/M) sum_k sum_c sum_{j=1..n} (1-R_c) beta_j MtM_c(t_j)^+ (e^{-Lambda_c(t_{j-1})} - e^{-Lambda_c(t_j)})
+ * over global outer paths [k0, k0 + M) of the model, one portfolio and grid of
+ * cva_sim_create (same Philox counters). grad_host (host double, cva_grad_num_params
+ * entries) receives dCVA_0/d theta in this order: curve levels f_e (E), rate
+ * volatilities sigma^r_e (E), FX volatilities sigma^chi_e for e = 1..E-1, CIR
+ * kappa_c (C), theta_c (C), nu_c (C) (gamma_0 and the swaps' fixed rates held
+ * fixed); cva0_host receives the smooth CVA_0. The forward sweep keeps the
+ * state every ckpt_every pricing dates (<= 16; sub-steps <= 4); the reverse sweep
+ * recomputes each segment from its checkpoint. forward_only = 1 computes only
+ * the smooth CVA_0 (grad_host may be NULL). Per-path adjoints are reduced in
+ * FP64. Allocates and frees its buffers; synchronises `stream`. */
+CVA_API cva_status cva_grad_cva0(const cva_model_desc *model, const cva_portfolio_desc *pf,
+                                 const cva_grid *grid, uint64_t M, uint64_t seed, uint64_t k0,
+                                 int ckpt_every, int forward_only, double *grad_host,
+                                 double *cva0_host, void *stream);
+
+/* Par fixed rate of every swap of `pf` at t = 0 under `model` (App. B third
+ * case, P^sw_0 = 0): the rates the library uses when fixed_rate is NULL. Host
+ * output rates_host [pf->n_swaps]. Host-only, no device work. */
+CVA_API cva_status cva_par_rates(const cva_model_desc *model, const cva_portfolio_desc *pf,
+                                 double *rates_host);
+
+/* Number of parameters of cva_grad_cva0: 3E - 1 + 3C (53 for 10 economies, 8 counterparties). */
+CVA_API int cva_grad_num_params(int E, int C);
 
 /* Neural regression of Sec. 2 (eq. (e:regrkappo)) at one date: the NN+ network of
  * eq. (e:nnp) with two hidden ReLU layers of width `hidden` (64 is compiled) on

@@ -53,7 +53,8 @@ class _Portfolio(ctypes.Structure):
                 ("ccy", ctypes.POINTER(ctypes.c_int)), ("cpty", ctypes.POINTER(ctypes.c_int)),
                 ("omega", ctypes.POINTER(ctypes.c_int)),
                 ("n_periods", ctypes.POINTER(ctypes.c_int)),
-                ("notional", ctypes.POINTER(ctypes.c_double)), ("delta", ctypes.c_double)]
+                ("notional", ctypes.POINTER(ctypes.c_double)), ("delta", ctypes.c_double),
+                ("fixed_rate", ctypes.POINTER(ctypes.c_double))]
 
 
 class _Grid(ctypes.Structure):
@@ -158,8 +159,10 @@ def _model_struct(model, keep: _Keep) -> _Model:
 
 
 def _pf_struct(pf, keep: _Keep) -> _Portfolio:
+    fr = getattr(pf, "fixed_rate", None)
     return _Portfolio(pf.n_swaps, keep.i(pf.ccy), keep.i(pf.cpty), keep.i(pf.omega),
-                      keep.i(pf.n_periods), keep.d(pf.notional), float(pf.delta))
+                      keep.i(pf.n_periods), keep.d(pf.notional), float(pf.delta),
+                      keep.d(fr) if fr is not None else ctypes.POINTER(ctypes.c_double)())
 
 
 def philox4x32_10(ctr, key):
@@ -196,6 +199,11 @@ def zc(model, e: int, t: float, T: float, r: float) -> float:
     keep = _Keep()
     m = _model_struct(model, keep)
     return float(lib().oracle_zc(ctypes.byref(m), e, t, T, r))
+
+
+def par_rates(model, pf) -> np.ndarray:
+    """Par fixed rate of every swap of a portfolio at t = 0 (App. B, P^sw_0 = 0)."""
+    return np.array([par_rate(model, int(e), int(m), float(pf.delta)) for e, m in zip(pf.ccy, pf.n_periods)])
 
 
 def par_rate(model, e: int, n_periods: int, delta: float) -> float:

@@ -136,6 +136,7 @@ typedef struct {
     const int *ccy, *cpty, *omega, *n_periods;
     const double *notional;
     double delta;
+    const double *fixed_rate;   /* [n_swaps] or NULL: par at t = 0 */
 } om_portfolio;
 
 typedef struct {
@@ -281,7 +282,7 @@ int oracle_simulate(const om_model *m, const om_portfolio *pf, const om_grid *g,
     }
     double *Sigma = (double *)malloc(sizeof(double) * (NS > 0 ? NS : 1));
     for (int s = 0; s < NS; ++s)
-        Sigma[s] = oracle_par_rate(m, pf->ccy[s], pf->n_periods[s], pf->delta);
+        Sigma[s] = pf->fixed_rate ? pf->fixed_rate[s] : oracle_par_rate(m, pf->ccy[s], pf->n_periods[s], pf->delta);
 
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);

@@ -34,7 +34,7 @@ class ModelDesc(ctypes.Structure):
 
 class PortfolioDesc(ctypes.Structure):
     _fields_ = [("n_swaps", ctypes.c_int), ("ccy", _ip), ("cpty", _ip), ("omega", _ip),
-                ("n_periods", _ip), ("notional", _dp), ("delta", ctypes.c_double)]
+                ("n_periods", _ip), ("notional", _dp), ("delta", ctypes.c_double), ("fixed_rate", _dp)]
 
 
 class GridDesc(ctypes.Structure):
@@ -57,6 +57,11 @@ SIGNATURES = {
                                    ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_void_p]),
     "cva_regress_all": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp,
                                        ctypes.c_void_p]),
+    "cva_grad_cva0": (ctypes.c_int, [ctypes.POINTER(ModelDesc), ctypes.POINTER(PortfolioDesc),
+                                     ctypes.POINTER(GridDesc), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_void_p]),
+    "cva_grad_num_params": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "cva_par_rates": (ctypes.c_int, [ctypes.POINTER(ModelDesc), ctypes.POINTER(PortfolioDesc), _dp]),
     "cva_mlp_fit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p]),

@@ -41,8 +41,10 @@ def model_desc(model, keep: _Keep) -> nat.ModelDesc:
 
 
 def portfolio_desc(pf, keep: _Keep) -> nat.PortfolioDesc:
+    fr = getattr(pf, "fixed_rate", None)
     return nat.PortfolioDesc(pf.n_swaps, keep.i(pf.ccy), keep.i(pf.cpty), keep.i(pf.omega),
-                           keep.i(pf.n_periods), keep.d(pf.notional), float(pf.delta))
+                             keep.i(pf.n_periods), keep.d(pf.notional), float(pf.delta),
+                             keep.d(fr) if fr is not None else ctypes.POINTER(ctypes.c_double)())
 
 
 def _stream_handle(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
@@ -256,3 +258,77 @@ def mlp_regress_all(sim: "Simulation", params: torch.Tensor, pf: int = 0, hidden
                                           ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(pred.data_ptr()),
                                           _stream_handle(stream)), "cva_mlp_regress_all")
     return pred
+
+
+# ------------------------------------------------------------ adjoint ------
+
+def par_rates(model, pf) -> np.ndarray:
+    """The par fixed rates at t = 0 the library uses for `pf` under `model`."""
+    keep = _Keep()
+    out = np.zeros(pf.n_swaps)
+    nat.check(N_lib().cva_par_rates(ctypes.byref(model_desc(model, keep)), ctypes.byref(portfolio_desc(pf, keep)),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "cva_par_rates")
+    return out
+
+
+def frozen(model, pf):
+    """A copy of `pf` whose fixed rates are the par rates under `model` (trade terms that
+    do not move when the model's parameters are bumped)."""
+    import dataclasses
+    return dataclasses.replace(pf, fixed_rate=par_rates(model, pf))
+
+
+def grad_params(model) -> np.ndarray:
+    """theta in the order of cva_grad_cva0: f (E), sigma^r (E), sigma^chi_1..E-1, kappa, theta, nu (C each)."""
+    return np.concatenate([model.curve, model.hw_sigma, model.fx_vol[1:], model.cir_kappa, model.cir_theta,
+                           model.cir_nu]).astype(np.float64)
+
+
+def with_params(model, theta) -> "object":
+    """A copy of `model` with the parameters of grad_params replaced by theta."""
+    import dataclasses
+    E, C = model.E, model.C
+    t = np.asarray(theta, dtype=np.float64)
+    o = 0
+    curve = t[o:o + E].copy(); o += E
+    hw_sigma = t[o:o + E].copy(); o += E
+    fx_vol = np.concatenate([[model.fx_vol[0]], t[o:o + E - 1]]); o += E - 1
+    kappa = t[o:o + C].copy(); o += C
+    theta_c = t[o:o + C].copy(); o += C
+    nu = t[o:o + C].copy()
+    return dataclasses.replace(model, curve=curve, hw_sigma=hw_sigma, fx_vol=fx_vol, cir_kappa=kappa,
+                               cir_theta=theta_c, cir_nu=nu)
+
+
+def grad_cva0(model, pf, grid, M: int, seed: int = 1, k0: int = 0, ckpt_every: int = 10,
+              forward_only: bool = False, stream=None):
+    """(smooth CVA_0, dCVA_0/dtheta or None) by the adjoint kernel; see cva_grad_cva0."""
+    keep = _Keep()
+    md = model_desc(model, keep)
+    pd = portfolio_desc(pf, keep)
+    gd = nat.GridDesc(float(grid.horizon), int(grid.n_steps), int(grid.substeps))
+    npar = int(N_lib().cva_grad_num_params(model.E, model.C))
+    g = np.zeros(npar)
+    c0 = ctypes.c_double()
+    nat.check(N_lib().cva_grad_cva0(ctypes.byref(md), ctypes.byref(pd), ctypes.byref(gd), int(M), int(seed), int(k0),
+                                    int(ckpt_every), 1 if forward_only else 0,
+                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(c0),
+                                    _stream_handle(stream)), "cva_grad_cva0")
+    return float(c0.value), (None if forward_only else g)
+
+
+class SmoothCVA0(torch.autograd.Function):
+    """CVA_0 (smooth form) as a function of theta = grad_params(model); backward returns
+    the adjoint sensitivities. Usage: SmoothCVA0.apply(theta, model, portfolio, grid, M, seed)."""
+
+    @staticmethod
+    def forward(ctx, theta, model, pf, grid, M, seed):
+        m = with_params(model, theta.detach().cpu().numpy())
+        c0, g = grad_cva0(m, pf, grid, M, seed)
+        ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
+        return torch.tensor(c0, dtype=theta.dtype, device=theta.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return grad_out * g, None, None, None, None, None

@@ -187,6 +187,7 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
             if (d.n_periods[s] < 1 || d.n_periods[s] > kMaxG)
                 return fail(CVA_EINVAL, "swap: n_periods must be in [1, 10]");
             if (!is_fin(d.notional[s])) return fail(CVA_EINVAL, "swap: notional must be finite");
+            if (d.fixed_rate && !is_fin(d.fixed_rate[s])) return fail(CVA_EINVAL, "swap: fixed rate must be finite");
             G = std::max(G, (int)d.n_periods[s]);
         }
     }
@@ -281,7 +282,8 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
                 const int e = d.ccy[sw], c = d.cpty[sw], m = d.n_periods[sw];
                 double ann = 0.0;
                 for (int g = 1; g <= m; ++g) ann += std::exp(-model->curve[e] * g * delta);
-                const double Sigma = (1.0 - std::exp(-model->curve[e] * m * delta)) / (delta * ann);
+                const double Sigma = d.fixed_rate ? d.fixed_rate[sw]
+                                                  : (1.0 - std::exp(-model->curve[e] * m * delta)) / (delta * ann);
                 const double wN = d.omega[sw] * d.notional[sw];
                 const size_t base = (((size_t)p * C + c) * E + e) * Ginst;
                 for (int h = 0; h < m; ++h) wA[base + h] += wN;                  // float notional, period h
@@ -473,6 +475,145 @@ cva_status cva_mlp_regress_all(const cva_sim *sim, int pf, int hidden, int n_bat
         if (r != CVA_OK) return r;
     }
     return CVA_OK;
+}
+
+int cva_grad_num_params(int E, int C) { return 3 * E - 1 + 3 * C; }
+
+cva_status cva_par_rates(const cva_model_desc *model, const cva_portfolio_desc *pf, double *rates_host)
+{
+    int F = 0, CS = 0;
+    std::vector<double> L;
+    cva_status st = validate_model(model, &F, &CS, L);
+    if (st != CVA_OK) return st;
+    if (!pf || !rates_host || pf->n_swaps < 0 || !(pf->delta > 0.0)) return fail(CVA_EINVAL, "par_rates: bad portfolio");
+    for (int s = 0; s < pf->n_swaps; ++s) {
+        const int e = pf->ccy[s], m = pf->n_periods[s];
+        if (e < 0 || e >= model->E || m < 1) return fail(CVA_EINVAL, "par_rates: bad swap");
+        double ann = 0.0;
+        for (int g = 1; g <= m; ++g) ann += std::exp(-model->curve[e] * g * pf->delta);
+        rates_host[s] = (1.0 - std::exp(-model->curve[e] * m * pf->delta)) / (pf->delta * ann);
+    }
+    return CVA_OK;
+}
+
+cva_status cva_grad_cva0(const cva_model_desc *model, const cva_portfolio_desc *pf, const cva_grid *grid,
+                         uint64_t M, uint64_t seed, uint64_t k0, int ckpt_every, int forward_only,
+                         double *grad_host, double *cva0_host, void *stream)
+{
+    if (!cva0_host || (!forward_only && !grad_host)) return fail(CVA_EINVAL, "grad: NULL output");
+    if (M < 1 || M > 0x7fffffffull || k0 + M > 0xffffffffull) return fail(CVA_EINVAL, "grad: bad path range");
+    cva_sim *hs = nullptr;
+    cva_status st = cva_sim_create(model, pf, 1, grid, 1, 1, 0, &hs);   // tables only
+    if (st != CVA_OK) return st;
+    Sim &s = *reinterpret_cast<Sim *>(hs);
+    const int E = s.E, C = s.C, n = s.n, S = s.S, G = s.Ginst, F = s.F;
+    const int NPAR = 3 * E - 1 + 3 * C, NV = 2 * E + 3 * C;
+    const int K = ckpt_every > 0 ? ckpt_every : 10;
+    const double Delta = s.horizon / n, ds = Delta / S, delta = s.delta;
+    const int ppp = s.ppp, periods = n / ppp + 1;
+    std::vector<HW> hw(E);
+    for (int e = 0; e < E; ++e) hw[e] = HW{model->hw_a[e], model->hw_sigma[e], model->curve[e]};
+    // derivatives of ln A(t, T) of the flat-curve Hull-White bond with respect to f and sigma:
+    //   d/df = -(T - t) + B(t, T),  d/dsigma = -sigma/(2a) (1 - e^{-2at}) B(t, T)^2
+    auto dA = [&](int e, double t, double T, double &df, double &dsg) {
+        const double b = hw[e].B(t, T), a = hw[e].a, sg = hw[e].s;
+        df = -(T - t) + b;
+        dsg = -sg / (2.0 * a) * (1.0 - std::exp(-2.0 * a * t)) * b * b;
+    };
+    std::vector<float4> dzc((size_t)(n + 1) * E * G, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int j = 0; j <= n; ++j) {
+        const double t = j * Delta;
+        for (int e = 0; e < E; ++e)
+            for (int g = 0; g < G; ++g) {
+                const double T = (g + 1) * delta;
+                if (T + 1e-12 < t) continue;
+                double df, dsg, df0 = 0.0, dsg0 = 0.0;
+                dA(e, t, T, df, dsg);
+                if (T - delta + 1e-12 >= t) dA(e, t, T - delta, df0, dsg0);
+                else df0 = df, dsg0 = dsg;
+                dzc[((size_t)j * E + e) * G + g] = make_float4((float)df, (float)dsg, (float)(df - df0), (float)(dsg - dsg0));
+            }
+    }
+    std::vector<float2> dfix((size_t)(periods + 1) * E);
+    for (int p = 0; p <= periods; ++p)
+        for (int e = 0; e < E; ++e) {
+            double df, dsg;
+            dA(e, p * delta, (p + 1) * delta, df, dsg);
+            dfix[(size_t)p * E + e] = make_float2((float)df, (float)dsg);
+        }
+    std::vector<float> rho(E, 0.f), sig(2 * E + 3 * C, 0.f);
+    std::vector<float2> ddrift((size_t)n * S * E);
+    for (int e = 1; e < E; ++e) rho[e] = (float)model->corr[e * F + (E - 1 + e)];
+    for (int q = 0; q < n * S; ++q)
+        for (int e = 0; e < E; ++e) {
+            const double a = hw[e].a, sg = hw[e].s, t = q * ds;
+            const double dq = e ? rho[e] * model->fx_vol[e] : 0.0;   // d quanto / d sigma^r
+            ddrift[(size_t)q * E + e] = make_float2((float)(a * ds),
+                                                    (float)((sg / a * (1.0 - std::exp(-2.0 * a * t)) - dq) * ds));
+        }
+    for (int e = 0; e < E; ++e) {
+        sig[e] = (float)model->hw_sigma[e];
+        sig[E + e] = e ? (float)model->fx_vol[e] : 0.f;
+    }
+    for (int c = 0; c < C; ++c) {
+        sig[2 * E + c] = (float)model->cir_kappa[c];
+        sig[2 * E + C + c] = (float)model->cir_theta[c];
+        sig[2 * E + 2 * C + c] = (float)model->cir_nu[c];
+    }
+    AdjBuffers b;
+    b.K = K;
+    b.nseg = (n + K - 1) / K;
+    b.forward_only = forward_only ? 1 : 0;
+    const size_t Mz = M;
+    const unsigned blocks = (unsigned)((M + 127) / 128);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    auto cleanup = [&]() {
+        cudaFree(b.dzc);
+        cudaFree(b.dfix);
+        cudaFree(b.ddrift);
+        cudaFree(b.rho);
+        cudaFree(b.sig);
+        cudaFree(b.ckpt);
+        cudaFree(b.ckpt_I0);
+        cudaFree(b.fixr);
+        cudaFree(b.part);
+        cudaFree(b.sum);
+        cva_sim_destroy(hs);
+    };
+    if (dev_alloc(&b.dzc, dzc.size()) != CVA_OK || dev_alloc(&b.dfix, dfix.size()) != CVA_OK ||
+        dev_alloc(&b.ddrift, ddrift.size()) != CVA_OK || dev_alloc(&b.rho, rho.size()) != CVA_OK ||
+        dev_alloc(&b.sig, sig.size()) != CVA_OK || dev_alloc(&b.ckpt, (size_t)b.nseg * NV * Mz) != CVA_OK ||
+        dev_alloc(&b.ckpt_I0, (size_t)b.nseg * Mz) != CVA_OK ||
+        dev_alloc(&b.fixr, (size_t)(periods + 1) * E * Mz) != CVA_OK ||
+        dev_alloc(&b.part, (size_t)blocks * (NPAR + 1)) != CVA_OK || dev_alloc(&b.sum, (size_t)NPAR + 1) != CVA_OK) {
+        cleanup();
+        return CVA_ENOMEM;
+    }
+    cudaError_t e1 = cudaMemcpyAsync(b.dzc, dzc.data(), dzc.size() * sizeof(float4), cudaMemcpyHostToDevice, cs);
+    cudaError_t e2 = cudaMemcpyAsync(b.dfix, dfix.data(), dfix.size() * sizeof(float2), cudaMemcpyHostToDevice, cs);
+    cudaError_t e3 = cudaMemcpyAsync(b.ddrift, ddrift.data(), ddrift.size() * sizeof(float2), cudaMemcpyHostToDevice, cs);
+    cudaError_t e4 = cudaMemcpyAsync(b.rho, rho.data(), rho.size() * sizeof(float), cudaMemcpyHostToDevice, cs);
+    cudaError_t e5 = cudaMemcpyAsync(b.sig, sig.data(), sig.size() * sizeof(float), cudaMemcpyHostToDevice, cs);
+    for (cudaError_t e : {e1, e2, e3, e4, e5})
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "grad: table upload");
+        }
+    st = launch_adjoint(s, b, seed, k0, (uint32_t)M, cs);
+    if (st == CVA_OK) st = sum_columns_fp64(b.part, (int)blocks, NPAR + 1, b.sum, cs);
+    std::vector<double> h(NPAR + 1);
+    if (st == CVA_OK) {
+        cudaError_t e = cudaMemcpyAsync(h.data(), b.sum, h.size() * sizeof(double), cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "grad: read-back");
+    }
+    if (st == CVA_OK) {
+        *cva0_host = h[NPAR] / (double)M;
+        if (grad_host && !forward_only)
+            for (int i = 0; i < NPAR; ++i) grad_host[i] = h[i] / (double)M;
+    }
+    cleanup();
+    return st;
 }
 
 cva_status cva_philox4x32_10(const uint32_t *ctr_dev, uint32_t *out_dev, uint64_t n, uint64_t seed,

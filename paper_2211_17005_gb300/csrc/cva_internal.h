@@ -86,11 +86,27 @@ struct Sim {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
+// Device buffers of the adjoint sweep (adjoint.cuh).
+struct AdjBuffers {
+    int K, nseg, forward_only;
+    float4 *dzc = nullptr;      // [n+1][E][G] d/df, d/dsigma of (lnA, dlnA)
+    float2 *dfix = nullptr;     // [periods+1][E] d/df, d/dsigma of lnA(p delta, (p+1) delta)
+    float2 *ddrift = nullptr;   // [n*S][E] d drift/df, d drift/dsigma^r
+    float *rho = nullptr;       // [E]
+    float *sig = nullptr;       // [2E + 3C]
+    float *ckpt = nullptr;      // [nseg][2E+3C][M]
+    double *ckpt_I0 = nullptr;  // [nseg][M]
+    float *fixr = nullptr;      // [periods+1][E][M]
+    double *part = nullptr;     // [blocks][npar+1]
+    double *sum = nullptr;      // [npar+1]
+};
+
 // One compiled shape of the outer-path kernel (outer_*.cu).
 struct OuterInst {
     int E, C, CS, G, NPF;
     cva_status (*launch)(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);
     void (*forget)(const Sim *s);
+    cva_status (*adjoint)(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st);
 };
 
 // Kernel launchers (sim.cu).
@@ -98,6 +114,8 @@ cva_status launch_outer(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);
 cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st);
 void forget_const_owner(const Sim *s);
 bool outer_supported(int E, int C, int CS, int G, int NPF, int *Ginst);
+cva_status launch_adjoint(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st);
+cva_status sum_columns_fp64(const double *part, int rows, int cols, double *out, cudaStream_t st);
 
 // Regression (lsq.cu): least squares for `groups` dates at once; group g reads
 // features feat0 + g*feat_stride ([F][M]) and targets targ0 + g*targ_stride.

@@ -242,6 +242,14 @@ __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
         }
 }
 
+}  // namespace
+}  // namespace cva
+
+#include "adjoint.cuh"
+
+namespace cva {
+namespace {
+
 // Constant-memory ownership of this translation unit: a launch for another
 // simulation re-uploads the tables, and every launch first waits for the
 // previous one (on whichever stream) before constant memory can change.
@@ -288,6 +296,49 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     CVA_CUDA_TRY(cudaGetLastError());
     if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
     price_kernel<E, C, CS, G, NPF><<<dim3((args.M + 255u) / 256u, (unsigned)s.n + 1u), 256, 0, st>>>(args);
+    CVA_CUDA_TRY(cudaGetLastError());
+    CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
+    return CVA_OK;
+}
+
+template <int E, int C, int CS, int G>
+cva_status adjoint_launch(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st)
+{
+    constexpr int KMAX = 16, SMAX = 4;
+    if (b.K < 1 || b.K > KMAX || s.S > SMAX) return fail(CVA_ENOTSUP, "adjoint: checkpoint interval <= 16, sub-steps <= 4");
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    AdjArgs a;
+    a.M = M;
+    a.k0 = (uint32_t)k0;
+    a.seed_lo = (uint32_t)seed;
+    a.seed_hi = (uint32_t)(seed >> 32);
+    a.K = b.K;
+    a.nseg = b.nseg;
+    a.forward_only = b.forward_only;
+    a.zc = s.d_zc;
+    a.fix = s.d_fix;
+    a.date_p = s.d_date_p;
+    a.drift = s.d_drift;
+    a.dzc = b.dzc;
+    a.dfix = b.dfix;
+    a.ddrift = b.ddrift;
+    a.rho = b.rho;
+    a.sig = b.sig;
+    a.ckpt = b.ckpt;
+    a.ckpt_I0 = b.ckpt_I0;
+    a.fixr = b.fixr;
+    a.part = b.part;
+    std::lock_guard<std::mutex> lk(t_const_mu);
+    if (!t_last[dev]) CVA_CUDA_TRY(cudaEventCreateWithFlags(&t_last[dev], cudaEventDisableTiming));
+    else CVA_CUDA_TRY(cudaStreamWaitEvent(st, t_last[dev], 0));
+    if (t_owner[dev] != &s) {
+        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_sim, &s.consts, sizeof(SimConsts), 0, cudaMemcpyHostToDevice, st));
+        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_w, &s.weights, sizeof(SimWeights), 0, cudaMemcpyHostToDevice, st));
+        t_owner[dev] = &s;
+    }
+    adjoint_kernel<E, C, CS, G, KMAX, SMAX><<<(M + 127u) / 128u, 128, 0, st>>>(a);
     CVA_CUDA_TRY(cudaGetLastError());
     CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
     return CVA_OK;

@@ -67,6 +67,16 @@ __global__ void philox_fill(const uint4 *__restrict__ ctr, uint4 *__restrict__ o
     if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
 }
 
+// out[c] = sum over rows r of part[r][c], in row order (one thread per column)
+__global__ void sum_cols(const double *__restrict__ part, int rows, int cols, double *__restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += part[(size_t)r * cols + c];
+    out[c] = s;
+}
+
 std::mutex g_red_mu;
 double2 *g_red_buf[64] = {};
 
@@ -81,6 +91,13 @@ cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_
     if (blocks > 0x7fffffffull) return fail(CVA_EINVAL, "philox: n too large");
     philox_fill<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const uint4 *>(ctr), reinterpret_cast<uint4 *>(out),
                                                   n, (uint32_t)seed, (uint32_t)(seed >> 32));
+    CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
+}
+
+cva_status sum_columns_fp64(const double *part, int rows, int cols, double *out, cudaStream_t st)
+{
+    sum_cols<<<(cols + 127) / 128, 128, 0, st>>>(part, rows, cols, out);
     CVA_CUDA_TRY(cudaGetLastError());
     return CVA_OK;
 }

@@ -176,6 +176,13 @@ void forget_const_owner(const Sim *s)
     }
 }
 
+cva_status launch_adjoint(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st)
+{
+    const OuterInst *o = find_outer(s.E, s.C, s.CS, s.G, s.NPF);
+    if (!o || o->G != s.Ginst || !o->adjoint) return fail(CVA_ENOTSUP, "no adjoint kernel for this model shape");
+    return o->adjoint(s, b, seed, k0, M, st);
+}
+
 cva_status launch_outer(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
 {
     const OuterInst *o = find_outer(s.E, s.C, s.CS, s.G, s.NPF);

@@ -76,6 +76,7 @@ class Portfolio:
     omega: np.ndarray      # [S] int32, +1 payer, -1 receiver
     n_periods: np.ndarray  # [S] int32, maturity in periods of length delta
     delta: float = 1.0
+    fixed_rate: Optional[np.ndarray] = None   # [S]; None: par at t = 0
 
     @property
     def n_swaps(self) -> int:
