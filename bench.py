@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--workload", default="paper")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--lsq", action="store_true", help="least-squares regression instead of the workload's MLP")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     p.add_argument("--paths", type=int, default=None,
                    help="override the number of outer paths (small cases for profiling captures)")
     return p.parse_args()
@@ -356,6 +357,29 @@ def main():
                     "algorithmic_flops_per_date": per_date, "dates": n - 1,
                     "peak_source": "measured bf16 cuBLAS, sustained", "ms": float(np.mean(reg_ms))}
 
+    # ---- adjoint / forward cost of CVA_0 sensitivities (adjoint workload, rank 0) ----
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        awl = workload.make("adjoint", M=args.paths)
+        apf = api.frozen(awl.model, awl.portfolios[0])
+
+        def timed(fwd_only):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c, g = api.grad_cva0(awl.model, apf, awl.grid, awl.M, awl.seed, ckpt_every=10, forward_only=fwd_only)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), c
+
+        timed(True)
+        timed(False)
+        t_f = [timed(True)[0] for _ in range(3)]
+        t_a = [timed(False)[0] for _ in range(3)]
+        adj = {"workload": describe(awl) + ", 53 parameters, checkpoint every 10 dates",
+               "adjoint_ms": float(np.median(t_a)), "smooth_forward_ms": float(np.median(t_f)),
+               "ratio": float(np.median(t_a) / np.median(t_f))}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         M_sample = 2048 if wl.name != "small" else wl.M
@@ -381,7 +405,7 @@ def main():
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
-               "mlp_roofline": mlp_roof, "cpu_baseline": cpu, "clocks": clk,
+               "mlp_roofline": mlp_roof, "adjoint_forward": adj, "cpu_baseline": cpu, "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
                "gpu_launches": 8 * args.steps}

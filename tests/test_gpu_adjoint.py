@@ -82,7 +82,7 @@ def test_adjoint_matches_gpu_crn_differences(api):
 
 
 def test_checkpoint_interval_does_not_change_the_gradient(api):
-    wl = W.make("adjoint", M=1000, n_steps=23)
+    wl = W.make("adjoint", M=1000, n_steps=30)
     pf = api.frozen(wl.model, wl.portfolios[0])
     ref_c, ref = api.grad_cva0(wl.model, pf, wl.grid, wl.M, wl.seed, ckpt_every=10)
     for K in (1, 7, 16):
