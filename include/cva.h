@@ -180,6 +180,28 @@ CVA_API cva_status cva_regress(const float *targets_dev, const float *features_d
 CVA_API cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float *pred_dev,
                            double *coef_host, void *stream);
 
+/* Least squares of eq. (e:forw) for every date 1..n-1 and every portfolio of a
+ * simulation in one grouped launch: the portfolios share each date's features,
+ * so every date's normal matrix is accumulated once (FP64) with one target column
+ * per portfolio and solved once (Cholesky, FP64) for all of them. pred_dev: float
+ * [n_pf][n][M] (date 0 untouched), nullable; coef_host: double [n_pf][n][m]
+ * (date 0 untouched), nullable. The scratch belongs to the simulation: the first
+ * call allocates it, so make one call before capturing this one in a CUDA graph.
+ * Without coef_host the call does not synchronise and can be captured together
+ * with cva_simulate. */
+CVA_API cva_status cva_regress_portfolios(cva_sim *sim, int basis, float *pred_dev, double *coef_host,
+                                          void *stream);
+
+/* Tile shapes of a simulation chosen by measurement: threads per block of the
+ * path-simulation and pricing kernels, outer paths per block of the
+ * inner-default kernel, and the number of blocks of the grouped regression
+ * (basis `basis`). Each candidate runs on the simulation's own shapes (CUDA-event
+ * timings, best of two after a warm-up); the choice is kept in the simulation and
+ * cached per (device, shape) for the life of the process. report (nullable)
+ * receives the choice as JSON. Runs the kernels; synchronises `stream`. */
+CVA_API cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, size_t report_len,
+                                void *stream);
+
 /* Sensitivities of CVA_0 by a hand-written adjoint (reverse-mode) sweep. The
  * sampled default indicators have zero pathwise derivative, so the function
  * differentiated is the smooth CVA_0 that the oversimulated average estimates,

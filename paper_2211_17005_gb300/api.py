@@ -137,6 +137,28 @@ class Simulation:
     def cva0(self, pf: int = 0, stream=None) -> Tuple[float, float]:
         return cva0(self.targets()[pf, 0], stream=stream)
 
+    def regress_portfolios(self, basis: str = "linear", pred: Optional[torch.Tensor] = None, stream=None,
+                           want_coef: bool = False):
+        """Least squares at every date 1..n-1 for every portfolio in one grouped launch;
+        returns (predictions [n_pf, n, M] on the device, coefficients [n_pf, n, m] or None)."""
+        b = nat.BASIS_POLY2 if basis == "poly2" else nat.BASIS_LINEAR
+        m = 3 if b == nat.BASIS_POLY2 else self.F + 1
+        if pred is None:
+            pred = torch.zeros((self.n_pf, self.n, self.M), dtype=torch.float32, device=self.device)
+        coef = np.zeros((self.n_pf, self.n, m)) if want_coef else None
+        cp = coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_coef else None
+        nat.check(N_lib().cva_regress_portfolios(self._h, b, ctypes.c_void_p(pred.data_ptr()), cp,
+                                                 _stream_handle(stream)), "cva_regress_portfolios")
+        return pred, coef
+
+    def autotune(self, seed: int = 1, basis: str = "linear", stream=None) -> dict:
+        """Pick the tile shapes by measurement (see cva_autotune); returns the choice."""
+        import json
+        buf = ctypes.create_string_buffer(512)
+        b = nat.BASIS_POLY2 if basis == "poly2" else nat.BASIS_LINEAR
+        nat.check(N_lib().cva_autotune(self._h, int(seed), b, buf, 512, _stream_handle(stream)), "cva_autotune")
+        return json.loads(buf.value.decode())
+
     def regress_all(self, pf: int = 0, basis: str = "poly2", stream=None, want_coef: bool = True):
         """Least squares at every date 1..n-1 in one grouped launch; returns
         (predictions [n, M] on the device, coefficients [n, m] numpy or None)."""

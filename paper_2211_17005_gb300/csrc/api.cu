@@ -4,7 +4,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <functional>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -94,6 +98,8 @@ void free_sim(Sim *s)
     cudaFree(s->d_mtm);
     cudaFree(s->d_targets);
     cudaFree(s->d_idx);
+    cudaFree(s->d_const_img);
+    cudaFree(s->d_lsq);
     for (cudaEvent_t &e : s->ev)
         if (e) cudaEventDestroy(e);
     delete s;
@@ -318,12 +324,15 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
     if (flags & CVA_KEEP_EXPOSURES) TRY_ALLOC(s->d_mtm, (size_t)n_pf * (n + 1) * C * Mz);
     TRY_ALLOC(s->d_targets, (size_t)n_pf * n * Mz);
     if (flags & CVA_KEEP_DEFAULTS) TRY_ALLOC(s->d_idx, Mz * N * C);
+    TRY_ALLOC(s->d_const_img, sizeof(SimConsts) + sizeof(SimWeights));
 #undef TRY_ALLOC
     cudaError_t e1 = cudaMemcpy(s->d_zc, zc.data(), zc.size() * sizeof(float4), cudaMemcpyHostToDevice);
     cudaError_t e2 = cudaMemcpy(s->d_fix, fix.data(), fix.size() * sizeof(float2), cudaMemcpyHostToDevice);
     cudaError_t e3 = cudaMemcpy(s->d_date_p, date_p.data(), date_p.size() * sizeof(int), cudaMemcpyHostToDevice);
     cudaError_t e4 = cudaMemcpy(s->d_drift, drift.data(), drift.size() * sizeof(float), cudaMemcpyHostToDevice);
-    for (cudaError_t e : {e1, e2, e3, e4})
+    cudaError_t e5 = cudaMemcpy(s->d_const_img, &s->consts, sizeof(SimConsts), cudaMemcpyHostToDevice);
+    cudaError_t e6 = cudaMemcpy(s->d_const_img + sizeof(SimConsts), &s->weights, sizeof(SimWeights), cudaMemcpyHostToDevice);
+    for (cudaError_t e : {e1, e2, e3, e4, e5, e6})
         if (e != cudaSuccess) {
             free_sim(s);
             return cuda_fail(e, "table upload");
@@ -437,6 +446,147 @@ cva_status cva_regress_batched_static(const float *targets_dev, const float *fea
 {
     return lsq_batched_static(targets_dev, features_dev, groups, F, M, basis, pred_dev, coef_host,
                               reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_regress_portfolios(cva_sim *sim, int basis, float *pred_dev, double *coef_host, void *stream)
+{
+    if (!sim) return fail(CVA_EINVAL, "sim is NULL");
+    Sim &s = *reinterpret_cast<Sim *>(sim);
+    if (s.n < 2) return fail(CVA_EINVAL, "need at least two pricing steps");
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const size_t M = s.M;
+    const int m = (basis == CVA_BASIS_POLY2) ? 3 : s.F + 1;
+    LsqJob j;
+    j.feat0 = s.d_features + (size_t)s.F * M;       // date 1
+    j.feat_stride = (size_t)s.F * M;
+    j.targ0 = s.d_targets + M;                       // portfolio 0, date 1
+    j.targ_stride = M;
+    j.targ_tstride = (size_t)s.n * M;
+    j.pred0 = pred_dev ? pred_dev + M : nullptr;
+    j.pred_stride = M;
+    j.pred_tstride = (size_t)s.n * M;
+    j.F = s.F;
+    j.M = M;
+    j.basis = basis;
+    j.groups = s.n - 1;
+    j.nt = s.NPF;
+    j.chunk_target = s.tune_lsq_chunks;
+    const size_t need = lsq_scratch_need(j);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CVA_CUDA_TRY(cudaStreamIsCapturing(cs, &cap));
+    if (s.lsq_cap < need) {
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(CVA_EINVAL, "regress_portfolios: call once before capturing so that the scratch exists");
+        CVA_CUDA_TRY(cudaStreamSynchronize(cs));
+        cudaFree(s.d_lsq);
+        s.d_lsq = nullptr;
+        s.lsq_cap = 0;
+        if (dev_alloc(&s.d_lsq, need) != CVA_OK) return CVA_ENOMEM;
+        s.lsq_cap = need;
+    }
+    if (!coef_host) return lsq_launch(j, s.d_lsq, s.lsq_cap, nullptr, cs);
+    std::vector<double> tmp((size_t)j.groups * j.nt * m);
+    cva_status r = lsq_launch(j, s.d_lsq, s.lsq_cap, tmp.data(), cs);
+    if (r != CVA_OK) return r;
+    for (int g = 0; g < j.groups; ++g)          // [date][portfolio][m] -> [portfolio][date][m]
+        for (int t = 0; t < j.nt; ++t)
+            for (int i = 0; i < m; ++i)
+                coef_host[((size_t)t * s.n + (g + 1)) * m + i] = tmp[((size_t)g * j.nt + t) * m + i];
+    return CVA_OK;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::array<int, 4>> g_tune_cache;
+
+float time_once(cudaStream_t st, const std::function<cva_status()> &f, cva_status *err)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    *err = f();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+}  // namespace
+
+cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, size_t report_len, void *stream)
+{
+    if (!sim) return fail(CVA_EINVAL, "sim is NULL");
+    Sim &s = *reinterpret_cast<Sim *>(sim);
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    CVA_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    char key[512];
+    snprintf(key, sizeof(key), "%s|E%d C%d CS%d G%d P%d n%d S%d M%llu N%u b%d", prop.name, s.E, s.C, s.CS, s.Ginst,
+             s.NPF, s.n, s.S, (unsigned long long)s.M, s.N, basis);
+    std::array<int, 4> best = {s.tune_sim_block, s.tune_price_block, s.tune_inner_P, s.tune_lsq_chunks};
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        cva_status err = CVA_OK;
+        auto measure = [&](int which, int value) -> float {
+            std::array<int, 4> save = {s.tune_sim_block, s.tune_price_block, s.tune_inner_P, s.tune_lsq_chunks};
+            int *slot[4] = {&s.tune_sim_block, &s.tune_price_block, &s.tune_inner_P, &s.tune_lsq_chunks};
+            *slot[which] = value;
+            auto run = [&]() -> cva_status {
+                if (which == 3) return cva_regress_portfolios(sim, basis, nullptr, nullptr, cs);
+                if (which == 2) return launch_inner(s, seed, 0, cs);
+                return launch_outer(s, seed, 0, cs);
+            };
+            time_once(cs, run, &err);              // warm-up
+            float t = 1e30f;
+            for (int rep = 0; rep < 2 && err == CVA_OK; ++rep) t = fminf(t, time_once(cs, run, &err));
+            s.tune_sim_block = save[0];
+            s.tune_price_block = save[1];
+            s.tune_inner_P = save[2];
+            s.tune_lsq_chunks = save[3];
+            return err == CVA_OK ? t : 1e30f;
+        };
+        const std::vector<std::vector<int>> cand = {{64, 128}, {128, 256}, {2, 4, 8}, {1216, 2432, 4864, 9728}};
+        // the first pass needs valid outputs of the earlier kernels: simulate once
+        cva_status r = cva_simulate(sim, seed, 0, stream);
+        if (r != CVA_OK) return r;
+        for (int w = 0; w < 4; ++w) {
+            float tb = 1e30f;
+            for (int v : cand[w]) {
+                const float t = measure(w, v);
+                if (t < tb) {
+                    tb = t;
+                    best[w] = v;
+                }
+            }
+            int *slot[4] = {&s.tune_sim_block, &s.tune_price_block, &s.tune_inner_P, &s.tune_lsq_chunks};
+            *slot[w] = best[w];
+        }
+        if (err != CVA_OK) return err;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    s.tune_sim_block = best[0];
+    s.tune_price_block = best[1];
+    s.tune_inner_P = best[2];
+    s.tune_lsq_chunks = best[3];
+    if (report && report_len)
+        snprintf(report, report_len, "{\"sim_block\": %d, \"price_block\": %d, \"inner_paths_per_block\": %d, "
+                                     "\"lsq_chunk_target\": %d, \"cached\": %s}",
+                 best[0], best[1], best[2], best[3], cached ? "true" : "false");
+    return CVA_OK;
 }
 
 int cva_mlp_num_params(int hidden) { return mlp_num_params(hidden); }

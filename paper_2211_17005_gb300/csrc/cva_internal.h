@@ -81,6 +81,14 @@ struct Sim {
     float *d_mtm = nullptr;        // [NPF][n+1][C][M] (optional)
     float *d_targets = nullptr;    // [NPF][n][M]
     uint8_t *d_idx = nullptr;      // [M][N][C] (optional)
+    // device image of consts + weights (constant uploads are device-to-device, so
+    // they can be captured in a CUDA graph)
+    unsigned char *d_const_img = nullptr;
+    // tile shapes, set by cva_autotune
+    int tune_sim_block = 128, tune_price_block = 256, tune_inner_P = 0, tune_lsq_chunks = 2432;
+    // scratch of the portfolio-grouped regression, owned by the simulation
+    double *d_lsq = nullptr;
+    size_t lsq_cap = 0;
     // profiling events: before the simulation kernel, after it, after the pricing
     // kernel, after the inner-default kernel
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -116,6 +124,22 @@ void forget_const_owner(const Sim *s);
 bool outer_supported(int E, int C, int CS, int G, int NPF, int *Ginst);
 cva_status launch_adjoint(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st);
 cva_status sum_columns_fp64(const double *part, int rows, int cols, double *out, cudaStream_t st);
+
+// One grouped least-squares job: group g reads features feat0 + g*feat_stride ([F][M])
+// and target t of it at targ0 + g*targ_stride + t*targ_tstride (nt targets share
+// the normal matrix); predictions go to pred0 + g*pred_stride + t*pred_tstride.
+struct LsqJob {
+    const float *feat0 = nullptr;
+    size_t feat_stride = 0;
+    const float *targ0 = nullptr;
+    size_t targ_stride = 0, targ_tstride = 0;
+    float *pred0 = nullptr;
+    size_t pred_stride = 0, pred_tstride = 0;
+    int F = 0, basis = 0, groups = 1, nt = 1, chunk_target = 0;
+    uint64_t M = 0;
+};
+cva_status lsq_launch(const LsqJob &j, double *scratch, size_t scratch_cap, double *coef_host, cudaStream_t st);
+size_t lsq_scratch_need(const LsqJob &j);
 
 // Regression (lsq.cu): least squares for `groups` dates at once; group g reads
 // features feat0 + g*feat_stride ([F][M]) and targets targ0 + g*targ_stride.

@@ -27,16 +27,19 @@ struct LsqArgs {
     int F, m, basis, chunks;
     uint32_t M, rows_per_chunk;
     double *part;         // [groups][chunks][NUT*16]
-    double *coef;         // [groups][m] centred basis
-    double *coef_raw;     // [groups][m] raw basis
+    double *coef;         // [groups][nt][m] centred basis
+    double *coef_raw;     // [groups][nt][m] raw basis
     int *status;          // [groups] dropped columns
+    int nt = 1;                 // target columns sharing one normal matrix
+    size_t targ_tstride = 0;    // floats between a group's targets
+    size_t pred_tstride = 0;    // floats between a group's predictions
 };
 
-// value of augmented column `col` at row k (col == m is the target)
+// value of augmented column `col` at row k (columns m..m+nt-1 are the targets)
 __device__ __forceinline__ float basis_value(const LsqArgs &a, const float *feat, const float *targ,
                                             int col, uint32_t k)
 {
-    if (col == a.m) return __ldg(targ + k);
+    if (col >= a.m) return __ldg(targ + (size_t)(col - a.m) * a.targ_tstride + k);
     if (col == 0) return 1.f;
     if (a.basis == CVA_BASIS_POLY2) {
         const float d = __ldg(feat + k) - __ldg(feat);
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram(LsqArgs a)
     const float *targ = a.targ0 + (size_t)g * a.targ_stride;
     const uint32_t r_begin = (uint32_t)chunk * a.rows_per_chunk;
     const uint32_t r_end = min(a.M, r_begin + a.rows_per_chunk);
-    const int mA = a.m + 1;
+    const int mA = a.m + a.nt;
 
     // this thread's 4x4 block (bi <= bj) and row group
     const int b = tid % NUT, rg = tid / NUT;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(256) lsq_solve(LsqArgs a)
     constexpr int NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2;
     __shared__ double blocks[NUT * 16];
     __shared__ double A[MP * MP];
-    const int g = blockIdx.x, tid = threadIdx.x, m = a.m, mA = m + 1;
+    const int g = blockIdx.x, tid = threadIdx.x, m = a.m, mA = m + a.nt;
     for (int e = tid; e < NUT * 16; e += blockDim.x) {
         double s = 0.0;
         const double *p = a.part + (size_t)g * a.chunks * NUT * 16 + e;
@@ -185,44 +188,47 @@ __global__ void __launch_bounds__(256) lsq_solve(LsqArgs a)
             }
         }
     }
-    for (int i = 0; i < m; ++i) {           // L y = D^{-1/2} b
-        double s = drop[i] ? 0.0 : A[i * MP + m] * sc[i];
-        for (int p = 0; p < i; ++p) s -= L[i * MP + p] * y[p];
-        y[i] = drop[i] ? 0.0 : s / L[i * MP + i];
-    }
-    double w[MP];
-    for (int i = m - 1; i >= 0; --i) {     // L^T z = y, w = D^{-1/2} z
-        double s = y[i];
-        for (int p = i + 1; p < m; ++p) s -= L[p * MP + i] * w[p];
-        w[i] = drop[i] ? 0.0 : s / L[i * MP + i];
-    }
-    for (int i = 0; i < m; ++i) w[i] *= sc[i];
-    double *co = a.coef + (size_t)g * m, *cr = a.coef_raw + (size_t)g * m;
-    for (int i = 0; i < m; ++i) co[i] = w[i];
     const float *feat = a.feat0 + (size_t)g * a.feat_stride;
-    if (a.basis == CVA_BASIS_POLY2) {
-        const double c = (double)feat[0];
-        cr[0] = w[0] - w[1] * c + w[2] * c * c;
-        cr[1] = w[1] - 2.0 * w[2] * c;
-        cr[2] = w[2];
-    } else {
-        double w0 = w[0];
-        for (int f = 0; f < a.F; ++f) {
-            const double c = (double)feat[(size_t)f * a.M];
-            w0 -= w[1 + f] * c;
-            cr[1 + f] = w[1 + f];
+    for (int t = 0; t < a.nt; ++t) {
+        const int rhs = m + t;
+        for (int i = 0; i < m; ++i) {           // L y = D^{-1/2} b
+            double s = drop[i] ? 0.0 : A[i * MP + rhs] * sc[i];
+            for (int p = 0; p < i; ++p) s -= L[i * MP + p] * y[p];
+            y[i] = drop[i] ? 0.0 : s / L[i * MP + i];
         }
-        cr[0] = w0;
+        double w[MP];
+        for (int i = m - 1; i >= 0; --i) {     // L^T z = y, w = D^{-1/2} z
+            double s = y[i];
+            for (int p = i + 1; p < m; ++p) s -= L[p * MP + i] * w[p];
+            w[i] = drop[i] ? 0.0 : s / L[i * MP + i];
+        }
+        for (int i = 0; i < m; ++i) w[i] *= sc[i];
+        double *co = a.coef + ((size_t)g * a.nt + t) * m, *cr = a.coef_raw + ((size_t)g * a.nt + t) * m;
+        for (int i = 0; i < m; ++i) co[i] = w[i];
+        if (a.basis == CVA_BASIS_POLY2) {
+            const double c = (double)feat[0];
+            cr[0] = w[0] - w[1] * c + w[2] * c * c;
+            cr[1] = w[1] - 2.0 * w[2] * c;
+            cr[2] = w[2];
+        } else {
+            double w0 = w[0];
+            for (int f = 0; f < a.F; ++f) {
+                const double c = (double)feat[(size_t)f * a.M];
+                w0 -= w[1 + f] * c;
+                cr[1 + f] = w[1 + f];
+            }
+            cr[0] = w0;
+        }
     }
     a.status[g] = dropped;
 }
 
 __global__ void __launch_bounds__(256) lsq_predict(LsqArgs a)
 {
-    const int g = blockIdx.y;
+    const int g = blockIdx.y, t = blockIdx.z;
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.M) return;
-    const double *co = a.coef + (size_t)g * a.m;
+    const double *co = a.coef + ((size_t)g * a.nt + t) * a.m;
     const float *feat = a.feat0 + (size_t)g * a.feat_stride;
     float acc = (float)co[0];
     if (a.basis == CVA_BASIS_POLY2) {
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(256) lsq_predict(LsqArgs a)
             acc = fmaf((float)co[1 + f], __ldg(fr + k) - __ldg(fr), acc);
         }
     }
-    a.pred0[(size_t)g * a.pred_stride + k] = acc;
+    a.pred0[(size_t)g * a.pred_stride + (size_t)t * a.pred_tstride + k] = acc;
 }
 
 // Library-owned scratch for the Gram partials and coefficients, per device.
@@ -250,31 +256,128 @@ LsqScratch g_lsq[64];
 
 }  // namespace
 
+// Launch the grouped regression with the given scratch ([groups] x (chunks x NUT x 16 +
+// 2 x nt x m) doubles + groups ints); chunk_target sets the blocks per launch.
+static size_t lsq_scratch_doubles(int groups, int m, int nt, uint64_t chunks, int NUT)
+{
+    return (size_t)groups * chunks * NUT * 16 + 2 * (size_t)groups * nt * m + (size_t)groups;
+}
+
+static int lsq_width(int m, int nt) { return (m + nt <= 4) ? 4 : (m + nt <= 12) ? 12 : (m + nt <= 32) ? 32 : 40; }
+
+static uint64_t lsq_chunks(uint64_t M, int groups, int chunk_target)
+{
+    const uint64_t max_chunks = (M + 1023) / 1024;
+    uint64_t chunks = ((uint64_t)chunk_target + groups - 1) / groups;
+    if (chunks > max_chunks) chunks = max_chunks;
+    return chunks < 1 ? 1 : chunks;
+}
+
+cva_status lsq_launch(const LsqJob &j, double *scratch, size_t scratch_cap, double *coef_host, cudaStream_t st)
+{
+    if (!j.feat0 || !j.targ0 || j.M == 0 || j.groups <= 0 || j.nt < 1)
+        return fail(CVA_EINVAL, "regress: bad arguments");
+    if (j.M > 0x7fffffffull) return fail(CVA_EINVAL, "regress: M too large");
+    if (j.basis != CVA_BASIS_LINEAR && j.basis != CVA_BASIS_POLY2) return fail(CVA_EINVAL, "regress: unknown basis");
+    const int m = (j.basis == CVA_BASIS_POLY2) ? 3 : j.F + 1;
+    if (j.F < 1) return fail(CVA_EINVAL, "regress: need one factor");
+    if (m + j.nt > 40) return fail(CVA_ENOTSUP, "regress: basis columns + targets must be <= 40");
+    const int MP = lsq_width(m, j.nt);
+    const int NUT = (MP / 4) * (MP / 4 + 1) / 2;
+    const uint64_t chunks = lsq_chunks(j.M, j.groups, j.chunk_target > 0 ? j.chunk_target : 2432);
+    if (lsq_scratch_doubles(j.groups, m, j.nt, chunks, NUT) > scratch_cap) return fail(CVA_ENOMEM, "regress: scratch too small");
+    LsqArgs a;
+    a.feat0 = j.feat0;
+    a.feat_stride = j.feat_stride;
+    a.targ0 = j.targ0;
+    a.targ_stride = j.targ_stride;
+    a.targ_tstride = j.targ_tstride;
+    a.pred0 = j.pred0;
+    a.pred_stride = j.pred_stride;
+    a.pred_tstride = j.pred_tstride;
+    a.nt = j.nt;
+    a.F = j.F;
+    a.m = m;
+    a.basis = j.basis;
+    a.chunks = (int)chunks;
+    a.M = (uint32_t)j.M;
+    a.rows_per_chunk = (uint32_t)((j.M + chunks - 1) / chunks);
+    a.part = scratch;
+    a.coef = a.part + (size_t)j.groups * chunks * NUT * 16;
+    a.coef_raw = a.coef + (size_t)j.groups * j.nt * m;
+    a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)j.groups * j.nt * m);
+    const dim3 ggrid((unsigned)chunks, (unsigned)j.groups);
+    switch (MP) {
+    case 4: lsq_gram<4, 1024><<<ggrid, kGramThreads, (size_t)1024 * 8 * sizeof(float), st>>>(a); break;
+    case 12: lsq_gram<12, 512><<<ggrid, kGramThreads, (size_t)512 * 16 * sizeof(float), st>>>(a); break;
+    case 32: lsq_gram<32, 256><<<ggrid, kGramThreads, (size_t)256 * 36 * sizeof(float), st>>>(a); break;
+    default: lsq_gram<40, 256><<<ggrid, kGramThreads, (size_t)256 * 44 * sizeof(float), st>>>(a); break;
+    }
+    CVA_CUDA_TRY(cudaGetLastError());
+    switch (MP) {
+    case 4: lsq_solve<4><<<j.groups, 256, 0, st>>>(a); break;
+    case 12: lsq_solve<12><<<j.groups, 256, 0, st>>>(a); break;
+    case 32: lsq_solve<32><<<j.groups, 256, 0, st>>>(a); break;
+    default: lsq_solve<40><<<j.groups, 256, 0, st>>>(a); break;
+    }
+    CVA_CUDA_TRY(cudaGetLastError());
+    if (j.pred0) {
+        lsq_predict<<<dim3((unsigned)((j.M + 255) / 256), (unsigned)j.groups, (unsigned)j.nt), 256, 0, st>>>(a);
+        CVA_CUDA_TRY(cudaGetLastError());
+    }
+    if (coef_host) {
+        std::vector<int> status(j.groups);
+        CVA_CUDA_TRY(cudaMemcpyAsync(coef_host, a.coef_raw, sizeof(double) * j.groups * j.nt * m,
+                                     cudaMemcpyDeviceToHost, st));
+        CVA_CUDA_TRY(cudaMemcpyAsync(status.data(), a.status, sizeof(int) * j.groups, cudaMemcpyDeviceToHost, st));
+        CVA_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int g = 0; g < j.groups; ++g)
+            if (status[g] != 0) return fail(CVA_ENUMERIC, "regress: rank-deficient normal equations");
+    }
+    return CVA_OK;
+}
+
+size_t lsq_scratch_need(const LsqJob &j)
+{
+    const int m = (j.basis == CVA_BASIS_POLY2) ? 3 : j.F + 1;
+    const int MP = lsq_width(m, j.nt);
+    const int NUT = (MP / 4) * (MP / 4 + 1) / 2;
+    return lsq_scratch_doubles(j.groups, m, j.nt, lsq_chunks(j.M, j.groups, j.chunk_target > 0 ? j.chunk_target : 2432), NUT);
+}
+
 cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const float *targ0,
                                size_t targ_stride, float *pred0, size_t pred_stride, int F,
                                uint64_t M, int basis, int groups, double *coef_host, cudaStream_t st)
 {
+    LsqJob j;
+    j.feat0 = feat0;
+    j.feat_stride = feat_stride;
+    j.targ0 = targ0;
+    j.targ_stride = targ_stride;
+    j.pred0 = pred0;
+    j.pred_stride = pred_stride;
+    j.F = F;
+    j.M = M;
+    j.basis = basis;
+    j.groups = groups;
     if (!feat0 || !targ0 || M == 0 || groups <= 0) return fail(CVA_EINVAL, "regress: bad arguments");
     if (M > 0x7fffffffull) return fail(CVA_EINVAL, "regress: M too large");
     if (basis != CVA_BASIS_LINEAR && basis != CVA_BASIS_POLY2) return fail(CVA_EINVAL, "regress: unknown basis");
-    const int m = (basis == CVA_BASIS_POLY2) ? 3 : F + 1;
-    if (basis == CVA_BASIS_LINEAR && (F < 1 || m + 1 > 32))
-        return fail(CVA_ENOTSUP, "regress: linear basis supports 1 <= F <= 30");
-    if (basis == CVA_BASIS_POLY2 && F < 1) return fail(CVA_EINVAL, "regress: need one factor");
-    const int MP = (m + 1 <= 4) ? 4 : 32;
-    const int NUT = (MP / 4) * (MP / 4 + 1) / 2;
-    const uint64_t max_chunks = (M + 1023) / 1024;
-    uint64_t chunks = (2432 + groups - 1) / groups;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks < 1) chunks = 1;
-    const uint32_t rows_per_chunk = (uint32_t)((M + chunks - 1) / chunks);
-
+    if (F < 1) return fail(CVA_EINVAL, "regress: need one factor");
+    if (basis == CVA_BASIS_LINEAR && F + 2 > 32) return fail(CVA_ENOTSUP, "regress: linear basis supports 1 <= F <= 30");
     int dev = 0;
     CVA_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CVA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lk(g_lsq_mu);
     LsqScratch &sc = g_lsq[dev];
-    const size_t need = (size_t)groups * chunks * NUT * 16 + 2 * (size_t)groups * m + groups;
+    const size_t need = lsq_scratch_need(j);
+    if (cap != cudaStreamCaptureStatusNone) {
+        // inside a stream capture the scratch must already be large enough: a graph keeps its address
+        if (sc.cap < need) return fail(CVA_EINVAL, "regress: call once before capturing so that the scratch exists");
+        return lsq_launch(j, sc.buf, sc.cap, coef_host, st);
+    }
     if (!sc.done) CVA_CUDA_TRY(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming));
     else CVA_CUDA_TRY(cudaStreamWaitEvent(st, sc.done, 0));
     if (sc.cap < need) {
@@ -288,55 +391,8 @@ cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const flo
             return fail(CVA_ENOMEM, "regress: scratch allocation failed");
         sc.cap = need;
     }
-    LsqArgs a;
-    a.feat0 = feat0;
-    a.feat_stride = feat_stride;
-    a.targ0 = targ0;
-    a.targ_stride = targ_stride;
-    a.pred0 = pred0;
-    a.pred_stride = pred_stride;
-    a.F = F;
-    a.m = m;
-    a.basis = basis;
-    a.chunks = (int)chunks;
-    a.M = (uint32_t)M;
-    a.rows_per_chunk = rows_per_chunk;
-    a.part = sc.buf;
-    a.coef = a.part + (size_t)groups * chunks * NUT * 16;
-    a.coef_raw = a.coef + (size_t)groups * m;
-    a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)groups * m);
-
-    const dim3 ggrid((unsigned)chunks, (unsigned)groups);
-    if (MP == 4) {
-        constexpr int TR = 1024;
-        const size_t sm = (size_t)TR * 8 * sizeof(float);
-        lsq_gram<4, TR><<<ggrid, kGramThreads, sm, st>>>(a);
-        CVA_CUDA_TRY(cudaGetLastError());
-        lsq_solve<4><<<groups, 256, 0, st>>>(a);
-    } else {
-        constexpr int TR = 256;
-        const size_t sm = (size_t)TR * 36 * sizeof(float);
-        lsq_gram<32, TR><<<ggrid, kGramThreads, sm, st>>>(a);
-        CVA_CUDA_TRY(cudaGetLastError());
-        lsq_solve<32><<<groups, 256, 0, st>>>(a);
-    }
-    CVA_CUDA_TRY(cudaGetLastError());
-    if (pred0) {
-        lsq_predict<<<dim3((unsigned)((M + 255) / 256), (unsigned)groups), 256, 0, st>>>(a);
-        CVA_CUDA_TRY(cudaGetLastError());
-    }
-    if (coef_host) {
-        CVA_CUDA_TRY(cudaMemcpyAsync(coef_host, a.coef_raw, sizeof(double) * groups * m,
-                                     cudaMemcpyDeviceToHost, st));
-        std::vector<int> status(groups);
-        CVA_CUDA_TRY(cudaMemcpyAsync(status.data(), a.status, sizeof(int) * groups,
-                                     cudaMemcpyDeviceToHost, st));
-        CVA_CUDA_TRY(cudaEventRecord(sc.done, st));
-        CVA_CUDA_TRY(cudaStreamSynchronize(st));
-        for (int g = 0; g < groups; ++g)
-            if (status[g] != 0) return fail(CVA_ENUMERIC, "regress: rank-deficient normal equations");
-        return CVA_OK;
-    }
+    cva_status r = lsq_launch(j, sc.buf, sc.cap, coef_host, st);
+    if (r != CVA_OK) return r;
     CVA_CUDA_TRY(cudaEventRecord(sc.done, st));
     return CVA_OK;
 }

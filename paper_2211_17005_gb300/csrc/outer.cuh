@@ -257,6 +257,14 @@ static std::mutex t_const_mu;
 static const Sim *t_owner[64] = {};
 static cudaEvent_t t_last[64] = {};
 
+static cudaError_t upload_consts(const Sim &s, cudaStream_t st)
+{
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_sim, s.d_const_img, sizeof(SimConsts), 0, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbolAsync(c_w, s.d_const_img + sizeof(SimConsts), sizeof(SimWeights), 0,
+                                   cudaMemcpyDeviceToDevice, st);
+}
+
 static void outer_forget(const Sim *s)
 {
     std::lock_guard<std::mutex> lk(t_const_mu);
@@ -284,20 +292,30 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.thr = s.d_thr;
     args.expo = s.d_expo;
     args.mtm = s.d_mtm;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CVA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
     std::lock_guard<std::mutex> lk(t_const_mu);
-    if (!t_last[dev]) CVA_CUDA_TRY(cudaEventCreateWithFlags(&t_last[dev], cudaEventDisableTiming));
-    else CVA_CUDA_TRY(cudaStreamWaitEvent(st, t_last[dev], 0));
-    if (t_owner[dev] != &s) {
-        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_sim, &s.consts, sizeof(SimConsts), 0, cudaMemcpyHostToDevice, st));
-        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_w, &s.weights, sizeof(SimWeights), 0, cudaMemcpyHostToDevice, st));
-        t_owner[dev] = &s;
+    if (capturing) {
+        // a captured graph uploads its own tables every time it runs
+        CVA_CUDA_TRY(upload_consts(s, st));
+        t_owner[dev] = nullptr;
+    } else {
+        if (!t_last[dev]) CVA_CUDA_TRY(cudaEventCreateWithFlags(&t_last[dev], cudaEventDisableTiming));
+        else CVA_CUDA_TRY(cudaStreamWaitEvent(st, t_last[dev], 0));
+        if (t_owner[dev] != &s) {
+            CVA_CUDA_TRY(upload_consts(s, st));
+            t_owner[dev] = &s;
+        }
     }
-    sim_kernel<E, C, CS><<<(args.M + 127u) / 128u, 128, 0, st>>>(args);
+    const unsigned sb = (unsigned)(s.tune_sim_block > 0 && s.tune_sim_block <= 128 ? s.tune_sim_block : 128);
+    const unsigned pb = (unsigned)(s.tune_price_block > 0 && s.tune_price_block <= 256 ? s.tune_price_block : 256);
+    sim_kernel<E, C, CS><<<(args.M + sb - 1) / sb, sb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
-    price_kernel<E, C, CS, G, NPF><<<dim3((args.M + 255u) / 256u, (unsigned)s.n + 1u), 256, 0, st>>>(args);
+    price_kernel<E, C, CS, G, NPF><<<dim3((args.M + pb - 1) / pb, (unsigned)s.n + 1u), pb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
-    CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
+    if (!capturing) CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
     return CVA_OK;
 }
 
@@ -334,8 +352,7 @@ cva_status adjoint_launch(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k
     if (!t_last[dev]) CVA_CUDA_TRY(cudaEventCreateWithFlags(&t_last[dev], cudaEventDisableTiming));
     else CVA_CUDA_TRY(cudaStreamWaitEvent(st, t_last[dev], 0));
     if (t_owner[dev] != &s) {
-        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_sim, &s.consts, sizeof(SimConsts), 0, cudaMemcpyHostToDevice, st));
-        CVA_CUDA_TRY(cudaMemcpyToSymbolAsync(c_w, &s.weights, sizeof(SimWeights), 0, cudaMemcpyHostToDevice, st));
+        CVA_CUDA_TRY(upload_consts(s, st));
         t_owner[dev] = &s;
     }
     adjoint_kernel<E, C, CS, G, KMAX, SMAX><<<(M + 127u) / 128u, 128, 0, st>>>(a);

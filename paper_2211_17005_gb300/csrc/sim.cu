@@ -217,7 +217,7 @@ cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.N = s.N;
     args.n = s.n;
     args.NPF = s.NPF;
-    int P = 8;
+    int P = (s.tune_inner_P >= 1 && s.tune_inner_P <= 8) ? s.tune_inner_P : 8;
     while (P > 1 && inner_smem(P, s.C, s.n) > 160 * 1024) P >>= 1;
     args.P = P;
     args.thr = s.d_thr;

@@ -1,0 +1,92 @@
+"""Batching: six portfolios of uneven size on one simulation, all (portfolio, date)
+regressions in one grouped launch, a CUDA graph of simulate + regress, and the
+autotuned tile shapes."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2211_17005_gb300 import workload as W
+from tests.gpu_helpers import compare_defaults, compare_targets
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2211_17005_gb300 import api as A, build
+    build.build()
+    oracle.build()
+    return A
+
+
+def test_six_portfolios_and_grouped_regression_match_oracle(api):
+    wl = W.make("batched", M=1024, N=16, n_steps=20)
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N, keep_defaults=True)
+    sim.run(wl.seed)
+    pred, coef = sim.regress_portfolios("linear", want_coef=True)
+    pred = pred.cpu().numpy()
+    xi = sim.targets().cpu().numpy()
+    idx = sim.defaults().cpu().numpy()
+    n = wl.grid.n_steps
+    for p, pf in enumerate(wl.portfolios):
+        o = oracle.simulate(wl.model, pf, wl.grid, 0, wl.M, wl.N, wl.seed,
+                            want=("features", "Lambda", "idx", "xi_bar"))
+        eps = oracle.exp_clocks(wl.seed, 0, wl.M, wl.N, wl.model.C)
+        skip, _, _ = compare_defaults(idx, o["idx"], o["Lambda"], eps, n)
+        cva0 = float(o["xi_bar"][0].mean())
+        compare_targets(xi[p], o["xi_bar"], skip, cva0)
+        for i in range(1, n):
+            _, p_or = oracle.lsq(oracle.linear_features(o["features"][i]), o["xi_bar"][i])
+            assert np.sqrt(np.mean((pred[p, i] - p_or) ** 2)) <= 1e-3 * cva0, (p, i)
+    # the shared normal matrix gives each portfolio its own coefficients
+    assert not np.allclose(coef[0, 5], coef[1, 5])
+    sim.close()
+
+
+def test_cuda_graph_replay_equals_eager(api):
+    wl = W.make("batched", M=4096, N=32, n_steps=20)
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N)
+    pred = torch.zeros((sim.n_pf, sim.n, sim.M), dtype=torch.float32, device="cuda")
+    sim.run(wl.seed)
+    sim.regress_portfolios("linear", pred=pred)       # eager: allocates the scratch
+    torch.cuda.synchronize()
+    ref_t = sim.targets().clone()
+    ref_p = pred.clone()
+    pred.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            sim.run(wl.seed, stream=s)
+            sim.regress_portfolios("linear", pred=pred, stream=s)
+    torch.cuda.synchronize()
+    sim.targets().zero_()
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(sim.targets(), ref_t)
+    assert torch.equal(pred, ref_p)
+    sim.close()
+
+
+def test_autotune_keeps_results(api):
+    wl = W.make("batched", M=8192, N=32, n_steps=20)
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N)
+    sim.run(wl.seed)
+    ref_t = sim.targets().clone()
+    ref_p, _ = sim.regress_portfolios("linear")
+    ref_p = ref_p.clone()
+    choice = sim.autotune(wl.seed, "linear")
+    assert choice["sim_block"] in (64, 128) and choice["price_block"] in (128, 256)
+    assert choice["inner_paths_per_block"] in (2, 4, 8)
+    sim.run(wl.seed)
+    p, _ = sim.regress_portfolios("linear")
+    torch.cuda.synchronize()
+    assert torch.equal(sim.targets(), ref_t)          # tile shapes do not change any path
+    scale = float(ref_p.abs().max())
+    assert float((p - ref_p).abs().max()) <= 1e-5 * scale
+    again = sim.autotune(wl.seed, "linear")
+    assert again["cached"] is True
+    sim.close()
