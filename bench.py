@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--lsq", action="store_true", help="least-squares regression instead of the workload's MLP")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
+    p.add_argument("--no-batched", action="store_true", help="skip the 6-portfolio CUDA-graph measurement")
     p.add_argument("--paths", type=int, default=None,
                    help="override the number of outer paths (small cases for profiling captures)")
     return p.parse_args()
@@ -380,6 +381,42 @@ def main():
                "adjoint_ms": float(np.median(t_a)), "smooth_forward_ms": float(np.median(t_f)),
                "ratio": float(np.median(t_a) / np.median(t_f))}
 
+    # ---- batched workload: 6 portfolios, all simulations and 120 x 6 regressions replayed as one CUDA graph ----
+    batched = None
+    if rank == 0 and not args.no_batched:
+        bwl = workload.make("batched", M=args.paths)
+        bsim = api.Simulation(bwl.model, bwl.portfolios, bwl.grid, bwl.M, bwl.N)
+        tiles = bsim.autotune(bwl.seed, "linear")
+        bpred = torch.zeros((bsim.n_pf, bsim.n, bsim.M), dtype=torch.float32, device="cuda")
+        bsim.run(bwl.seed)
+        bsim.regress_portfolios("linear", pred=bpred)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream()
+        with torch.cuda.stream(gs):
+            with torch.cuda.graph(graph, stream=gs):
+                bsim.run(bwl.seed, stream=gs)
+                bsim.regress_portfolios("linear", pred=bpred, stream=gs)
+        graph.replay()
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        g0.record(stream)
+        for _ in range(reps):
+            graph.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / reps
+        bn = bwl.grid.n_steps
+        batched = {"workload": describe(bwl), "regression": "least squares [1, Y] for 6 x 119 (portfolio, date) pairs, "
+                   "one grouped launch, shared normal matrices", "graph_ms": gms,
+                   "value": bwl.M * bwl.N * bn / (gms / 1e3), "unit": UNIT,
+                   "regression_samples_per_s": bwl.M * (bn - 1) * len(bwl.portfolios) / (gms / 1e3),
+                   "tiles": tiles, "replays": reps, "l2": "working set 48 GB > L2"}
+        bsim.close()
+        del bpred, graph
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         M_sample = 2048 if wl.name != "small" else wl.M
@@ -405,7 +442,8 @@ def main():
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
-               "mlp_roofline": mlp_roof, "adjoint_forward": adj, "cpu_baseline": cpu, "clocks": clk,
+               "mlp_roofline": mlp_roof, "adjoint_forward": adj, "batched": batched, "cpu_baseline": cpu,
+               "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
                "gpu_launches": 8 * args.steps}
