@@ -52,11 +52,12 @@ struct Layout {
     static constexpr int sW2t = sW2 + U * U * 2;                    // [U][U]
     static constexpr int sH = sW2t + U * U * 2;                     // [128][U]
     static constexpr int sA = sH + kRows * U * 2;                   // [2U][128]
-    static constexpr int sVec = sA + 2 * U * kRows * 2;             // floats
+    static constexpr int sP = sA + 2 * U * kRows * 2;               // [128][U+1] FP32 h2 * dout
+    static constexpr int sVec = sP + kRows * (U + 1) * 4;           // floats
     static constexpr int nVec = 3 * U + 2 + 2 * kIn + 4 * (U + 2) + 64;
     static constexpr int sMisc = sVec + nVec * 4;
     static constexpr int bytes = sMisc + 64;
-    static_assert((U + 2) * (U + 2) * 8 <= sVec - sH, "refit normal matrix must fit over H and A");
+    static_assert((U + 2) * (U + 2) * 8 <= sP - sH, "refit normal matrix must fit over H and A");
     static constexpr uint32_t tmem_cols = (U + 128 <= 256) ? 256 : 512;   // D at [0,U), DW at [U, U+128)
 };
 
@@ -119,7 +120,7 @@ struct Mlp {
 
     __device__ uint32_t saddr(int off) const { return umma::smem_u32(smem + off); }
 
-    __device__ bool barrier() { return umma::grid_barrier(a.bar_count, a.bar_gen, nblk, gen, a.err, kGridPolls); }
+    __device__ bool barrier() { return umma::flag_barrier(a.bar_count, nblk, gen, a.err, kGridPolls); }
 
     // issue D (+)= A B^T over K with A at `aoff` (rows 128, width K) and B at `boff`
     // (N rows, width K); thread 0 only
@@ -312,12 +313,12 @@ struct Mlp {
             ld16(16 * c, v);
             umma::tmem_wait_ld();
             float d[16];
+            float *prod = reinterpret_cast<float *>(smem + L::sP) + tid * (U + 1);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const float h2 = fmaxf(v[i] + b2[16 * c + i], 0.f);
                 d[i] = h2 > 0.f ? dout * w3[16 * c + i] : 0.f;
-                const float s = warp_sum(h2 * dout);     // dw3 contribution of this warp's rows
-                if (lane == 0) slot[16 * c + i] += s;
+                prod[16 * c + i] = h2 * dout;            // dw3 contribution of this row
             }
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
@@ -341,6 +342,12 @@ struct Mlp {
         }
         // GEMM3: dH1 pre-activation = dH2 W2 (B = W2^T rows)
         if (!run(0, L::sH, L::sW2t, U, U, false)) return false;
+        if (tid < U) {   // dw3[i] += sum over the tile's rows of h2[r][i] dout[r] (FP32, fixed order)
+            const float *prod = reinterpret_cast<const float *>(smem + L::sP) + tid;
+            float s = 0.f;
+            for (int r = 0; r < kRows; ++r) s += prod[r * (U + 1)];
+            gslot[tid] += s;
+        }
 #pragma unroll
         for (int c = 0; c < U / 16; ++c) {
             float v[16];
@@ -372,7 +379,7 @@ struct Mlp {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int col = 16 * c + i;
-                    if (col < U) P[L::oW2 + o * U + col] = v[i];
+                    if (col < U) P[L::oW2 + col * U + o] = v[i];     // column-major: coalesced over o
                     else if (col == U) P[L::ob2 + o] = v[i];
                 }
             }
@@ -386,7 +393,7 @@ struct Mlp {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     const int col = 16 * c + i;     // relative to X^T rows
-                    if (col < kIn) P[L::oW1 + i0 * kIn + col] = v[i];
+                    if (col < kIn) P[L::oW1 + col * U + i0] = v[i];   // column-major: coalesced over i0
                     else if (col == kIn) P[L::ob1 + i0] = v[i];
                 }
             }
@@ -408,8 +415,11 @@ struct Mlp {
     {
         const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
         for (int p = blockIdx.x * blockDim.x + tid; p < L::NP; p += nblk * blockDim.x) {
+            int q = p;   // position of parameter p in the (column-major) partial layout
+            if (p < L::ob1) q = L::oW1 + (p % kIn) * U + p / kIn;
+            else if (p >= L::oW2 && p < L::ob2) q = L::oW2 + ((p - L::oW2) % U) * U + (p - L::oW2) / U;
             float g = 0.f;
-            for (int b = 0; b < nblk; ++b) g += __ldcg(a.partial + (size_t)b * L::NP + p);
+            for (int b = 0; b < nblk; ++b) g += __ldcg(a.partial + (size_t)b * L::NP + q);
             if (step == 1 && a.grad_out) a.grad_out[p] = g;
             if (p >= L::oW1 && p < L::ob1 && (p % kIn) >= a.F) continue;   // padded inputs
             const float m = a.beta1 * a.adam_m[p] + (1.f - a.beta1) * g;
@@ -725,7 +735,7 @@ cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t 
     CVA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_train_kernel<64>, 128, L::bytes));
     int grid = 1;   // largest divisor of the tiles per batch that fits co-resident
     for (int g = 1; g <= tiles_per_batch; ++g)
-        if (tiles_per_batch % g == 0 && g <= sms * per_sm) grid = g;
+        if (tiles_per_batch % g == 0 && g <= sms * per_sm && g <= 256) grid = g;
     const int red_stride = (L::NP > (64 + 2) * (64 + 2) ? L::NP : (64 + 2) * (64 + 2));
     std::lock_guard<std::mutex> lk(g_mlp_mu);
     MlpWork &w = g_mlp[dev];
@@ -742,10 +752,10 @@ cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t 
         w.cap = need;
     }
     if (!w.bar) {
-        if (cudaMalloc(&w.bar, 2 * sizeof(unsigned)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: barrier");
+        if (cudaMalloc(&w.bar, 256 * sizeof(unsigned)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: barrier");
         if (cudaMalloc(&w.err, sizeof(int)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: status");
     }
-    CVA_CUDA_TRY(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), st));
+    CVA_CUDA_TRY(cudaMemsetAsync(w.bar, 0, 256 * sizeof(unsigned), st));
     CVA_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     MlpArgs a;
     a.feat = feat;

@@ -161,5 +161,38 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned 
     return s_ok != 0;
 }
 
+// Grid-wide barrier on per-block flags (cooperative launch): every block
+// publishes its generation with a release store, then its threads poll the
+// other blocks' flags in parallel with acquire loads; no atomic counter to
+// serialise on. Bounded like grid_barrier: a timeout records *err, returns false.
+__device__ __forceinline__ bool flag_barrier(unsigned *flags, unsigned nblocks, unsigned &gen, int *err,
+                                             uint32_t max_iter)
+{
+    __threadfence();   // every thread's global writes before the block's release
+    __syncthreads();
+    gen += 1u;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + blockIdx.x), "r"(gen) : "memory");
+    }
+    int ok = 1;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        uint32_t it = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flags + b) : "memory");
+            if ((int)(v - gen) >= 0) break;
+            if (++it > max_iter || *(volatile int *)err) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    __threadfence();
+    return __syncthreads_and(ok) != 0;
+}
+
 }  // namespace umma
 }  // namespace cva
