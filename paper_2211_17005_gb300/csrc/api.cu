@@ -596,8 +596,12 @@ cva_status cva_mlp_fit(const float *targets_dev, const float *features_dev, int 
                        void *stream)
 {
     if (!targets_dev || !features_dev || !params_dev) return fail(CVA_EINVAL, "mlp: NULL pointer");
-    return mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, epochs, lr, 0, params_dev, pred_dev,
-                          nullptr, loss_dev, reinterpret_cast<cudaStream_t>(stream));
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cva_status r = mlp_begin(st);
+    if (r == CVA_OK)
+        r = mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, epochs, lr, 0, params_dev, pred_dev,
+                           nullptr, loss_dev, st);
+    return r == CVA_OK ? mlp_finish(st) : r;
 }
 
 cva_status cva_mlp_first_gradient(const float *targets_dev, const float *features_dev, int F, uint64_t M,
@@ -605,8 +609,12 @@ cva_status cva_mlp_first_gradient(const float *targets_dev, const float *feature
                                   void *stream)
 {
     if (!targets_dev || !features_dev || !params_dev || !grad_dev) return fail(CVA_EINVAL, "mlp: NULL pointer");
-    return mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, 1, lr, 1, params_dev, nullptr,
-                          grad_dev, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cva_status r = mlp_begin(st);
+    if (r == CVA_OK)
+        r = mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, 1, lr, 1, params_dev, nullptr,
+                           grad_dev, nullptr, st);
+    return r == CVA_OK ? mlp_finish(st) : r;
 }
 
 cva_status cva_mlp_regress_all(const cva_sim *sim, int pf, int hidden, int n_batches, int epochs, float lr,
@@ -616,15 +624,15 @@ cva_status cva_mlp_regress_all(const cva_sim *sim, int pf, int hidden, int n_bat
     const Sim &s = *reinterpret_cast<const Sim *>(sim);
     if (pf < 0 || pf >= s.NPF) return fail(CVA_EINVAL, "portfolio index out of range");
     const size_t M = s.M;
-    for (int i = s.n - 1; i >= 1; --i) {
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cva_status r = mlp_begin(st);
+    for (int i = s.n - 1; i >= 1 && r == CVA_OK; --i) {
         const float *feat = s.d_features + (size_t)i * s.F * M;
         const float *targ = s.d_targets + ((size_t)pf * s.n + i) * M;
-        cva_status r = mlp_train_date(feat, s.F, targ, M, hidden, n_batches, epochs, lr, 0, params_dev,
-                                      pred_dev ? pred_dev + (size_t)i * M : nullptr, nullptr, nullptr,
-                                      reinterpret_cast<cudaStream_t>(stream));
-        if (r != CVA_OK) return r;
+        r = mlp_train_date(feat, s.F, targ, M, hidden, n_batches, epochs, lr, 0, params_dev,
+                           pred_dev ? pred_dev + (size_t)i * M : nullptr, nullptr, nullptr, st);
     }
-    return CVA_OK;
+    return r == CVA_OK ? mlp_finish(st) : r;
 }
 
 int cva_grad_num_params(int E, int C) { return 3 * E - 1 + 3 * C; }

@@ -7,23 +7,38 @@
 //     least squares on the last hidden layer (normal equations in FP64);
 //   * after every epoch the full-sample loss (output ReLU on) decides whether the
 //     parameters are the best so far.
-// Algorithm 2 (backward learning) calls this once per date, from the last date
+// Algorithm 2 (backward learning) runs this once per date, from the last date
 // down, each date starting from the previous date's best parameters.
 //
-// One cooperative launch per date. Every block owns 128-row tiles; per tile:
-//   GEMM1  D = X W1^T            (K = 32 padded inputs)
-//   GEMM2  D = H1 W2^T           (K = U)
-//   GEMM3  D = dH2 W2            (K = U)
-//   GEMMW  D = [dH2^T; dH1^T] [H1 | 1 | X | 1]   (K = 128 rows): dW2, db2, dW1, db1,
-//          accumulated in tensor memory over the block's tiles of a batch
-// with BF16 operands in shared memory and FP32 accumulators in tensor memory;
-// biases, ReLU, the output layer and the loss run on the CUDA cores in FP32.
-// Blocks exchange FP32 gradient partials through global memory; a bounded grid
-// barrier separates the reduction + Adam update from the next step.
+// Kernels of one date, in order on the caller's stream:
+//   mlp_stats_kernel   input standardisation (FP64 sums), Adam state reset
+//   mlp_train_kernel   one epoch of Adam steps on ONE thread-block cluster
+//   mlp_sweep_kernel   full-sample forward passes on all SMs: the epoch loss and
+//                      the best-parameter choice, the Gram matrix of the refit, or
+//                      the predictions
+//   mlp_refit_kernel   sum of the Gram partials, FP64 Cholesky, new (w3, b3)
+//
+// Every CTA runs two warpgroups, each owning one 128-row tile slot. Per tile:
+//   GEMM1  D = X W1^T                    (K = 32 padded inputs)
+//   GEMM2  D = H1 W2^T                   (K = U)
+//   GEMM3  D = dH2 W2                    (K = U; the W2 image read MN-major)
+//   GEMMW  DW (+)= [dH2 | dH1]^T [H1 | 1 | X | 1]   (K = the tile's 128 paths;
+//          both operands read MN-major from per-path rows)
+// so that every operand is written as 16-byte pieces of its path's row. BF16
+// operands in shared memory, FP32 accumulators in tensor memory; biases, ReLU,
+// the output layer and the loss in FP32 on the CUDA cores.
+//
+// One Adam step inside the cluster: each CTA writes its FP32 gradient partial
+// into its own shared memory; after a cluster barrier CTA c sums slice c of the
+// parameter vector over all CTAs' partials (distributed shared memory, fixed CTA
+// order), applies Adam to the slice and stores the new values into every CTA's
+// copy of the parameters; a second cluster barrier publishes them.
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <climits>
 #include <mutex>
+#include <string>
 
 #include "cva_internal.h"
 #include "umma.cuh"
@@ -32,51 +47,94 @@ namespace cva {
 
 namespace {
 
-constexpr int kRows = 128;      // rows per tile (tcgen05 M)
-constexpr int kIn = 32;         // padded input width
+constexpr int kRows = 128;        // rows per tile (tcgen05 M)
+constexpr int kIn = 32;           // padded input width
+constexpr int kThreads = 256;     // two warpgroups, one tile slot each
+constexpr int kMaxCluster = 16;
 constexpr uint32_t kMbarPolls = 1u << 26;
-constexpr uint32_t kGridPolls = 1u << 24;
+
+// byte offset of element c of row r in a 128-element-wide BF16 row buffer stored
+// as K-major core matrices (8 rows x 16 bytes): 16 core matrices per 8-row group
+__host__ __device__ constexpr uint32_t row_off(uint32_t r, uint32_t c)
+{
+    return (r >> 3) * 2048u + (c >> 3) * 128u + (r & 7u) * 16u + (c & 7u) * 2u;
+}
 
 template <int U>
 struct Layout {
+    static_assert(U == 64, "the operand rows [dH2 | dH1] and [H1 | 1 | X | 1] are 128 wide for U = 64");
     static constexpr int NP = 35 * U + U * U + 2;     // parameters
+    static constexpr int NPpad = (NP + 63) / 64 * 64;
     static constexpr int oW1 = 0, ob1 = kIn * U, oW2 = ob1 + U, ob2 = oW2 + U * U, ow3 = ob2 + U,
                          ob3 = ow3 + U, omu = ob3 + 1;
-    static constexpr int BROWS = U + 64;               // [H1^T | 1 | X^T | 1]
-    static constexpr int bOnes1 = U, bX = U + 16, bOnes2 = U + 48;
+    static constexpr int Z = U + 2;                   // refit: [h2 | 1] unknowns and the target column
+    // columns of the row buffers: B = [H1 | 1 0.. | X | 1 0..], A = [dH2 | dH1]
+    static constexpr int cOne1 = U, cX = U + 16, cOne2 = U + 48, cDH1 = U;
     // shared memory (bytes)
-    static constexpr int sX = 0;                                    // [128][32]
-    static constexpr int sB = sX + kRows * kIn * 2;                 // [BROWS][128]
-    static constexpr int sW1 = sB + BROWS * kRows * 2;              // [U][32]
-    static constexpr int sW2 = sW1 + U * kIn * 2;                   // [U][U]
-    static constexpr int sW2t = sW2 + U * U * 2;                    // [U][U]
-    static constexpr int sH = sW2t + U * U * 2;                     // [128][U]
-    static constexpr int sA = sH + kRows * U * 2;                   // [2U][128]
-    static constexpr int sP = sA + 2 * U * kRows * 2;               // [128][U+1] FP32 h2 * dout
-    static constexpr int sVec = sP + kRows * (U + 1) * 4;           // floats
-    static constexpr int nVec = 3 * U + 2 + 2 * kIn + 4 * (U + 2) + 64;
-    static constexpr int sMisc = sVec + nVec * 4;
-    static constexpr int bytes = sMisc + 64;
-    static_assert((U + 2) * (U + 2) * 8 <= sP - sH, "refit normal matrix must fit over H and A");
-    static constexpr uint32_t tmem_cols = (U + 128 <= 256) ? 256 : 512;   // D at [0,U), DW at [U, U+128)
+    static constexpr int sSlot = 65536;                         // slot s: A at s * sSlot, B at + 32768
+    static constexpr int sW1 = 2 * sSlot;                       // W1 image [U][32], K-major
+    static constexpr int sW2 = sW1 + U * kIn * 2;               // W2 image [U][U], K-major
+    static constexpr int sTh = sW2 + U * U * 2;                 // parameters, FP32, column order
+    static constexpr int sStage = sTh + NPpad * 4;              // [2][kIn + 1][128] FP32 inputs, target
+    static constexpr int sVec = sStage + 2 * (kIn + 1) * kRows * 4;   // mean[32], istd[32]
+    static constexpr int sGsl = sVec + 2 * kIn * 4;             // [8 warps][U + 2] output-layer gradients
+    static constexpr int sMom = sGsl + 8 * (U + 2) * 4;         // Adam moments of the owned slice
+    static constexpr int kSliceMax = (NP + 3) / 4;              // clusters of at least 4 CTAs
+    static constexpr int bytes_train = sMom + 2 * kSliceMax * 4;
+    static constexpr int bytes_sweep = sMom;
+    static constexpr uint32_t tmem_cols = 512;   // D of slot s at [64 s, 64 s + U), DW at [128 + 128 s, +128)
+
+    // The shared copy of the parameters and the gradient partials keep W1 and W2
+    // column by column (q order), so that the owner of a slice and the writers of
+    // the partials touch consecutive words; global memory keeps the row order (p).
+    __host__ __device__ static int q_of(int p)
+    {
+        if (p < ob1) return oW1 + (p % kIn) * U + p / kIn;
+        if (p >= oW2 && p < ob2) {
+            const int t = p - oW2;
+            return oW2 + (t % U) * U + t / U;
+        }
+        return p;
+    }
+    __host__ __device__ static int p_of(int q)
+    {
+        if (q < ob1) return oW1 + (q % U) * kIn + q / U;
+        if (q >= oW2 && q < ob2) {
+            const int t = q - oW2;
+            return oW2 + (t % U) * U + t / U;
+        }
+        return q;
+    }
 };
 
-struct MlpArgs {
-    const float *feat;      // [F][M] state at the date
-    const float *targ;      // [M]
+struct TrainArgs {
+    const float *feat, *targ;      // [F][M] state at the date, [M] targets
     int F;
     uint32_t M;
-    int n_batches, epochs, max_steps;   // max_steps > 0 stops after that many Adam steps (validation)
+    int tiles_per_batch, n_steps, step0, pos;   // batches 0..n_steps-1; Adam steps step0+1..; output ReLU
     float lr, beta1, beta2, eps;
-    float *params, *adam_m, *adam_v, *best;   // [NP]
-    uint16_t *img_w1, *img_w2, *img_w2t;      // BF16 operand images in the tile layout
-    float *partial;                            // [grid][NP]
-    double *red;                               // [grid][red_stride]
-    int red_stride;
-    float *pred;                               // [M] predictions (nullable)
-    float *grad_out;                           // [NP] gradient of the first step (nullable)
-    float *loss_out;                           // [epochs] full-sample losses (nullable)
-    unsigned *bar_count, *bar_gen;
+    float *params;                 // [NP] row order, in/out
+    float *adam_m, *adam_v;        // [NPpad] column order
+    const float *stats;            // mean[32], 1/std[32]
+    float *grad_out;               // [NP] row order: gradient of the date's first step (nullable)
+    int *err;
+};
+
+struct SweepArgs {
+    const float *feat, *targ;
+    int F;
+    uint32_t M;
+    int mode;                      // 0 loss, 1 Gram of the refit, 2 predictions
+    const float *theta;            // [NP] parameters of the pass, row order
+    const float *stats;
+    double *part;                  // per-CTA partials
+    unsigned *count;               // last-CTA ticket (mode 0)
+    double *best_loss;             // mode 0
+    float *best;                   // mode 0: receives theta when its loss is the lowest so far
+    float *loss_out;               // mode 0: [epochs] (nullable)
+    int epoch;
+    float *pred;                   // mode 2 (nullable)
+    float *params_out;             // mode 2: receives theta (nullable)
     int *err;
 };
 
@@ -87,162 +145,204 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
     return (uint32_t)bf16_bits(a) | ((uint32_t)bf16_bits(b) << 16);
 }
 
-template <int U>
-struct Mlp {
-    using L = Layout<U>;
-    const MlpArgs &a;
-    unsigned char *smem;
-    uint32_t tmem;
-    uint64_t *mbar;
-    uint32_t phase;
-    unsigned gen;
-    int nblk, tid, warp, lane;
-    float *b1, *b2, *w3, *misc, *mean, *istd, *gslot;   // gslot[4][U+2]: per-warp dw3, db3, dmu
+__device__ __forceinline__ uint4 pack8(const float *v)
+{
+    return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+}
 
-    __device__ Mlp(const MlpArgs &args, unsigned char *s) : a(args), smem(s)
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums of 16 columns over the 32 lanes of a warp by recursive halving: at each
+// level a lane keeps half of its columns and adds its partner's copy of them.
+// Lane l ends with the total of column (l >> 1) (lanes l and l ^ 1 agree).
+__device__ __forceinline__ float column_sums16(const float (&v)[16], int lane)
+{
+    float a8[8], a4[4], a2[2];
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float send = u16 ? v[i] : v[8 + i], keep = u16 ? v[8 + i] : v[i];
+        a8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = u8 ? a8[i] : a8[4 + i], keep = u8 ? a8[4 + i] : a8[i];
+        a4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = u4 ? a4[i] : a4[2 + i], keep = u4 ? a4[2 + i] : a4[i];
+        a2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const float send = u2 ? a2[0] : a2[1], keep = u2 ? a2[1] : a2[0];
+    const float a1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
+}
+
+template <int U>
+struct Net {
+    using L = Layout<U>;
+    unsigned char *smem;
+    uint32_t tmem = 0;
+    uint64_t *mbar;
+    uint32_t phase = 0;
+    int tid, warp, lane, slot, row;
+    const float *th, *mean, *istd;
+    float *stage;
+
+    __device__ Net(unsigned char *s, uint64_t *mbars) : smem(s)
     {
         tid = threadIdx.x;
         warp = tid >> 5;
         lane = tid & 31;
-        nblk = gridDim.x;
-        float *v = reinterpret_cast<float *>(smem + L::sVec);
-        b1 = v;
-        b2 = b1 + U;
-        w3 = b2 + U;
-        misc = w3 + U;             // [0] = b3, [1] = mu
-        mean = misc + 2;
+        slot = tid >> 7;
+        row = tid & 127;
+        mbar = mbars + slot;
+        th = reinterpret_cast<const float *>(smem + L::sTh);
+        mean = reinterpret_cast<const float *>(smem + L::sVec);
         istd = mean + kIn;
-        gslot = istd + kIn;
-        mbar = reinterpret_cast<uint64_t *>(smem + L::sMisc);
-        phase = 0;
-        gen = 0;
+        stage = reinterpret_cast<float *>(smem + L::sStage) + slot * (kIn + 1) * kRows;
     }
 
+    __device__ int offA() const { return slot * L::sSlot; }
+    __device__ int offB() const { return slot * L::sSlot + 32768; }
+    __device__ uint32_t dcol() const { return 64u * (uint32_t)slot; }
+    __device__ uint32_t wcol() const { return 128u + 128u * (uint32_t)slot; }
     __device__ uint32_t saddr(int off) const { return umma::smem_u32(smem + off); }
+    __device__ uint32_t taddr(uint32_t col) const { return tmem + ((uint32_t)((warp & 3) * 32) << 16) + col; }
+    __device__ void ld16(uint32_t col, float (&v)[16]) const { umma::tmem_ld16(taddr(col), v); }
 
-    __device__ bool barrier() { return umma::flag_barrier(a.bar_count, nblk, gen, a.err, kGridPolls); }
-
-    // issue D (+)= A B^T over K with A at `aoff` (rows 128, width K) and B at `boff`
-    // (N rows, width K); thread 0 only
-    __device__ void gemm(uint32_t dcol, int aoff, int boff, int K, int N, bool acc_in)
+    // the 128 threads of this slot
+    __device__ void wg_sync() const { asm volatile("bar.sync %0, 128;" ::"r"(1 + slot) : "memory"); }
+    __device__ bool wg_all(bool p) const
     {
-        const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-        const uint32_t id = umma::idesc_bf16_f32(kRows, (uint32_t)N);
-        for (int kk = 0; kk < K / 16; ++kk) {
-            const uint64_t ad = umma::smem_desc(saddr(aoff) + kk * 256u, 128u, sbo);
-            const uint64_t bd = umma::smem_desc(saddr(boff) + kk * 256u, 128u, sbo);
-            umma::mma_bf16(tmem + dcol, ad, bd, id, (acc_in || kk > 0) ? 1u : 0u);
-        }
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, %2, 128, p;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(r)
+            : "r"((uint32_t)p), "r"(1 + slot)
+            : "memory");
+        return r != 0;
     }
 
-    // operand writes done -> issue (thread 0) -> wait for completion; false on timeout
-    __device__ bool run(uint32_t dcol, int aoff, int boff, int K, int N, bool acc_in)
+    // one tensor-core step of this slot: operands written -> issue (row 0) ->
+    // completion; the result is the same for the whole slot
+    template <class Issue>
+    __device__ bool mma(Issue issue)
     {
         umma::fence_proxy_async();
         umma::fence_before_sync();
-        __syncthreads();
+        wg_sync();
         umma::fence_after_sync();
-        if (tid == 0) {
-            gemm(dcol, aoff, boff, K, N, acc_in);
+        if (row == 0) {
+            issue();
             umma::commit(mbar);
         }
-        const bool ok = umma::mbar_wait(mbar, phase, kMbarPolls);
+        const bool done = umma::mbar_wait(mbar, phase, kMbarPolls);
         phase ^= 1u;
         umma::fence_after_sync();
-        if (!ok) atomicExch(a.err, 2);
-        return ok;
+        return wg_all(done);
     }
 
-    __device__ uint32_t lane_addr(uint32_t col) const { return tmem + ((uint32_t)(warp * 32) << 16) + col; }
-
-    __device__ void ld16(uint32_t col, float (&v)[16]) { umma::tmem_ld16(lane_addr(col), v); }
-
-    // ---- operand staging ----
-    // tile rows [r0, r0+128): standardised inputs into X (row layout) and X^T (rows of B)
-    __device__ void load_tile(uint32_t r0, float &y)
+    // D = A B^T: A = K columns of the rows from column c0 (K-major), B = a K-major image [N][K]
+    __device__ void gemm_rows(uint32_t d, int a_off, int c0, int b_off, int K, int N, bool acc) const
     {
-        const uint32_t r = r0 + tid;
+        const uint32_t id = umma::idesc_bf16_f32(kRows, (uint32_t)N);
+        const uint32_t a0 = saddr(a_off) + (uint32_t)(c0 / 8) * 128u, b0 = saddr(b_off);
+        const uint32_t bsbo = (uint32_t)(K / 8) * 128u;
+        for (int kk = 0; kk < K / 16; ++kk)
+            umma::mma_bf16(tmem + d, umma::smem_desc(a0 + kk * 256u, 128u, 2048u),
+                           umma::smem_desc(b0 + kk * 256u, 128u, bsbo), id, (acc || kk > 0) ? 1u : 0u);
+    }
+
+    // D = A W2 (B[n][k] = W2[k][n]): the W2 image read MN-major
+    __device__ void gemm_rows_w2t(uint32_t d, int a_off) const
+    {
+        const uint32_t id = umma::idesc_bf16_f32(kRows, U) | umma::kMnMajorB;
+        const uint32_t a0 = saddr(a_off), b0 = saddr(L::sW2), lbo = (U / 8) * 128u;
+        for (int kk = 0; kk < U / 16; ++kk)
+            umma::mma_bf16(tmem + d, umma::smem_desc(a0 + kk * 256u, 128u, 2048u),
+                           umma::smem_desc(b0 + kk * 2u * lbo, lbo, 128u), id, kk > 0 ? 1u : 0u);
+    }
+
+    // D (+)= A^T B over the tile's 128 rows: the 128 columns of A's rows and the
+    // first N columns of B's rows, both read MN-major
+    __device__ void gemm_paths(uint32_t d, int a_off, int b_off, int N, bool acc) const
+    {
+        const uint32_t id = umma::idesc_bf16_f32(kRows, (uint32_t)N) | umma::kMnMajorA | umma::kMnMajorB;
+        const uint32_t a0 = saddr(a_off), b0 = saddr(b_off);
+        for (int kk = 0; kk < kRows / 16; ++kk)
+            umma::mma_bf16(tmem + d, umma::smem_desc(a0 + kk * 4096u, 2048u, 128u),
+                           umma::smem_desc(b0 + kk * 4096u, 2048u, 128u), id, (acc || kk > 0) ? 1u : 0u);
+    }
+
+    // ---- inputs ----
+    // copy this thread's row (features, target) of the tile at `path - row` into the staging area
+    __device__ void prefetch(const float *feat, const float *targ, uint32_t M, int F, uint32_t path) const
+    {
+        const uint32_t s = umma::smem_u32(stage);
+        for (int f = 0; f < F; ++f) umma::cp_async4(s + (uint32_t)(f * kRows + row) * 4u, feat + (size_t)f * M + path);
+        umma::cp_async4(s + (uint32_t)(kIn * kRows + row) * 4u, targ + path);
+        umma::cp_async_commit();
+    }
+
+    // standardised inputs of this thread's row into the X columns of B; returns the target
+    __device__ float stage_x(int F) const
+    {
+        umma::cp_async_wait_all();
         float x[kIn];
 #pragma unroll
-        for (int f = 0; f < kIn; ++f) x[f] = 0.f;
+        for (int f = 0; f < kIn; ++f) x[f] = f < F ? (stage[f * kRows + row] - mean[f]) * istd[f] : 0.f;
+        unsigned char *b = smem + offB();
 #pragma unroll
-        for (int f = 0; f < kIn; ++f)
-            if (f < a.F) x[f] = (__ldg(a.feat + (size_t)f * a.M + r) - mean[f]) * istd[f];
-        y = __ldg(a.targ + r);
-        unsigned char *sx = smem + L::sX, *sb = smem + L::sB;
+        for (int g = 0; g < kIn / 8; ++g) *reinterpret_cast<uint4 *>(b + row_off(row, L::cX + 8 * g)) = pack8(x + 8 * g);
+        return stage[kIn * kRows + row];
+    }
+
+    // constant columns of B (ones after H1 and after X, zeros beside them), both slots
+    __device__ void init_constants()
+    {
+        const uint4 one = make_uint4((uint32_t)bf16_bits(1.f), 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+        unsigned char *b = smem + offB();
+        *reinterpret_cast<uint4 *>(b + row_off(row, L::cOne1)) = one;
+        *reinterpret_cast<uint4 *>(b + row_off(row, L::cOne1 + 8)) = zero;
+        *reinterpret_cast<uint4 *>(b + row_off(row, L::cOne2)) = one;
+        *reinterpret_cast<uint4 *>(b + row_off(row, L::cOne2 + 8)) = zero;
+    }
+
+    // BF16 images of W1 and W2 from the shared parameters (all 256 threads)
+    __device__ void build_images()
+    {
+        const int o = tid & (U - 1), g = tid / U;   // 4 column groups of 8
+        float v[8];
 #pragma unroll
-        for (int g = 0; g < kIn / 8; ++g) {
-            uint4 v;
-            v.x = pack2(x[8 * g], x[8 * g + 1]);
-            v.y = pack2(x[8 * g + 2], x[8 * g + 3]);
-            v.z = pack2(x[8 * g + 4], x[8 * g + 5]);
-            v.w = pack2(x[8 * g + 6], x[8 * g + 7]);
-            *reinterpret_cast<uint4 *>(sx + umma::kmajor_offset(tid, 8 * g, kIn)) = v;
-        }
+        for (int k = 0; k < 8; ++k) v[k] = th[L::oW1 + (8 * g + k) * U + o];
+        *reinterpret_cast<uint4 *>(smem + L::sW1 + umma::kmajor_offset(o, 8 * g, kIn)) = pack8(v);
 #pragma unroll
-        for (int f = 0; f < kIn; ++f)
-            *reinterpret_cast<uint16_t *>(sb + umma::kmajor_offset(L::bX + f, tid, kRows)) = bf16_bits(x[f]);
-    }
-
-    // fixed rows of B: one row of ones after H1^T and after X^T, zeros elsewhere
-    __device__ void init_b_constants()
-    {
-        unsigned char *sb = smem + L::sB;
-        for (int i = tid; i < 16 * kRows; i += blockDim.x) {
-            const int rr = i / kRows, k = i % kRows;
-            const uint16_t one = bf16_bits(1.f), zero = 0;
-            *reinterpret_cast<uint16_t *>(sb + umma::kmajor_offset(L::bOnes1 + rr, k, kRows)) = rr == 0 ? one : zero;
-            *reinterpret_cast<uint16_t *>(sb + umma::kmajor_offset(L::bOnes2 + rr, k, kRows)) = rr == 0 ? one : zero;
+        for (int h = 0; h < 2; ++h) {
+            const int gg = g + 4 * h;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = th[L::oW2 + (8 * gg + k) * U + o];
+            *reinterpret_cast<uint4 *>(smem + L::sW2 + umma::kmajor_offset(o, 8 * gg, U)) = pack8(v);
         }
     }
 
-    // parameters from global memory into shared memory
-    __device__ void load_params(const float *P)
+    // ---- epilogues (thread = row of the tile) ----
+    // H1 = relu(D + b1) into B; the mask of h1 > 0 in m1
+    __device__ void epi1(uint32_t (&m1)[U / 32]) const
     {
-        const uint4 *g1 = reinterpret_cast<const uint4 *>(a.img_w1), *g2 = reinterpret_cast<const uint4 *>(a.img_w2),
-                    *g3 = reinterpret_cast<const uint4 *>(a.img_w2t);
-        uint4 *s1 = reinterpret_cast<uint4 *>(smem + L::sW1), *s2 = reinterpret_cast<uint4 *>(smem + L::sW2),
-              *s3 = reinterpret_cast<uint4 *>(smem + L::sW2t);
-        for (int i = tid; i < U * kIn * 2 / 16; i += blockDim.x) s1[i] = __ldcg(g1 + i);
-        for (int i = tid; i < U * U * 2 / 16; i += blockDim.x) {
-            s2[i] = __ldcg(g2 + i);
-            s3[i] = __ldcg(g3 + i);
-        }
-        for (int i = tid; i < U; i += blockDim.x) {
-            b1[i] = __ldcg(P + L::ob1 + i);
-            b2[i] = __ldcg(P + L::ob2 + i);
-            w3[i] = __ldcg(P + L::ow3 + i);
-        }
-        if (tid == 0) {
-            misc[0] = __ldcg(P + L::ob3);
-            misc[1] = __ldcg(P + L::omu);
-        }
-        __syncthreads();
-    }
-
-    // BF16 operand images of parameter p (grid-stride writers)
-    __device__ void write_image(int p, float v)
-    {
-        if (p < L::ob1) {
-            const int o = p / kIn, f = p % kIn;
-            a.img_w1[umma::kmajor_offset(o, f, kIn) / 2] = bf16_bits(v);
-        } else if (p >= L::oW2 && p < L::ob2) {
-            const int q = p - L::oW2, o = q / U, i = q % U;
-            a.img_w2[umma::kmajor_offset(o, i, U) / 2] = bf16_bits(v);
-            a.img_w2t[umma::kmajor_offset(i, o, U) / 2] = bf16_bits(v);
-        }
-    }
-
-    // ---- forward to the second hidden layer; h2 of this thread's row stays in TMEM ----
-    // returns the h1 > 0 mask bits in m1 and writes H1 (rows) and H1^T (rows of B)
-    __device__ bool forward12(uint32_t (&m1)[U / 32])
-    {
-        if (!run(0, L::sX, L::sW1, kIn, U, false)) return false;
-        unsigned char *sh = smem + L::sH, *sb = smem + L::sB;
+        unsigned char *b = smem + offB();
+        const float *b1 = th + L::ob1;
 #pragma unroll
         for (int c = 0; c < U / 16; ++c) {
             float v[16];
-            ld16(16 * c, v);
+            ld16(dcol() + 16 * c, v);
             umma::tmem_wait_ld();
             uint32_t bits = 0;
 #pragma unroll
@@ -252,547 +352,772 @@ struct Mlp {
             }
             if (c % 2 == 0) m1[c / 2] = bits;
             else m1[c / 2] |= bits << 16;
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                uint4 q;
-                q.x = pack2(v[8 * g], v[8 * g + 1]);
-                q.y = pack2(v[8 * g + 2], v[8 * g + 3]);
-                q.z = pack2(v[8 * g + 4], v[8 * g + 5]);
-                q.w = pack2(v[8 * g + 6], v[8 * g + 7]);
-                *reinterpret_cast<uint4 *>(sh + umma::kmajor_offset(tid, 16 * c + 8 * g, U)) = q;
-            }
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                *reinterpret_cast<uint16_t *>(sb + umma::kmajor_offset(16 * c + i, tid, kRows)) = bf16_bits(v[i]);
+            *reinterpret_cast<uint4 *>(b + row_off(row, 16 * c)) = pack8(v);
+            *reinterpret_cast<uint4 *>(b + row_off(row, 16 * c + 8)) = pack8(v + 8);
         }
-        return run(0, L::sH, L::sW2, U, U, false);
     }
 
-    // output of this thread's row from the second-layer accumulator
-    __device__ float output(int pos, float &outv)
+    // output of this thread's row from the second-layer accumulator: zeta (+ relu if pos) + mu
+    __device__ float output(int pos, float &outv) const
     {
-        float out = misc[0];
+        const float *b2 = th + L::ob2, *w3 = th + L::ow3;
+        float out = th[L::ob3];
 #pragma unroll
         for (int c = 0; c < U / 16; ++c) {
             float v[16];
-            ld16(16 * c, v);
+            ld16(dcol() + 16 * c, v);
             umma::tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i) out = fmaf(fmaxf(v[i] + b2[16 * c + i], 0.f), w3[16 * c + i], out);
         }
         outv = out;
-        return (pos ? fmaxf(out, 0.f) : out) + misc[1];
+        return (pos ? fmaxf(out, 0.f) : out) + th[L::omu];
     }
 
-    // warp sum of 32 lanes' values of one column, result in every lane
-    __device__ static float warp_sum(float v)
+    // dH2 = dout w3 (h2 > 0) into A; dw3 += column sums of h2 dout into this warp's slots
+    __device__ void back2(float dout, float *gsl) const
     {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        return v;
-    }
-
-    // one tile of forward + backward; weight gradients accumulate in TMEM columns
-    // [U, U+128), output-layer gradients in the per-warp slots
-    __device__ bool tile_step(uint32_t r0, int pos, float inv_batch, bool first)
-    {
-        float y;
-        load_tile(r0, y);
-        uint32_t m1[U / 32];
-        if (!forward12(m1)) return false;
-        float out;
-        const float pred = output(pos, out);
-        const float dpred = 2.f * (pred - y) * inv_batch;
-        const float dout = pos ? (out > 0.f ? dpred : 0.f) : dpred;
-        // dH2 = dout w3 (h2 > 0): rows into H (A of GEMM3), columns into A rows [0, U)
-        unsigned char *sh = smem + L::sH, *sa = smem + L::sA;
-        float *slot = gslot + warp * (U + 2);
+        unsigned char *a = smem + offA();
+        const float *b2 = th + L::ob2, *w3 = th + L::ow3;
 #pragma unroll
         for (int c = 0; c < U / 16; ++c) {
             float v[16];
-            ld16(16 * c, v);
+            ld16(dcol() + 16 * c, v);
             umma::tmem_wait_ld();
-            float d[16];
-            float *prod = reinterpret_cast<float *>(smem + L::sP) + tid * (U + 1);
+            float d[16], pr[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const float h2 = fmaxf(v[i] + b2[16 * c + i], 0.f);
                 d[i] = h2 > 0.f ? dout * w3[16 * c + i] : 0.f;
-                prod[16 * c + i] = h2 * dout;            // dw3 contribution of this row
+                pr[i] = h2 * dout;
             }
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                uint4 q;
-                q.x = pack2(d[8 * g], d[8 * g + 1]);
-                q.y = pack2(d[8 * g + 2], d[8 * g + 3]);
-                q.z = pack2(d[8 * g + 4], d[8 * g + 5]);
-                q.w = pack2(d[8 * g + 6], d[8 * g + 7]);
-                *reinterpret_cast<uint4 *>(sh + umma::kmajor_offset(tid, 16 * c + 8 * g, U)) = q;
-            }
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                *reinterpret_cast<uint16_t *>(sa + umma::kmajor_offset(16 * c + i, tid, kRows)) = bf16_bits(d[i]);
+            *reinterpret_cast<uint4 *>(a + row_off(row, 16 * c)) = pack8(d);
+            *reinterpret_cast<uint4 *>(a + row_off(row, 16 * c + 8)) = pack8(d + 8);
+            const float s = column_sums16(pr, lane);
+            if (!(lane & 1)) gsl[16 * c + (lane >> 1)] += s;
         }
-        {
-            const float s3 = warp_sum(dout), smu = warp_sum(dpred);
-            if (lane == 0) {
-                slot[U] += s3;
-                slot[U + 1] += smu;
-            }
-        }
-        // GEMM3: dH1 pre-activation = dH2 W2 (B = W2^T rows)
-        if (!run(0, L::sH, L::sW2t, U, U, false)) return false;
-        if (tid < U) {   // dw3[i] += sum over the tile's rows of h2[r][i] dout[r] (FP32, fixed order)
-            const float *prod = reinterpret_cast<const float *>(smem + L::sP) + tid;
-            float s = 0.f;
-            for (int r = 0; r < kRows; ++r) s += prod[r * (U + 1)];
-            gslot[tid] += s;
-        }
+    }
+
+    // dH1 = D (h1 > 0) into A
+    __device__ void back1(const uint32_t (&m1)[U / 32]) const
+    {
+        unsigned char *a = smem + offA();
 #pragma unroll
         for (int c = 0; c < U / 16; ++c) {
             float v[16];
-            ld16(16 * c, v);
+            ld16(dcol() + 16 * c, v);
             umma::tmem_wait_ld();
             const uint32_t bits = m1[c / 2] >> (16 * (c % 2));
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const float d1 = ((bits >> i) & 1u) ? v[i] : 0.f;
-                *reinterpret_cast<uint16_t *>(sa + umma::kmajor_offset(U + 16 * c + i, tid, kRows)) = bf16_bits(d1);
-            }
+            for (int i = 0; i < 16; ++i) v[i] = ((bits >> i) & 1u) ? v[i] : 0.f;
+            *reinterpret_cast<uint4 *>(a + row_off(row, L::cDH1 + 16 * c)) = pack8(v);
+            *reinterpret_cast<uint4 *>(a + row_off(row, L::cDH1 + 16 * c + 8)) = pack8(v + 8);
         }
-        // GEMMW: [dH2^T; dH1^T] x [H1^T | 1 | X^T | 1]^T, accumulated over the batch's tiles
-        static_assert(2 * U == kRows, "stacked weight-gradient GEMM needs 2U = 128");
-        return run(U, L::sA, L::sB, kRows, L::BROWS, !first);
     }
 
-    // write this block's gradient partials (TMEM weight gradients + output slots)
-    __device__ void write_partials()
+    // first two layers of the staged tile; D holds the second-layer pre-activation after it
+    __device__ bool forward12(uint32_t (&m1)[U / 32])
     {
-        float *P = a.partial + (size_t)blockIdx.x * L::NP;
-        if (warp < 2) {   // rows 0..U-1: dW2[o][:] at cols [0,U), db2[o] at col U
-            const int o = tid;
-#pragma unroll
-            for (int c = 0; c < U / 16 + 1; ++c) {
-                float v[16];
-                ld16(U + 16 * c, v);
+        if (!mma([&] { gemm_rows(dcol(), offB(), L::cX, L::sW1, kIn, U, false); })) return false;
+        epi1(m1);
+        return mma([&] { gemm_rows(dcol(), offB(), 0, L::sW2, U, U, false); });
+    }
+
+    // forward + backward of one tile; weight gradients accumulate in this slot's DW
+    __device__ bool train_tile(const TrainArgs &a, bool first, float inv_batch, bool has_next, uint32_t next_path,
+                               float *gsl)
+    {
+        const float y = stage_x(a.F);
+        if (has_next) prefetch(a.feat, a.targ, a.M, a.F, next_path + row);
+        uint32_t m1[U / 32];
+        if (!forward12(m1)) return false;
+        float out;
+        const float pred = output(a.pos, out);
+        const float dpred = 2.f * (pred - y) * inv_batch;
+        const float dout = a.pos ? (out > 0.f ? dpred : 0.f) : dpred;
+        back2(dout, gsl);
+        {
+            const float s3 = warp_sum(dout), smu = warp_sum(dpred);
+            if (lane == 0) {
+                gsl[U] += s3;
+                gsl[U + 1] += smu;
+            }
+        }
+        if (!mma([&] { gemm_rows_w2t(dcol(), offA()); })) return false;
+        back1(m1);
+        return mma([&] { gemm_paths(wcol(), offA(), offB(), kRows, !first); });
+    }
+
+    // this CTA's gradient partial (both slots' DW + the output-layer slots) into P, q order
+    __device__ void write_partial(float *P, float *gsl, bool h0, bool h1) const
+    {
+        const int q4 = warp & 3, wg = warp >> 2;
+        const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+        if (q4 < 2) {   // rows o < U: dW2[o][:] at columns [0, U), db2[o] at column U
+            const int o = q4 * 32 + lane;
+            const int k0 = wg ? 3 : 0, k1 = wg ? 5 : 3;
+            for (int k = k0; k < k1; ++k) {
+                float v0[16], v1[16];
+                umma::tmem_ld16(tmem + lanes + 128u + 16u * k, v0);
+                umma::tmem_ld16(tmem + lanes + 256u + 16u * k, v1);
                 umma::tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const int col = 16 * c + i;
-                    if (col < U) P[L::oW2 + col * U + o] = v[i];     // column-major: coalesced over o
-                    else if (col == U) P[L::ob2 + o] = v[i];
+                    const int col = 16 * k + i;
+                    const float g = (h0 ? v0[i] : 0.f) + (h1 ? v1[i] : 0.f);
+                    if (col < U) P[L::oW2 + col * U + o] = g;
+                    else if (col == U) P[L::ob2 + o] = g;
                 }
             }
-        } else {          // rows U..2U-1: dW1[i][:] at cols [U+16, U+48), db1[i] at col U+48
-            const int i0 = tid - U;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float v[16];
-                ld16(U + U + 16 + 16 * c, v);
+        } else {        // rows U + i: dW1[i][:] at columns [cX, cX + 32), db1[i] at column cOne2
+            const int i0 = (q4 - 2) * 32 + lane;
+            const int k0 = wg ? 7 : 5, k1 = wg ? 8 : 7;
+            for (int k = k0; k < k1; ++k) {
+                float v0[16], v1[16];
+                umma::tmem_ld16(tmem + lanes + 128u + 16u * k, v0);
+                umma::tmem_ld16(tmem + lanes + 256u + 16u * k, v1);
                 umma::tmem_wait_ld();
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const int col = 16 * c + i;     // relative to X^T rows
-                    if (col < kIn) P[L::oW1 + col * U + i0] = v[i];   // column-major: coalesced over i0
-                    else if (col == kIn) P[L::ob1 + i0] = v[i];
+                    const int f = 16 * k + i - L::cX;
+                    const float g = (h0 ? v0[i] : 0.f) + (h1 ? v1[i] : 0.f);
+                    if (f < kIn) P[L::oW1 + f * U + i0] = g;
+                    else if (f == kIn) P[L::ob1 + i0] = g;
                 }
             }
         }
+        if (tid < U + 2) {
+            float s = 0.f;
+            for (int w = 0; w < 8; ++w) s += gsl[w * (U + 2) + tid];
+            P[tid < U ? L::ow3 + tid : (tid == U ? L::ob3 : L::omu)] = s;
+        }
         __syncthreads();
-        for (int i = tid; i < U + 2; i += blockDim.x) {
-            const float s = gslot[i] + gslot[(U + 2) + i] + gslot[2 * (U + 2) + i] + gslot[3 * (U + 2) + i];
-            if (i < U) P[L::ow3 + i] = s;
-            else if (i == U) P[L::ob3] = s;
-            else P[L::omu] = s;
-        }
-        __syncthreads();   // every slot is read before any is cleared
-        for (int i = tid; i < 4 * (U + 2); i += blockDim.x) gslot[i] = 0.f;
-        __syncthreads();
-    }
-
-    // sum of the partials over blocks (fixed order), Adam, new images
-    __device__ void adam_update(int step)
-    {
-        const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
-        for (int p = blockIdx.x * blockDim.x + tid; p < L::NP; p += nblk * blockDim.x) {
-            int q = p;   // position of parameter p in the (column-major) partial layout
-            if (p < L::ob1) q = L::oW1 + (p % kIn) * U + p / kIn;
-            else if (p >= L::oW2 && p < L::ob2) q = L::oW2 + ((p - L::oW2) % U) * U + (p - L::oW2) / U;
-            float g = 0.f;
-            for (int b = 0; b < nblk; ++b) g += __ldcg(a.partial + (size_t)b * L::NP + q);
-            if (step == 1 && a.grad_out) a.grad_out[p] = g;
-            if (p >= L::oW1 && p < L::ob1 && (p % kIn) >= a.F) continue;   // padded inputs
-            const float m = a.beta1 * a.adam_m[p] + (1.f - a.beta1) * g;
-            const float v = a.beta2 * a.adam_v[p] + (1.f - a.beta2) * g * g;
-            a.adam_m[p] = m;
-            a.adam_v[p] = v;
-            const float th = __ldcg(a.params + p) - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
-            a.params[p] = th;
-            write_image(p, th);
-        }
-    }
-
-    // full-sample loss (output ReLU on) over this block's tiles, or the refit Gram
-    __device__ bool sweep(int mode /*0 loss, 1 gram, 2 predict*/, double &acc)
-    {
-        const uint32_t tiles = a.M / kRows;
-        bool first = true;
-        for (uint32_t t = blockIdx.x; t < tiles; t += nblk) {
-            const uint32_t r0 = t * kRows;
-            float y;
-            load_tile(r0, y);
-            uint32_t m1[U / 32];
-            if (!forward12(m1)) return false;
-            if (mode == 0 || mode == 2) {
-                float out;
-                const float pred = output(1, out);
-                if (mode == 2) a.pred[r0 + tid] = pred;
-                else acc += (double)((pred - y) * (pred - y));
-            } else {
-                // Z^T = [h2^T; 1; (y - mu)] into A rows [0, U+2), rows [U+2, 2U) zero
-                unsigned char *sa = smem + L::sA;
-#pragma unroll
-                for (int c = 0; c < U / 16; ++c) {
-                    float v[16];
-                    ld16(16 * c, v);
-                    umma::tmem_wait_ld();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        *reinterpret_cast<uint16_t *>(sa + umma::kmajor_offset(16 * c + i, tid, kRows)) =
-                            bf16_bits(fmaxf(v[i] + b2[16 * c + i], 0.f));
-                }
-                *reinterpret_cast<uint16_t *>(sa + umma::kmajor_offset(U, tid, kRows)) = bf16_bits(1.f);
-                *reinterpret_cast<uint16_t *>(sa + umma::kmajor_offset(U + 1, tid, kRows)) = bf16_bits(y - misc[1]);
-                for (int rr = U + 2; rr < 2 * U; ++rr)
-                    *reinterpret_cast<uint16_t *>(sa + umma::kmajor_offset(rr, tid, kRows)) = 0;
-                // G (+)= Z^T Z over this block's tiles, rows/cols [0, U+2) of an M=128, N=U+16 product
-                if (!run(U, L::sA, L::sA, kRows, U + 16, !first)) return false;
-            }
-            first = false;
-        }
-        if (mode == 1 && first) {   // block without tiles: zero Gram
-            for (int i = tid; i < (U + 2) * (U + 2); i += blockDim.x) a.red[(size_t)blockIdx.x * a.red_stride + i] = 0.0;
-        } else if (mode == 1) {
-            // every warp executes the collective loads; rows >= U+2 are discarded
-            for (int c = 0; c < (U + 16) / 16; ++c) {
-                float v[16];
-                ld16(U + 16 * c, v);
-                umma::tmem_wait_ld();
-                if (tid < U + 2)
-                    for (int i = 0; i < 16; ++i) {
-                        const int col = 16 * c + i;
-                        if (col < U + 2) a.red[(size_t)blockIdx.x * a.red_stride + tid * (U + 2) + col] = (double)v[i];
-                    }
-            }
-        }
-        return true;
+        for (int i = tid; i < 8 * (U + 2); i += kThreads) gsl[i] = 0.f;
     }
 };
 
+// common start of the train and sweep kernels: TMEM, mbarriers, parameters (q
+// order), standardisation, constant operand columns, weight images
 template <int U>
-__global__ void __launch_bounds__(128, 1) mlp_train_kernel(MlpArgs a)
+__device__ void net_setup(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *params, const float *stats,
+                          bool zero_a)
 {
     using L = Layout<U>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    Mlp<U> m(a, smem);
-    __shared__ uint32_t s_tmem;
-    __shared__ double s_red[128];
-    __shared__ int s_flag;
-
-    if (m.warp == 0) {
-        umma::tmem_alloc(&s_tmem, L::tmem_cols);
+    if (n.warp == 0) {
+        umma::tmem_alloc(s_tmem, L::tmem_cols);
         umma::tmem_relinquish();
     }
-    if (m.tid == 0) {
-        umma::mbar_init(m.mbar, 1);
+    if (n.tid == 0) {
+        umma::mbar_init(&s_mbar[0], 1);
+        umma::mbar_init(&s_mbar[1], 1);
         umma::fence_mbar_init();
     }
-    for (int i = m.tid; i < 4 * (U + 2); i += blockDim.x) m.gslot[i] = 0.f;
-    m.init_b_constants();
+    float *th = reinterpret_cast<float *>(n.smem + L::sTh);
+    for (int q = n.tid; q < L::NPpad; q += kThreads) th[q] = q < L::NP ? __ldg(params + L::p_of(q)) : 0.f;
+    float *vec = reinterpret_cast<float *>(n.smem + L::sVec);
+    if (n.tid < 2 * kIn) vec[n.tid] = __ldg(stats + n.tid);
+    float *gsl = reinterpret_cast<float *>(n.smem + L::sGsl);
+    for (int i = n.tid; i < 8 * (U + 2); i += kThreads) gsl[i] = 0.f;
+    if (zero_a) {
+        uint4 *a = reinterpret_cast<uint4 *>(n.smem + n.offA());
+        for (int i = n.row; i < 32768 / 16; i += kRows) a[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    n.init_constants();
+    __syncthreads();
+    n.build_images();
+    umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
-    m.tmem = s_tmem;
+    n.tmem = *s_tmem;
+}
 
-    const int nblk = gridDim.x;
-    bool ok = true;
-    // ---- start of the date: Adam state, images, input standardisation ----
-    for (int p = blockIdx.x * blockDim.x + m.tid; p < L::NP; p += nblk * blockDim.x) {
-        a.adam_m[p] = 0.f;
-        a.adam_v[p] = 0.f;
-        m.write_image(p, __ldcg(a.params + p));
-    }
-    {
-        // per-feature sums over this block's rows (FP64), then every block combines all
-        double s1[kIn], s2[kIn];
-        for (int f = 0; f < kIn; ++f) s1[f] = s2[f] = 0.0;
-        for (uint32_t r = blockIdx.x * blockDim.x + m.tid; r < a.M; r += nblk * blockDim.x)
-            for (int f = 0; f < a.F; ++f) {
-                const double x = (double)__ldg(a.feat + (size_t)f * a.M + r);
-                s1[f] += x;
-                s2[f] += x * x;
-            }
-        for (int f = 0; f < a.F; ++f) {
-            s_red[m.tid] = s1[f];
-            __syncthreads();
-            for (int s = 64; s > 0; s >>= 1) {
-                if (m.tid < s) s_red[m.tid] += s_red[m.tid + s];
-                __syncthreads();
-            }
-            if (m.tid == 0) a.red[(size_t)blockIdx.x * a.red_stride + f] = s_red[0];
-            __syncthreads();
-            s_red[m.tid] = s2[f];
-            __syncthreads();
-            for (int s = 64; s > 0; s >>= 1) {
-                if (m.tid < s) s_red[m.tid] += s_red[m.tid + s];
-                __syncthreads();
-            }
-            if (m.tid == 0) a.red[(size_t)blockIdx.x * a.red_stride + kIn + f] = s_red[0];
-            __syncthreads();
-        }
-    }
-    ok = m.barrier();
-    if (ok) {
-        if (m.tid < kIn) {
-            const int f = m.tid;
-            double t1 = 0.0, t2 = 0.0;
-            if (f < a.F)
-                for (int b = 0; b < nblk; ++b) {
-                    t1 += __ldcg(a.red + (size_t)b * a.red_stride + f);
-                    t2 += __ldcg(a.red + (size_t)b * a.red_stride + kIn + f);
-                }
-            const double mu = t1 / a.M, var = t2 / a.M - mu * mu;
-            m.mean[f] = f < a.F ? (float)mu : 0.f;
-            m.istd[f] = (f < a.F && var > 0.0) ? (float)(1.0 / sqrt(var)) : 0.f;
-        }
-        ok = m.barrier();   // everyone has read the sums before they are overwritten
-    }
-    if (ok) m.load_params(a.params);
+template <int U>
+__device__ void net_teardown(Net<U> &n)
+{
+    umma::cp_async_wait_all();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (n.warp == 0) umma::tmem_dealloc(n.tmem, Layout<U>::tmem_cols);
+}
 
-    const uint32_t per_batch = a.M / (uint32_t)a.n_batches;
-    const uint32_t tiles_per_batch = per_batch / kRows;
+// One epoch (or its first n_steps batches) of Adam on one cluster of CL >= 4 CTAs.
+// Batch b covers paths [b * P, (b + 1) * P), P = tiles_per_batch * 128; in each
+// step the cluster's 2 CL slots take the batch's tiles round-robin.
+template <int U>
+__global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a)
+{
+    using L = Layout<U>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    Net<U> n(smem, s_mbar);
+    const uint32_t rank = umma::cluster_rank(), CL = umma::cluster_size();
+    float *th = reinterpret_cast<float *>(smem + L::sTh);
+    float *part = reinterpret_cast<float *>(smem);   // slot 0's A rows, free between steps
+    float *gsl = reinterpret_cast<float *>(smem + L::sGsl);
+    float *mom = reinterpret_cast<float *>(smem + L::sMom);
+    const int S = (L::NP + (int)CL - 1) / (int)CL, lo = (int)rank * S, hi = min(L::NP, lo + S);
+
+    net_setup<U>(n, &s_tmem, s_mbar, a.params, a.stats, false);
+    for (int q = lo + n.tid; q < hi; q += kThreads) {
+        mom[q - lo] = a.adam_m[q];
+        mom[L::kSliceMax + q - lo] = a.adam_v[q];
+    }
+
+    const uint32_t per_batch = (uint32_t)a.tiles_per_batch * kRows;
     const float inv_batch = 1.f / (float)per_batch;
-    int pos = 0, step = 0;
-    double best = 1e300;
-    for (int epoch = 1; ok && epoch <= a.epochs; ++epoch) {
-        for (int bt = 0; ok && bt < a.n_batches; ++bt) {
-            bool first = true;
-            for (uint32_t t = blockIdx.x; ok && t < tiles_per_batch; t += nblk) {
-                ok = m.tile_step((uint32_t)bt * per_batch + t * kRows, pos, inv_batch, first);
-                first = false;
-            }
-            if (!ok) break;
-            if (first) {   // a block without a tile in this batch contributes zero
-                float *P = a.partial + (size_t)blockIdx.x * L::NP;
-                for (int i = m.tid; i < L::NP; i += blockDim.x) P[i] = 0.f;
-                __syncthreads();
-            } else {
-                m.write_partials();
-            }
-            if (!(ok = m.barrier())) break;
-            ++step;
-            m.adam_update(step);
-            if (!(ok = m.barrier())) break;
-            m.load_params(a.params);
-            if (a.max_steps > 0 && step >= a.max_steps) break;
+    const int span = 2 * (int)CL, my = 2 * (int)rank + n.slot;
+    const int my_rounds = my < a.tiles_per_batch ? (a.tiles_per_batch - 1 - my) / span + 1 : 0;
+    auto path_of = [&](int st, int rd) { return (uint32_t)st * per_batch + (uint32_t)(rd * span + my) * kRows; };
+    const bool h0 = 2 * (int)rank < a.tiles_per_batch, h1 = 2 * (int)rank + 1 < a.tiles_per_batch;
+    float *my_gsl = gsl + n.warp * (U + 2);
+
+    bool ok = true;
+    if (my_rounds > 0) n.prefetch(a.feat, a.targ, a.M, a.F, path_of(0, 0) + n.row);
+    for (int st = 0; st < a.n_steps; ++st) {
+        for (int rd = 0; rd < my_rounds && ok; ++rd) {
+            const bool last = rd + 1 == my_rounds;
+            const bool has_next = !last || st + 1 < a.n_steps;
+            const uint32_t next = last ? path_of(st + 1, 0) : path_of(st, rd + 1);
+            ok = n.train_tile(a, rd == 0, inv_batch, has_next, next, my_gsl);
+            if (!ok && n.row == 0) atomicExch(a.err, 2);
         }
-        if (!ok || (a.max_steps > 0 && step >= a.max_steps)) break;
-        if (epoch == a.epochs / 2) {
-            // closed-form least squares of (w3, b3) on the last hidden layer, mu fixed
-            double dummy = 0.0;
-            ok = m.sweep(1, dummy);
-            if (ok) ok = m.barrier();
-            if (ok && blockIdx.x == 0) {
-                constexpr int Z = U + 2;
-                double *G = reinterpret_cast<double *>(smem + L::sH);   // [Z][Z] FP64 over H and A
-                for (int i = m.tid; i < Z * Z; i += blockDim.x) {
-                    double s = 0.0;
-                    for (int b = 0; b < nblk; ++b) s += __ldcg(a.red + (size_t)b * a.red_stride + i);
-                    G[i] = s;
-                }
-                __syncthreads();
-                if (m.tid == 0) {
-                    // Jacobi-scaled Cholesky of the (U+1) x (U+1) normal matrix, in place
-                    constexpr int n1 = U + 1;
-                    double sc[n1];
-                    for (int i = 0; i < n1; ++i) sc[i] = G[i * Z + i] > 0.0 ? 1.0 / sqrt(G[i * Z + i]) : 0.0;
-                    for (int i = 0; i < n1; ++i)
-                        for (int j = 0; j < n1; ++j) G[i * Z + j] *= sc[i] * sc[j];
-                    for (int i = 0; i < n1; ++i) G[i * Z + n1] *= sc[i];
-                    bool singular = false;
-                    for (int j = 0; j < n1; ++j) {
-                        double d = G[j * Z + j];
-                        for (int p = 0; p < j; ++p) d -= G[j * Z + p] * G[j * Z + p];
-                        if (!(d > 1e-12)) {
-                            singular = true;
-                            d = 1.0;
-                        }
-                        d = sqrt(d);
-                        G[j * Z + j] = d;
-                        for (int i = j + 1; i < n1; ++i) {
-                            double s = G[i * Z + j];
-                            for (int p = 0; p < j; ++p) s -= G[i * Z + p] * G[j * Z + p];
-                            G[i * Z + j] = s / d;
-                        }
-                    }
-                    double y[n1];
-                    for (int i = 0; i < n1; ++i) {
-                        double s = G[i * Z + n1];
-                        for (int p = 0; p < i; ++p) s -= G[i * Z + p] * y[p];
-                        y[i] = s / G[i * Z + i];
-                    }
-                    for (int i = n1 - 1; i >= 0; --i) {
-                        double s = y[i];
-                        for (int p = i + 1; p < n1; ++p) s -= G[p * Z + i] * y[p];
-                        y[i] = s / G[i * Z + i];
-                    }
-                    if (!singular) {
-                        for (int i = 0; i < U; ++i) a.params[L::ow3 + i] = (float)(y[i] * sc[i]);
-                        a.params[L::ob3] = (float)(y[U] * sc[U]);
-                    }
-                }
-            }
-            if (ok) ok = m.barrier();
-            if (ok) m.load_params(a.params);
-            pos = 1;
-        }
-        // full-sample loss with the output ReLU; keep the best parameters
-        double acc = 0.0;
-        if (ok) ok = m.sweep(0, acc);
-        if (!ok) break;
-        s_red[m.tid] = acc;
+        umma::fence_before_sync();
         __syncthreads();
-        for (int s = 64; s > 0; s >>= 1) {
-            if (m.tid < s) s_red[m.tid] += s_red[m.tid + s];
-            __syncthreads();
+        umma::fence_after_sync();
+        n.write_partial(part, gsl, h0, h1);
+        umma::cluster_sync();   // every CTA's partial is complete
+
+        // the owned slice: sum over the cluster (CTA order), Adam, new values everywhere
+        const int step = a.step0 + st + 1;
+        const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
+        const uint32_t part_s = umma::smem_u32(part), th_s = umma::smem_u32(th);
+        for (int q = lo + n.tid; q < hi; q += kThreads) {
+            float gv[kMaxCluster];
+#pragma unroll
+            for (int c = 0; c < kMaxCluster; ++c)
+                gv[c] = (uint32_t)c < CL ? umma::ld_cluster_f32(umma::map_rank(part_s + 4u * (uint32_t)q, (uint32_t)c))
+                                         : 0.f;
+            float g = 0.f;
+#pragma unroll
+            for (int c = 0; c < kMaxCluster; ++c) g += gv[c];
+            if (step == 1 && a.grad_out) a.grad_out[L::p_of(q)] = g;
+            if (q < L::ob1 && q / U >= a.F) continue;   // padded inputs stay zero
+            float &m = mom[q - lo], &v = mom[L::kSliceMax + q - lo];
+            m = a.beta1 * m + (1.f - a.beta1) * g;
+            v = a.beta2 * v + (1.f - a.beta2) * g * g;
+            const float t = th[q] - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
+            for (uint32_t c = 0; c < CL; ++c) umma::st_cluster_f32(umma::map_rank(th_s + 4u * (uint32_t)q, c), t);
         }
-        if (m.tid == 0) a.red[(size_t)blockIdx.x * a.red_stride + 0] = s_red[0];
-        if (!(ok = m.barrier())) break;
-        if (m.tid == 0) {
-            double tot = 0.0;
-            for (int b = 0; b < nblk; ++b) tot += __ldcg(a.red + (size_t)b * a.red_stride);
-            tot /= (double)a.M;
-            s_flag = tot < best;
-            if (tot < best) best = tot;
-            if (blockIdx.x == 0 && a.loss_out) a.loss_out[epoch - 1] = (float)tot;
-        }
+        umma::cluster_sync();   // new parameters everywhere; partials read
+        n.build_images();
+        umma::fence_proxy_async();
         __syncthreads();
-        if (s_flag)
-            for (int p = blockIdx.x * blockDim.x + m.tid; p < L::NP; p += nblk * blockDim.x) a.best[p] = __ldcg(a.params + p);
-        if (!(ok = m.barrier())) break;   // the sums are read before the next epoch overwrites them
     }
-    // ---- end of the date: best parameters become the current ones; predictions ----
-    if (ok && a.max_steps == 0) {
-        for (int p = blockIdx.x * blockDim.x + m.tid; p < L::NP; p += nblk * blockDim.x) {
-            const float v = __ldcg(a.best + p);
-            a.params[p] = v;
-            m.write_image(p, v);
+    for (int q = lo + n.tid; q < hi; q += kThreads) {
+        a.params[L::p_of(q)] = th[q];
+        a.adam_m[q] = mom[q - lo];
+        a.adam_v[q] = mom[L::kSliceMax + q - lo];
+    }
+    umma::cluster_sync();   // no CTA leaves while another may address its shared memory
+    net_teardown<U>(n);
+}
+
+// Full-sample passes with fixed parameters, output ReLU on: the loss (mode 0), the
+// refit's Gram matrix of Z = [h2 | 1 | y - mu] (mode 1), the predictions (mode 2).
+template <int U>
+__global__ void __launch_bounds__(kThreads, 1) mlp_sweep_kernel(SweepArgs a)
+{
+    using L = Layout<U>;
+    constexpr int Z = L::Z;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ double s_red[8];
+    __shared__ int s_flag[2];
+    Net<U> n(smem, s_mbar);
+    net_setup<U>(n, &s_tmem, s_mbar, a.theta, a.stats, a.mode == 1);
+
+    const uint32_t tiles = a.M / kRows, stride = 2u * gridDim.x;
+    uint32_t t = 2u * blockIdx.x + (uint32_t)n.slot;
+    double acc = 0.0;
+    bool ok = true, first = true;
+    if (t < tiles) n.prefetch(a.feat, a.targ, a.M, a.F, t * kRows + n.row);
+    for (; t < tiles && ok; t += stride) {
+        const uint32_t nt = t + stride;
+        const float y = n.stage_x(a.F);
+        if (nt < tiles) n.prefetch(a.feat, a.targ, a.M, a.F, nt * kRows + n.row);
+        uint32_t m1[U / 32];
+        ok = n.forward12(m1);
+        if (ok && a.mode != 1) {
+            float out;
+            const float pred = n.output(1, out);
+            if (a.mode == 2) {
+                if (a.pred) a.pred[t * kRows + n.row] = pred;
+            } else {
+                acc += (double)((pred - y) * (pred - y));
+            }
+        } else if (ok) {
+            // row of Z into A: [relu(D + b2) | 1 | y - mu | 0 ...]
+            unsigned char *ar = smem + n.offA();
+            const float *b2 = n.th + L::ob2;
+#pragma unroll
+            for (int c = 0; c < U / 16; ++c) {
+                float v[16];
+                n.ld16(n.dcol() + 16 * c, v);
+                umma::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b2[16 * c + i], 0.f);
+                *reinterpret_cast<uint4 *>(ar + row_off(n.row, 16 * c)) = pack8(v);
+                *reinterpret_cast<uint4 *>(ar + row_off(n.row, 16 * c + 8)) = pack8(v + 8);
+            }
+            *reinterpret_cast<uint4 *>(ar + row_off(n.row, U)) =
+                make_uint4(pack2(1.f, y - n.th[L::omu]), 0u, 0u, 0u);
+            // G (+)= Z^T Z: M = the 128 columns of the rows (Z in the first U + 2), N = U + 16
+            ok = n.mma([&] { n.gemm_paths(n.wcol(), n.offA(), n.offA(), U + 16, !first); });
         }
-        ok = m.barrier();
-        if (ok) m.load_params(a.params);
-        double dummy = 0.0;
-        if (ok && a.pred) ok = m.sweep(2, dummy);
+        if (!ok && n.row == 0) atomicExch(a.err, 2);
+        first = false;
     }
     umma::fence_before_sync();
     __syncthreads();
-    if (m.warp == 0) umma::tmem_dealloc(m.tmem, L::tmem_cols);
+    umma::fence_after_sync();
+
+    if (a.mode == 0) {
+        double s = acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (n.lane == 0) s_red[n.warp] = s;
+        __syncthreads();
+        if (n.tid == 0) {
+            double b = 0.0;
+            for (int w = 0; w < 8; ++w) b += s_red[w];
+            a.part[blockIdx.x] = b;
+            __threadfence();
+            s_flag[0] = atomicAdd(a.count, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_flag[0]) {   // the last CTA: total loss, best parameters so far
+            __threadfence();
+            if (n.tid == 0) {
+                double tot = 0.0;
+                for (uint32_t b = 0; b < gridDim.x; ++b) tot += __ldcg(a.part + b);
+                tot /= (double)a.M;
+                if (a.loss_out) a.loss_out[a.epoch - 1] = (float)tot;
+                s_flag[1] = tot < *a.best_loss;
+                if (s_flag[1]) *a.best_loss = tot;
+                *a.count = 0u;
+            }
+            __syncthreads();
+            if (s_flag[1])
+                for (int p = n.tid; p < L::NP; p += kThreads) a.best[p] = __ldg(a.theta + p);
+        }
+    } else if (a.mode == 1) {   // this CTA's Gram (both slots) as FP64, rows/columns [0, Z)
+        const int q4 = n.warp & 3, wg = n.warp >> 2, R = q4 * 32 + n.lane;
+        const bool h0 = 2u * blockIdx.x < tiles, h1 = 2u * blockIdx.x + 1u < tiles;
+        double *P = a.part + (size_t)blockIdx.x * Z * Z;
+        if (q4 < 3) {
+            const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+            const int k0 = wg ? 3 : 0, k1 = wg ? 5 : 3;
+            for (int k = k0; k < k1; ++k) {
+                float v0[16], v1[16];
+                umma::tmem_ld16(n.tmem + lanes + 128u + 16u * k, v0);
+                umma::tmem_ld16(n.tmem + lanes + 256u + 16u * k, v1);
+                umma::tmem_wait_ld();
+                if (R < Z)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int c = 16 * k + i;
+                        if (c < Z) P[R * Z + c] = (h0 ? (double)v0[i] : 0.0) + (h1 ? (double)v1[i] : 0.0);
+                    }
+            }
+        }
+    } else if (blockIdx.x == 0 && a.params_out) {
+        for (int p = n.tid; p < L::NP; p += kThreads) a.params_out[p] = __ldg(a.theta + p);
+    }
+    net_teardown<U>(n);
 }
 
+// Refit of (w3, b3) at epoch floor(E/2): block i sums row i of the CTAs' Gram
+// partials (fixed order); the last block solves the Jacobi-scaled normal
+// equations of [h2 | 1] (w3, b3) = y - mu by FP64 Cholesky. A numerically
+// singular system keeps the old (w3, b3).
+template <int U>
+__global__ void __launch_bounds__(128) mlp_refit_kernel(const double *part, int nparts, double *G, unsigned *count,
+                                                        float *params)
+{
+    using L = Layout<U>;
+    constexpr int Z = L::Z, n1 = U + 1;
+    __shared__ double A[Z * Z];
+    __shared__ double sc[n1], xv[n1];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int i = blockIdx.x;
+    for (int c = tid; c < Z; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += __ldg(part + (size_t)b * Z * Z + i * Z + c);
+        G[i * Z + c] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int e = tid; e < Z * Z; e += blockDim.x) A[e] = __ldcg(G + e);
+    if (tid == 0) *count = 0u;
+    __syncthreads();
+    for (int j = tid; j < n1; j += blockDim.x) sc[j] = A[j * Z + j] > 0.0 ? 1.0 / sqrt(A[j * Z + j]) : 0.0;
+    __syncthreads();
+    for (int e = tid; e < n1 * (n1 + 1); e += blockDim.x) {
+        const int r = e / (n1 + 1), c = e % (n1 + 1);
+        A[r * Z + c] *= sc[r] * (c < n1 ? sc[c] : 1.0);
+    }
+    __syncthreads();
+    bool singular = false;
+    for (int j = 0; j < n1; ++j) {
+        double d = A[j * Z + j];
+        if (!(d > 1e-12)) {
+            singular = true;
+            d = 1.0;
+        }
+        d = sqrt(d);
+        __syncthreads();
+        if (tid == 0) A[j * Z + j] = d;
+        for (int r = j + 1 + tid; r < n1; r += blockDim.x) A[r * Z + j] /= d;
+        __syncthreads();
+        const int m = n1 - j - 1;
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const int r = j + 1 + e / m, c = j + 1 + e % m;
+            if (c <= r) A[r * Z + c] -= A[r * Z + j] * A[c * Z + j];
+        }
+        __syncthreads();
+    }
+    if (tid < 32) {
+        for (int r = 0; r < n1; ++r) {   // L y = b
+            double s = 0.0;
+            for (int p = lane; p < r; p += 32) s += A[r * Z + p] * xv[p];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) xv[r] = (A[r * Z + n1] - s) / A[r * Z + r];
+            __syncwarp();
+        }
+        for (int r = n1 - 1; r >= 0; --r) {   // L^T x = y
+            double s = 0.0;
+            for (int p = r + 1 + lane; p < n1; p += 32) s += A[p * Z + r] * xv[p];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) xv[r] = (xv[r] - s) / A[r * Z + r];
+            __syncwarp();
+        }
+        if (!singular)
+            for (int r = lane; r < n1; r += 32) params[r < U ? L::ow3 + r : L::ob3] = (float)(xv[r] * sc[r]);
+    }
+}
+
+// Start of a date: FP64 feature sums -> mean and 1/std (population), Adam state
+// zero, best loss +inf, best parameters = the starting ones.
+__global__ void __launch_bounds__(256) mlp_stats_kernel(const float *feat, int F, uint32_t M, double *part,
+                                                        unsigned *count, float *stats, float *adam, int n_adam,
+                                                        const float *params, float *best, int np, double *best_loss)
+{
+    __shared__ double red[2][8];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int f = 0; f < F; ++f) {
+        double s1 = 0.0, s2 = 0.0;
+        for (uint32_t r = blockIdx.x * 256u + tid; r < M; r += gridDim.x * 256u) {
+            const double x = (double)__ldg(feat + (size_t)f * M + r);
+            s1 += x;
+            s2 += x * x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            red[0][warp] = s1;
+            red[1][warp] = s2;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int w = 0; w < 8; ++w) {
+                t1 += red[0][w];
+                t2 += red[1][w];
+            }
+            part[blockIdx.x * 64 + f] = t1;
+            part[blockIdx.x * 64 + 32 + f] = t2;
+        }
+        __syncthreads();
+    }
+    for (int i = blockIdx.x * 256 + tid; i < n_adam; i += gridDim.x * 256) adam[i] = 0.f;
+    for (int i = blockIdx.x * 256 + tid; i < np; i += gridDim.x * 256) best[i] = __ldg(params + i);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid < kIn) {
+        const int f = tid;
+        double t1 = 0.0, t2 = 0.0;
+        if (f < F)
+            for (uint32_t b = 0; b < gridDim.x; ++b) {
+                t1 += __ldcg(part + b * 64 + f);
+                t2 += __ldcg(part + b * 64 + 32 + f);
+            }
+        const double mu = t1 / M, var = t2 / M - mu * mu;
+        stats[f] = f < F ? (float)mu : 0.f;
+        stats[kIn + f] = (f < F && var > 0.0) ? (float)(1.0 / sqrt(var)) : 0.f;
+    }
+    if (tid == 0) {
+        *best_loss = 1e300;
+        *count = 0u;
+    }
+}
+
+// ---- host side ----
 struct MlpWork {
-    float *buf = nullptr;
-    size_t cap = 0;
-    unsigned *bar = nullptr;
+    void *buf = nullptr;
+    size_t cap = 0;          // bytes
+    unsigned *count = nullptr;
     int *err = nullptr;
+    bool attrs = false;
+    int max_cluster = 0;     // 16 when a 16-CTA cluster of the train kernel fits, else 8
 };
 std::mutex g_mlp_mu;
 MlpWork g_mlp[64];
 
-}  // namespace
+struct MlpPlan {
+    float *adam, *best, *stats;
+    double *best_loss, *part, *G;
+    int sweep_grid, stats_grid, cluster;
+};
 
-int mlp_num_params(int U) { return 35 * U + U * U + 2; }
-
-cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t M, int U, int n_batches,
-                          int epochs, float lr, int max_steps, float *params_dev, float *pred_dev,
-                          float *grad_out_dev, float *loss_out_dev, cudaStream_t st)
+cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, cudaStream_t st, MlpWork *&wout,
+                       MlpPlan &pl)
 {
-    if (U != 64) return fail(CVA_ENOTSUP, "mlp: hidden width 64 is compiled");
-    if (F < 1 || F > kIn) return fail(CVA_EINVAL, "mlp: need 1 <= F <= 32 inputs");
-    if (n_batches < 1 || epochs < 1) return fail(CVA_EINVAL, "mlp: need batches >= 1, epochs >= 1");
-    if (M % ((uint64_t)n_batches * kRows) != 0 || M > 0x7fffffffull)
-        return fail(CVA_EINVAL, "mlp: M must be a multiple of 128 * batches");
     using L = Layout<64>;
-    const int tiles_per_batch = (int)(M / n_batches / kRows);
-    int dev = 0, sms = 0;
-    CVA_CUDA_TRY(cudaGetDevice(&dev));
-    CVA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
-    static bool attr = false;
-    if (!attr) {
-        CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::bytes));
-        attr = true;
-    }
-    int per_sm = 0;
-    CVA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_train_kernel<64>, 128, L::bytes));
-    int grid = 1;   // largest divisor of the tiles per batch that fits co-resident
-    for (int g = 1; g <= tiles_per_batch; ++g)
-        if (tiles_per_batch % g == 0 && g <= sms * per_sm && g <= 256) grid = g;
-    const int red_stride = (L::NP > (64 + 2) * (64 + 2) ? L::NP : (64 + 2) * (64 + 2));
-    std::lock_guard<std::mutex> lk(g_mlp_mu);
     MlpWork &w = g_mlp[dev];
-    auto al = [](size_t n) { return (n + 63) & ~(size_t)63; };   // 256-byte aligned pieces (in floats)
-    const size_t nNP = al(L::NP), nPart = al((size_t)grid * L::NP), nRed = al(2 * (size_t)grid * red_stride),
-                 nImg = al((64 * kIn + 2 * 64 * 64) / 2);
-    const size_t need = 3 * nNP + nPart + nRed + nImg;
+    if (!w.attrs) {
+        CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          L::bytes_train));
+        CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel<64>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_sweep_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          L::bytes_sweep));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(16);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = L::bytes_train;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n16 = 0;
+        if (cudaOccupancyMaxActiveClusters(&n16, mlp_train_kernel<64>, &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            n16 = 0;
+        }
+        w.max_cluster = n16 >= 1 ? 16 : 8;
+        w.attrs = true;
+    }
+    const uint64_t tiles = M / kRows;
+    const int rounds = (int)((tiles + 2 * (uint64_t)sms - 1) / (2 * (uint64_t)sms));
+    pl.sweep_grid = (int)((tiles + 2 * (uint64_t)rounds - 1) / (2 * (uint64_t)rounds));
+    pl.stats_grid = sms;
+    int cl = 4;
+    while (cl < w.max_cluster && 2 * cl < tiles_per_batch) cl *= 2;
+    pl.cluster = cl;
+    constexpr int Z = L::Z;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_adam = al(2 * (size_t)L::NPpad * 4), b_best = al((size_t)L::NPpad * 4), b_stats = al(64 * 4),
+                 b_bl = al(8), b_G = al((size_t)Z * Z * 8);
+    size_t nparts = (size_t)pl.sweep_grid * Z * Z;
+    if ((size_t)pl.stats_grid * 64 > nparts) nparts = (size_t)pl.stats_grid * 64;
+    const size_t b_part = al(nparts * 8);
+    const size_t need = b_adam + b_best + b_stats + b_bl + b_G + b_part;
     if (w.cap < need) {
         CVA_CUDA_TRY(cudaStreamSynchronize(st));
         if (w.buf) cudaFree(w.buf);
         w.buf = nullptr;
         w.cap = 0;
-        if (cudaMalloc(&w.buf, need * sizeof(float)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: workspace");
+        if (cudaMalloc(&w.buf, need) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: workspace");
         w.cap = need;
     }
-    if (!w.bar) {
-        if (cudaMalloc(&w.bar, 256 * sizeof(unsigned)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: barrier");
+    if (!w.count) {
+        if (cudaMalloc(&w.count, 4 * sizeof(unsigned)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: counters");
         if (cudaMalloc(&w.err, sizeof(int)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: status");
     }
-    CVA_CUDA_TRY(cudaMemsetAsync(w.bar, 0, 256 * sizeof(unsigned), st));
+    char *p = static_cast<char *>(w.buf);
+    pl.adam = reinterpret_cast<float *>(p);
+    p += b_adam;
+    pl.best = reinterpret_cast<float *>(p);
+    p += b_best;
+    pl.stats = reinterpret_cast<float *>(p);
+    p += b_stats;
+    pl.best_loss = reinterpret_cast<double *>(p);
+    p += b_bl;
+    pl.G = reinterpret_cast<double *>(p);
+    p += b_G;
+    pl.part = reinterpret_cast<double *>(p);
+    wout = &w;
+    return CVA_OK;
+}
+
+// validation shared by every entry
+cva_status mlp_check_args(int F, uint64_t M, int U, int n_batches, int epochs)
+{
+    if (U != 64) return fail(CVA_ENOTSUP, "mlp: hidden width 64 is compiled");
+    if (F < 1 || F > kIn) return fail(CVA_EINVAL, "mlp: need 1 <= F <= 32 inputs");
+    if (n_batches < 1 || epochs < 1) return fail(CVA_EINVAL, "mlp: need batches >= 1, epochs >= 1");
+    if (M == 0 || M % ((uint64_t)n_batches * kRows) != 0 || M > 0x7fffffffull)
+        return fail(CVA_EINVAL, "mlp: M must be a positive multiple of 128 * batches");
+    return CVA_OK;
+}
+
+}  // namespace
+
+int mlp_num_params(int U) { return 35 * U + U * U + 2; }
+
+cva_status mlp_begin(cudaStream_t st)
+{
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    MlpWork &w = g_mlp[dev];
+    if (!w.count) {
+        if (cudaMalloc(&w.count, 4 * sizeof(unsigned)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: counters");
+        if (cudaMalloc(&w.err, sizeof(int)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: status");
+    }
+    CVA_CUDA_TRY(cudaMemsetAsync(w.count, 0, 4 * sizeof(unsigned), st));
     CVA_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-    MlpArgs a;
-    a.feat = feat;
-    a.targ = targ;
-    a.F = F;
-    a.M = (uint32_t)M;
-    a.n_batches = n_batches;
-    a.epochs = epochs;
-    a.max_steps = max_steps;
-    a.lr = lr;
-    a.beta1 = 0.9f;
-    a.beta2 = 0.999f;
-    a.eps = 1e-8f;
-    a.params = params_dev;
-    a.adam_m = w.buf;
-    a.adam_v = a.adam_m + nNP;
-    a.best = a.adam_v + nNP;
-    a.partial = a.best + nNP;
-    a.red = reinterpret_cast<double *>(a.partial + nPart);
-    a.red_stride = red_stride;
-    uint16_t *img = reinterpret_cast<uint16_t *>(a.partial + nPart + nRed);
-    a.img_w1 = img;
-    a.img_w2 = img + 64 * kIn;
-    a.img_w2t = a.img_w2 + 64 * 64;
-    a.pred = pred_dev;
-    a.grad_out = grad_out_dev;
-    a.loss_out = loss_out_dev;
-    a.bar_count = w.bar;
-    a.bar_gen = w.bar + 1;
-    a.err = w.err;
-    void *kargs[] = {&a};
-    CVA_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)mlp_train_kernel<64>, dim3(grid), dim3(128), kargs,
-                                             (size_t)L::bytes, st));
+    return CVA_OK;
+}
+
+cva_status mlp_finish(cudaStream_t st)
+{
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    int *err = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mlp_mu);
+        err = g_mlp[dev].err;
+    }
     int herr = 0;
-    CVA_CUDA_TRY(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (err) CVA_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CVA_CUDA_TRY(cudaStreamSynchronize(st));
     if (herr != 0) return fail(CVA_ETIMEOUT, "mlp: a bounded device wait gave up (status " + std::to_string(herr) + ")");
+    return CVA_OK;
+}
+
+cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t M, int U, int n_batches,
+                          int epochs, float lr, int max_steps, float *params_dev, float *pred_dev,
+                          float *grad_out_dev, float *loss_out_dev, cudaStream_t st)
+{
+    cva_status r = mlp_check_args(F, M, U, n_batches, epochs);
+    if (r != CVA_OK) return r;
+    using L = Layout<64>;
+    constexpr int Z = L::Z;
+    const int tiles_per_batch = (int)(M / n_batches / kRows);
+    int dev = 0, sms = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    CVA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    MlpWork *w = nullptr;
+    MlpPlan pl;
+    r = mlp_prepare(dev, sms, M, tiles_per_batch, st, w, pl);
+    if (r != CVA_OK) return r;
+    float *adam_m = pl.adam, *adam_v = pl.adam + L::NPpad;
+
+    mlp_stats_kernel<<<pl.stats_grid, 256, 0, st>>>(feat, F, (uint32_t)M, pl.part, w->count + 0, pl.stats, pl.adam,
+                                                     2 * L::NPpad, params_dev, pl.best, L::NP, pl.best_loss);
+    CVA_CUDA_TRY(cudaGetLastError());
+
+    SweepArgs sw = {};
+    sw.feat = feat;
+    sw.targ = targ;
+    sw.F = F;
+    sw.M = (uint32_t)M;
+    sw.stats = pl.stats;
+    sw.part = pl.part;
+    sw.count = w->count + 1;
+    sw.best_loss = pl.best_loss;
+    sw.best = pl.best;
+    sw.loss_out = loss_out_dev;
+    sw.err = w->err;
+
+    TrainArgs ta = {};
+    ta.feat = feat;
+    ta.targ = targ;
+    ta.F = F;
+    ta.M = (uint32_t)M;
+    ta.tiles_per_batch = tiles_per_batch;
+    ta.lr = lr;
+    ta.beta1 = 0.9f;
+    ta.beta2 = 0.999f;
+    ta.eps = 1e-8f;
+    ta.params = params_dev;
+    ta.adam_m = adam_m;
+    ta.adam_v = adam_v;
+    ta.stats = pl.stats;
+    ta.grad_out = grad_out_dev;
+    ta.err = w->err;
+
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)pl.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)pl.cluster);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = L::bytes_train;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+
+    int steps_left = max_steps > 0 ? max_steps : INT_MAX;
+    for (int e = 1; e <= epochs; ++e) {
+        ta.n_steps = n_batches < steps_left ? n_batches : steps_left;
+        ta.step0 = (e - 1) * n_batches;
+        ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;   // on once the refit of epoch floor(E/2) ran
+        CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, mlp_train_kernel<64>, ta));
+        steps_left -= ta.n_steps;
+        if (max_steps > 0 && steps_left <= 0) return CVA_OK;
+        if (e == epochs / 2) {
+            sw.mode = 1;
+            sw.theta = params_dev;
+            mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, st>>>(sw);
+            CVA_CUDA_TRY(cudaGetLastError());
+            mlp_refit_kernel<64><<<Z, 128, 0, st>>>(pl.part, pl.sweep_grid, pl.G, w->count + 2, params_dev);
+            CVA_CUDA_TRY(cudaGetLastError());
+        }
+        sw.mode = 0;
+        sw.theta = params_dev;
+        sw.epoch = e;
+        mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, st>>>(sw);
+        CVA_CUDA_TRY(cudaGetLastError());
+    }
+    // the best parameters become the current ones; predictions with them
+    if (pred_dev) {
+        sw.mode = 2;
+        sw.theta = pl.best;
+        sw.pred = pred_dev;
+        sw.params_out = params_dev;
+        mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, st>>>(sw);
+        CVA_CUDA_TRY(cudaGetLastError());
+    } else {
+        CVA_CUDA_TRY(cudaMemcpyAsync(params_dev, pl.best, L::NP * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
     return CVA_OK;
 }
 

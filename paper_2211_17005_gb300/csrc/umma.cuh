@@ -1,13 +1,22 @@
 // Blackwell (sm_100 family) tensor-core helpers written as inline PTX: tensor
 // memory (TMEM) allocation, shared-memory matrix descriptors, tcgen05.mma of
 // kind::f16 (BF16 x BF16 -> FP32 in TMEM), tcgen05.commit to an mbarrier,
-// tcgen05.ld of accumulator rows, the proxy fences, and a bounded grid barrier.
+// tcgen05.ld of accumulator rows, the proxy fences, thread-block cluster
+// barriers and distributed shared memory, and 4-byte cp.async staging.
 //
 // Operand layout (both A and B "K-major", no swizzle): an R x K tile of BF16 is
 // stored as 8 x 8 core matrices of 128 contiguous bytes (8 rows of 16 bytes);
 // core matrix (r/8, k/8) starts at (r/8) * (K/8) * 128 + (k/8) * 128 bytes, so the
 // leading-dimension byte offset (between core matrices along K) is 128 and the
 // stride-dimension byte offset (between 8-row groups) is (K/8) * 128.
+//
+// An "MN-major" operand (instruction-descriptor bit 15 for A, 16 for B) has the
+// M (or N) index contiguous instead: a core matrix is 8 consecutive K rows of 8
+// consecutive M/N elements (16 bytes each); the leading-dimension byte offset is
+// then the stride between core matrices along K and the stride-dimension byte
+// offset the stride between core matrices along M/N. A buffer of per-row records
+// (row r holding elements c) in K-major core matrices can therefore feed a
+// contraction over r directly, read as MN-major, without being transposed.
 #pragma once
 #include <stdint.h>
 
@@ -41,6 +50,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
+
+constexpr uint32_t kMnMajorA = 1u << 15, kMnMajorB = 1u << 16;
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *smem_result, uint32_t ncols)
 {
@@ -124,75 +135,57 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident). Thread 0
-// of each block arrives on a counter; the last one bumps the generation. Waits
-// are bounded: after `max_iter` polls the barrier records a timeout in *err and
-// returns false, and every block then leaves the kernel.
-__device__ __forceinline__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks,
-                                             unsigned &local_gen, int *err, uint32_t max_iter)
+// ---- thread-block clusters: rank, size, barrier, distributed shared memory ----
+__device__ __forceinline__ uint32_t cluster_rank()
 {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = local_gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            *count = 0u;
-            __threadfence();
-            atomicExch(const_cast<unsigned *>(gen), g + 1u);
-        } else {
-            uint32_t it = 0;
-            while (*gen == g) {
-                if (++it > max_iter || *(volatile int *)err) {
-                    ok = 0;
-                    atomicExch(err, 1);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        local_gen = g + 1u;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
 }
 
-// Grid-wide barrier on per-block flags (cooperative launch): every block
-// publishes its generation with a release store, then its threads poll the
-// other blocks' flags in parallel with acquire loads; no atomic counter to
-// serialise on. Bounded like grid_barrier: a timeout records *err, returns false.
-__device__ __forceinline__ bool flag_barrier(unsigned *flags, unsigned nblocks, unsigned &gen, int *err,
-                                             uint32_t max_iter)
+__device__ __forceinline__ uint32_t cluster_size()
 {
-    __threadfence();   // every thread's global writes before the block's release
-    __syncthreads();
-    gen += 1u;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + blockIdx.x), "r"(gen) : "memory");
-    }
-    int ok = 1;
-    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        uint32_t it = 0;
-        for (;;) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flags + b) : "memory");
-            if ((int)(v - gen) >= 0) break;
-            if (++it > max_iter || *(volatile int *)err) {
-                ok = 0;
-                atomicExch(err, 1);
-                break;
-            }
-            __nanosleep(32);
-        }
-    }
-    __threadfence();
-    return __syncthreads_and(ok) != 0;
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
 }
+
+// all threads of all CTAs of the cluster; shared-memory writes before it (local or
+// remote) are visible to every CTA after it
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// address in CTA `rank`'s shared memory of the same offset as the local address `saddr`
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+// no memory clobber: consecutive remote loads stay in flight together; the
+// cluster barriers (which clobber memory) order them against the writes
+__device__ __forceinline__ float ld_cluster_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// ---- asynchronous global -> shared copies of 4 bytes (per-thread staging) ----
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void *g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 }  // namespace umma
 }  // namespace cva
