@@ -599,8 +599,8 @@ cva_status cva_mlp_fit(const float *targets_dev, const float *features_dev, int 
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cva_status r = mlp_begin(st);
     if (r == CVA_OK)
-        r = mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, epochs, lr, 0, params_dev, pred_dev,
-                           nullptr, loss_dev, st);
+        r = mlp_fit_dates(features_dev, 0, targets_dev, 0, 1, F, M, hidden, n_batches, epochs, lr, 0, params_dev,
+                          pred_dev, nullptr, loss_dev, st);
     return r == CVA_OK ? mlp_finish(st) : r;
 }
 
@@ -612,8 +612,8 @@ cva_status cva_mlp_first_gradient(const float *targets_dev, const float *feature
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cva_status r = mlp_begin(st);
     if (r == CVA_OK)
-        r = mlp_train_date(features_dev, F, targets_dev, M, hidden, n_batches, 1, lr, 1, params_dev, nullptr,
-                           grad_dev, nullptr, st);
+        r = mlp_fit_dates(features_dev, 0, targets_dev, 0, 1, F, M, hidden, n_batches, 1, lr, 1, params_dev, nullptr,
+                          grad_dev, nullptr, st);
     return r == CVA_OK ? mlp_finish(st) : r;
 }
 
@@ -626,12 +626,10 @@ cva_status cva_mlp_regress_all(const cva_sim *sim, int pf, int hidden, int n_bat
     const size_t M = s.M;
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cva_status r = mlp_begin(st);
-    for (int i = s.n - 1; i >= 1 && r == CVA_OK; --i) {
-        const float *feat = s.d_features + (size_t)i * s.F * M;
-        const float *targ = s.d_targets + ((size_t)pf * s.n + i) * M;
-        r = mlp_train_date(feat, s.F, targ, M, hidden, n_batches, epochs, lr, 0, params_dev,
-                           pred_dev ? pred_dev + (size_t)i * M : nullptr, nullptr, nullptr, st);
-    }
+    if (r == CVA_OK && s.n >= 2)   // dates n-1 .. 1
+        r = mlp_fit_dates(s.d_features + (size_t)s.F * M, (size_t)s.F * M, s.d_targets + ((size_t)pf * s.n + 1) * M, M,
+                          s.n - 1, s.F, M, hidden, n_batches, epochs, lr, 0, params_dev,
+                          pred_dev ? pred_dev + M : nullptr, nullptr, nullptr, st);
     return r == CVA_OK ? mlp_finish(st) : r;
 }
 

@@ -151,15 +151,16 @@ cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const flo
 cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups, int F, uint64_t M,
                               int basis, float *pred0, double *coef_host, cudaStream_t st);
 
-// Neural regression (mlp.cu). mlp_train_date enqueues one date of Algorithm 1 on
-// `st`; mlp_begin clears the device status before a sequence of dates and
-// mlp_finish synchronises `st` and reports a bounded wait that gave up.
+// Neural regression (mlp.cu). mlp_fit_dates enqueues Algorithm 2 over n_dates
+// consecutive dates of date-major arrays (Algorithm 1 when n_dates = 1) on `st`;
+// mlp_begin clears the device status before it and mlp_finish synchronises `st`
+// and reports a bounded wait that gave up.
 int mlp_num_params(int U);
 cva_status mlp_begin(cudaStream_t st);
 cva_status mlp_finish(cudaStream_t st);
-cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t M, int U, int n_batches,
-                          int epochs, float lr, int max_steps, float *params_dev, float *pred_dev,
-                          float *grad_out_dev, float *loss_out_dev, cudaStream_t st);
+cva_status mlp_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride, int n_dates,
+                         int F, uint64_t M, int U, int n_batches, int epochs, float lr, int max_steps,
+                         float *params_dev, float *pred0, float *grad_out_dev, float *loss_out_dev, cudaStream_t st);
 
 // CVA_0 reduction (reduce.cu).
 cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);

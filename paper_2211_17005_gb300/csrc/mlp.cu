@@ -26,13 +26,25 @@
 //          both operands read MN-major from per-path rows)
 // so that every operand is written as 16-byte pieces of its path's row. BF16
 // operands in shared memory, FP32 accumulators in tensor memory; biases, ReLU,
-// the output layer and the loss in FP32 on the CUDA cores.
+// the output layer and the loss in FP32 on the CUDA cores. A tile's inputs (one
+// 128-path row per feature, one 2-D TMA box of the feature array, and the 512
+// bytes of targets, one bulk copy) are requested one tile ahead by a single
+// thread while the tensor core runs the tile's first GEMM, and complete on the
+// slot's staging mbarrier.
 //
 // One Adam step inside the cluster: each CTA writes its FP32 gradient partial
 // into its own shared memory; after a cluster barrier CTA c sums slice c of the
-// parameter vector over all CTAs' partials (distributed shared memory, fixed CTA
-// order), applies Adam to the slice and stores the new values into every CTA's
-// copy of the parameters; a second cluster barrier publishes them.
+// parameter vector over all CTAs' partials (distributed shared memory, 16-byte
+// accesses, fixed CTA order), applies Adam to the slice and stores the new values
+// into every CTA's copy of the parameters; a second cluster barrier publishes them.
+//
+// Consecutive train launches of a date use programmatic dependent launch: a
+// running train kernel lets the next one become resident (on its own cluster of
+// SMs) and that one waits, in hardware, for its predecessor to complete before
+// it reads anything. The next epoch's cluster is thus placed before the loss pass
+// of the side stream can take the SMs it needs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -79,7 +91,7 @@ struct Layout {
     static constexpr int sVec = sStage + 2 * (kIn + 1) * kRows * 4;   // mean[32], istd[32]
     static constexpr int sGsl = sVec + 2 * kIn * 4;             // [8 warps][U + 2] output-layer gradients
     static constexpr int sMom = sGsl + 8 * (U + 2) * 4;         // Adam moments of the owned slice
-    static constexpr int kSliceMax = (NP + 3) / 4;              // clusters of at least 4 CTAs
+    static constexpr int kSliceMax = NPpad / 4;                 // clusters of at least 4 CTAs
     static constexpr int bytes_train = sMom + 2 * kSliceMax * 4;
     static constexpr int bytes_sweep = sMom;
     static constexpr uint32_t tmem_cols = 512;   // D of slot s at [64 s, 64 s + U), DW at [128 + 128 s, +128)
@@ -113,8 +125,12 @@ struct TrainArgs {
     uint32_t M;
     int tiles_per_batch, n_steps, step0, pos;   // batches 0..n_steps-1; Adam steps step0+1..; output ReLU
     float lr, beta1, beta2, eps;
-    float *params;                 // [NP] row order, in/out
-    float *adam_m, *adam_v;        // [NPpad] column order
+    const float *init;             // [NP] row order: parameters at the start of the launch
+    float *params;                 // [NP] row order: parameters at its end (may equal init)
+    float *snap;                   // [NP] row order: a second copy of them (nullable)
+    float *best;                   // step0 == 0: receives init (the date's best so far) ...
+    double *best_loss;             // ... and +inf
+    float *adam_m, *adam_v;        // [NPpad] column order; step0 == 0: the moments start at zero
     const float *stats;            // mean[32], 1/std[32]
     float *grad_out;               // [NP] row order: gradient of the date's first step (nullable)
     int *err;
@@ -157,31 +173,39 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// Sums of 16 columns over the 32 lanes of a warp by recursive halving: at each
-// level a lane keeps half of its columns and adds its partner's copy of them.
-// Lane l ends with the total of column (l >> 1) (lanes l and l ^ 1 agree).
-__device__ __forceinline__ float column_sums16(const float (&v)[16], int lane)
+// Sums of 64 columns over the 32 lanes of a warp by recursive halving (levels
+// 16, 8, 4, 2, 1): lane l ends with the totals of columns 2l and 2l + 1.
+__device__ __forceinline__ float2 column_sums64(const float (&v)[64], int lane)
 {
-    float a8[8], a4[4], a2[2];
-    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
+    float a32[32], a16[16], a8[8], a4[4];
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2, u1 = lane & 1;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const float send = u16 ? v[i] : v[32 + i], keep = u16 ? v[32 + i] : v[i];
+        a32[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float send = u8 ? a32[i] : a32[16 + i], keep = u8 ? a32[16 + i] : a32[i];
+        a16[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const float send = u16 ? v[i] : v[8 + i], keep = u16 ? v[8 + i] : v[i];
-        a8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        const float send = u4 ? a16[i] : a16[8 + i], keep = u4 ? a16[8 + i] : a16[i];
+        a8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float send = u8 ? a8[i] : a8[4 + i], keep = u8 ? a8[4 + i] : a8[i];
-        a4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        const float send = u2 ? a8[i] : a8[4 + i], keep = u2 ? a8[4 + i] : a8[i];
+        a4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
     }
+    float r[2];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const float send = u4 ? a4[i] : a4[2 + i], keep = u4 ? a4[2 + i] : a4[i];
-        a2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        const float send = u1 ? a4[i] : a4[2 + i], keep = u1 ? a4[2 + i] : a4[i];
+        r[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
     }
-    const float send = u2 ? a2[0] : a2[1], keep = u2 ? a2[1] : a2[0];
-    const float a1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-    return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
+    return make_float2(r[0], r[1]);
 }
 
 template <int U>
@@ -189,8 +213,9 @@ struct Net {
     using L = Layout<U>;
     unsigned char *smem;
     uint32_t tmem = 0;
-    uint64_t *mbar;
-    uint32_t phase = 0;
+    uint64_t *mbar, *sbar;         // tensor-core completion, input staging (this slot's)
+    uint32_t phase = 0, sphase = 0;
+    bool pending = false;          // a staging copy was issued and not yet consumed
     int tid, warp, lane, slot, row;
     const float *th, *mean, *istd;
     float *stage;
@@ -203,6 +228,7 @@ struct Net {
         slot = tid >> 7;
         row = tid & 127;
         mbar = mbars + slot;
+        sbar = mbars + 2 + slot;
         th = reinterpret_cast<const float *>(smem + L::sTh);
         mean = reinterpret_cast<const float *>(smem + L::sVec);
         istd = mean + kIn;
@@ -233,8 +259,10 @@ struct Net {
 
     // one tensor-core step of this slot: operands written -> issue (row 0) ->
     // completion; the result is the same for the whole slot
-    template <class Issue>
-    __device__ bool mma(Issue issue)
+    // side() runs in every thread of the slot after the slot barrier, while the
+    // tensor core works (it may request the next tile's inputs)
+    template <class Issue, class Side>
+    __device__ bool mma(Issue issue, bool pre_ok, Side side)
     {
         umma::fence_proxy_async();
         umma::fence_before_sync();
@@ -244,10 +272,16 @@ struct Net {
             issue();
             umma::commit(mbar);
         }
+        side();
         const bool done = umma::mbar_wait(mbar, phase, kMbarPolls);
         phase ^= 1u;
         umma::fence_after_sync();
-        return wg_all(done);
+        return wg_all(done && pre_ok);
+    }
+    template <class Issue>
+    __device__ bool mma(Issue issue)
+    {
+        return mma(issue, true, [] {});
     }
 
     // D = A B^T: A = K columns of the rows from column c0 (K-major), B = a K-major image [N][K]
@@ -283,26 +317,43 @@ struct Net {
     }
 
     // ---- inputs ----
-    // copy this thread's row (features, target) of the tile at `path - row` into the staging area
-    __device__ void prefetch(const float *feat, const float *targ, uint32_t M, int F, uint32_t path) const
+    // stage the tile of paths [path0, path0 + 128): the F feature rows (one box of
+    // the tensor map at (path0, 0)) and the target row, completing on this slot's
+    // staging barrier. Called by every thread of the slot once all of them are done
+    // reading the staging area; one thread issues the copies.
+    __device__ void prefetch(const CUtensorMap *tm, const float *targ, int F, uint32_t path0)
     {
-        const uint32_t s = umma::smem_u32(stage);
-        for (int f = 0; f < F; ++f) umma::cp_async4(s + (uint32_t)(f * kRows + row) * 4u, feat + (size_t)f * M + path);
-        umma::cp_async4(s + (uint32_t)(kIn * kRows + row) * 4u, targ + path);
-        umma::cp_async_commit();
+        if (row == 32) {
+            umma::mbar_arrive_expect_tx(sbar, (uint32_t)(F + 1) * kRows * 4u);
+            umma::tma_load_2d(umma::smem_u32(stage), tm, (int32_t)path0, 0, sbar);
+            umma::bulk_g2s(umma::smem_u32(stage + kIn * kRows), targ + path0, kRows * 4u, sbar);
+        }
+        pending = true;
     }
 
-    // standardised inputs of this thread's row into the X columns of B; returns the target
-    __device__ float stage_x(int F) const
+    // wait for the staged tile; standardised inputs of this thread's row into the X
+    // columns of B (rows f >= F of the staging area hold zeros, as do their mean and
+    // 1/std); y receives the target. False if the bounded wait gave up.
+    __device__ bool stage_x(float &y)
     {
-        umma::cp_async_wait_all();
+        const bool ok = umma::mbar_wait(sbar, sphase, kMbarPolls);
+        sphase ^= 1u;
+        pending = false;
+        const float4 *mv = reinterpret_cast<const float4 *>(mean), *iv = reinterpret_cast<const float4 *>(istd);
         float x[kIn];
 #pragma unroll
-        for (int f = 0; f < kIn; ++f) x[f] = f < F ? (stage[f * kRows + row] - mean[f]) * istd[f] : 0.f;
+        for (int g = 0; g < kIn / 4; ++g) {
+            const float4 m = mv[g], r = iv[g];
+            x[4 * g + 0] = (stage[(4 * g + 0) * kRows + row] - m.x) * r.x;
+            x[4 * g + 1] = (stage[(4 * g + 1) * kRows + row] - m.y) * r.y;
+            x[4 * g + 2] = (stage[(4 * g + 2) * kRows + row] - m.z) * r.z;
+            x[4 * g + 3] = (stage[(4 * g + 3) * kRows + row] - m.w) * r.w;
+        }
         unsigned char *b = smem + offB();
 #pragma unroll
         for (int g = 0; g < kIn / 8; ++g) *reinterpret_cast<uint4 *>(b + row_off(row, L::cX + 8 * g)) = pack8(x + 8 * g);
-        return stage[kIn * kRows + row];
+        y = stage[kIn * kRows + row];
+        return ok;
     }
 
     // constant columns of B (ones after H1 and after X, zeros beside them), both slots
@@ -338,63 +389,85 @@ struct Net {
     __device__ void epi1(uint32_t (&m1)[U / 32]) const
     {
         unsigned char *b = smem + offB();
-        const float *b1 = th + L::ob1;
+        const float4 *b1 = reinterpret_cast<const float4 *>(th + L::ob1);
+        float v[64];
+        umma::tmem_ld64(taddr(dcol()), v);
+        m1[0] = m1[1] = 0u;
 #pragma unroll
-        for (int c = 0; c < U / 16; ++c) {
-            float v[16];
-            ld16(dcol() + 16 * c, v);
-            umma::tmem_wait_ld();
-            uint32_t bits = 0;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                v[i] = fmaxf(v[i] + b1[16 * c + i], 0.f);
-                bits |= (v[i] > 0.f ? 1u : 0u) << i;
-            }
-            if (c % 2 == 0) m1[c / 2] = bits;
-            else m1[c / 2] |= bits << 16;
-            *reinterpret_cast<uint4 *>(b + row_off(row, 16 * c)) = pack8(v);
-            *reinterpret_cast<uint4 *>(b + row_off(row, 16 * c + 8)) = pack8(v + 8);
+        for (int g = 0; g < 16; ++g) {
+            const float4 c = b1[g];
+            v[4 * g + 0] = fmaxf(v[4 * g + 0] + c.x, 0.f);
+            v[4 * g + 1] = fmaxf(v[4 * g + 1] + c.y, 0.f);
+            v[4 * g + 2] = fmaxf(v[4 * g + 2] + c.z, 0.f);
+            v[4 * g + 3] = fmaxf(v[4 * g + 3] + c.w, 0.f);
         }
+#pragma unroll
+        for (int i = 0; i < 64; ++i) m1[i / 32] |= (v[i] > 0.f ? 1u : 0u) << (i % 32);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) *reinterpret_cast<uint4 *>(b + row_off(row, 8 * g)) = pack8(v + 8 * g);
     }
 
-    // output of this thread's row from the second-layer accumulator: zeta (+ relu if pos) + mu
+    // second hidden layer of this thread's row from its accumulator: h2 = relu(D + b2)
+    // in place, and zeta = w3 . h2 + b3 (four partial sums)
+    __device__ float layer2(float (&v)[64]) const
+    {
+        const float4 *b2 = reinterpret_cast<const float4 *>(th + L::ob2), *w3 = reinterpret_cast<const float4 *>(th + L::ow3);
+        umma::tmem_ld64(taddr(dcol()), v);
+        float acc[4] = {th[L::ob3], 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const float4 c = b2[g], w = w3[g];
+            v[4 * g + 0] = fmaxf(v[4 * g + 0] + c.x, 0.f);
+            v[4 * g + 1] = fmaxf(v[4 * g + 1] + c.y, 0.f);
+            v[4 * g + 2] = fmaxf(v[4 * g + 2] + c.z, 0.f);
+            v[4 * g + 3] = fmaxf(v[4 * g + 3] + c.w, 0.f);
+            acc[0] = fmaf(v[4 * g + 0], w.x, acc[0]);
+            acc[1] = fmaf(v[4 * g + 1], w.y, acc[1]);
+            acc[2] = fmaf(v[4 * g + 2], w.z, acc[2]);
+            acc[3] = fmaf(v[4 * g + 3], w.w, acc[3]);
+        }
+        return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }
+
+    // output of this thread's row: zeta (+ relu if pos) + mu
     __device__ float output(int pos, float &outv) const
     {
-        const float *b2 = th + L::ob2, *w3 = th + L::ow3;
-        float out = th[L::ob3];
-#pragma unroll
-        for (int c = 0; c < U / 16; ++c) {
-            float v[16];
-            ld16(dcol() + 16 * c, v);
-            umma::tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) out = fmaf(fmaxf(v[i] + b2[16 * c + i], 0.f), w3[16 * c + i], out);
-        }
+        float v[64];
+        const float out = layer2(v);
         outv = out;
         return (pos ? fmaxf(out, 0.f) : out) + th[L::omu];
     }
 
-    // dH2 = dout w3 (h2 > 0) into A; dw3 += column sums of h2 dout into this warp's slots
-    __device__ void back2(float dout, float *gsl) const
+    // output, loss derivative and the output-layer backward of this thread's row:
+    // dH2 = dout w3 (h2 > 0) into A; the column sums of h2 dout (dw3), of dout (db3)
+    // and of dpred (dmu) over the warp's rows into this warp's slots gsl
+    __device__ void out_back2(int pos, float y, float inv_batch, float *gsl) const
     {
         unsigned char *a = smem + offA();
-        const float *b2 = th + L::ob2, *w3 = th + L::ow3;
+        const float4 *w3 = reinterpret_cast<const float4 *>(th + L::ow3);
+        float v[64];
+        const float out = layer2(v);
+        const float pred = (pos ? fmaxf(out, 0.f) : out) + th[L::omu];
+        const float dpred = 2.f * (pred - y) * inv_batch;
+        const float dout = pos ? (out > 0.f ? dpred : 0.f) : dpred;
 #pragma unroll
-        for (int c = 0; c < U / 16; ++c) {
-            float v[16];
-            ld16(dcol() + 16 * c, v);
-            umma::tmem_wait_ld();
-            float d[16], pr[16];
+        for (int g = 0; g < 8; ++g) {
+            const float4 w0 = w3[2 * g], w1 = w3[2 * g + 1];
+            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            float d[8];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const float h2 = fmaxf(v[i] + b2[16 * c + i], 0.f);
-                d[i] = h2 > 0.f ? dout * w3[16 * c + i] : 0.f;
-                pr[i] = h2 * dout;
-            }
-            *reinterpret_cast<uint4 *>(a + row_off(row, 16 * c)) = pack8(d);
-            *reinterpret_cast<uint4 *>(a + row_off(row, 16 * c + 8)) = pack8(d + 8);
-            const float s = column_sums16(pr, lane);
-            if (!(lane & 1)) gsl[16 * c + (lane >> 1)] += s;
+            for (int i = 0; i < 8; ++i) d[i] = v[8 * g + i] > 0.f ? dout * wv[i] : 0.f;
+            *reinterpret_cast<uint4 *>(a + row_off(row, 8 * g)) = pack8(d);
+        }
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] *= dout;
+        const float2 cs = column_sums64(v, lane);
+        gsl[2 * lane] += cs.x;
+        gsl[2 * lane + 1] += cs.y;
+        const float s3 = warp_sum(dout), smu = warp_sum(dpred);
+        if (lane == 0) {
+            gsl[U] += s3;
+            gsl[U + 1] += smu;
         }
     }
 
@@ -402,47 +475,37 @@ struct Net {
     __device__ void back1(const uint32_t (&m1)[U / 32]) const
     {
         unsigned char *a = smem + offA();
+        float v[64];
+        umma::tmem_ld64(taddr(dcol()), v);
 #pragma unroll
-        for (int c = 0; c < U / 16; ++c) {
-            float v[16];
-            ld16(dcol() + 16 * c, v);
-            umma::tmem_wait_ld();
-            const uint32_t bits = m1[c / 2] >> (16 * (c % 2));
+        for (int i = 0; i < 64; ++i) v[i] = ((m1[i / 32] >> (i % 32)) & 1u) ? v[i] : 0.f;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = ((bits >> i) & 1u) ? v[i] : 0.f;
-            *reinterpret_cast<uint4 *>(a + row_off(row, L::cDH1 + 16 * c)) = pack8(v);
-            *reinterpret_cast<uint4 *>(a + row_off(row, L::cDH1 + 16 * c + 8)) = pack8(v + 8);
-        }
+        for (int g = 0; g < 8; ++g) *reinterpret_cast<uint4 *>(a + row_off(row, L::cDH1 + 8 * g)) = pack8(v + 8 * g);
     }
 
-    // first two layers of the staged tile; D holds the second-layer pre-activation after it
-    __device__ bool forward12(uint32_t (&m1)[U / 32])
+    // first two layers of the staged tile (staging status in_ok); D holds the second-layer
+    // pre-activation after it. side() runs during the first GEMM, when every thread of
+    // the slot is past the staging area (the next tile's copies may be requested).
+    template <class Side>
+    __device__ bool forward12(uint32_t (&m1)[U / 32], bool in_ok, Side side)
     {
-        if (!mma([&] { gemm_rows(dcol(), offB(), L::cX, L::sW1, kIn, U, false); })) return false;
+        if (!mma([&] { gemm_rows(dcol(), offB(), L::cX, L::sW1, kIn, U, false); }, in_ok, side)) return false;
         epi1(m1);
         return mma([&] { gemm_rows(dcol(), offB(), 0, L::sW2, U, U, false); });
     }
 
     // forward + backward of one tile; weight gradients accumulate in this slot's DW
-    __device__ bool train_tile(const TrainArgs &a, bool first, float inv_batch, bool has_next, uint32_t next_path,
-                               float *gsl)
+    __device__ bool train_tile(const TrainArgs &a, const CUtensorMap *tm, bool first, float inv_batch, bool has_next,
+                               uint32_t next_path, float *gsl)
     {
-        const float y = stage_x(a.F);
-        if (has_next) prefetch(a.feat, a.targ, a.M, a.F, next_path + row);
+        float y;
+        const bool in_ok = stage_x(y);
         uint32_t m1[U / 32];
-        if (!forward12(m1)) return false;
-        float out;
-        const float pred = output(a.pos, out);
-        const float dpred = 2.f * (pred - y) * inv_batch;
-        const float dout = a.pos ? (out > 0.f ? dpred : 0.f) : dpred;
-        back2(dout, gsl);
-        {
-            const float s3 = warp_sum(dout), smu = warp_sum(dpred);
-            if (lane == 0) {
-                gsl[U] += s3;
-                gsl[U + 1] += smu;
-            }
-        }
+        if (!forward12(m1, in_ok, [&] {
+                if (has_next) prefetch(tm, a.targ, a.F, next_path);
+            }))
+            return false;
+        out_back2(a.pos, y, inv_batch, gsl);
         if (!mma([&] { gemm_rows_w2t(dcol(), offA()); })) return false;
         back1(m1);
         return mma([&] { gemm_paths(wcol(), offA(), offB(), kRows, !first); });
@@ -500,7 +563,7 @@ struct Net {
 // order), standardisation, constant operand columns, weight images
 template <int U>
 __device__ void net_setup(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *params, const float *stats,
-                          bool zero_a)
+                          int F, bool zero_a)
 {
     using L = Layout<U>;
     if (n.warp == 0) {
@@ -508,8 +571,7 @@ __device__ void net_setup(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const f
         umma::tmem_relinquish();
     }
     if (n.tid == 0) {
-        umma::mbar_init(&s_mbar[0], 1);
-        umma::mbar_init(&s_mbar[1], 1);
+        for (int i = 0; i < 4; ++i) umma::mbar_init(&s_mbar[i], 1);
         umma::fence_mbar_init();
     }
     float *th = reinterpret_cast<float *>(n.smem + L::sTh);
@@ -518,6 +580,12 @@ __device__ void net_setup(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const f
     if (n.tid < 2 * kIn) vec[n.tid] = __ldg(stats + n.tid);
     float *gsl = reinterpret_cast<float *>(n.smem + L::sGsl);
     for (int i = n.tid; i < 8 * (U + 2); i += kThreads) gsl[i] = 0.f;
+    // staging rows of the padded inputs stay zero (the copies fill rows < F)
+    float *stg = reinterpret_cast<float *>(n.smem + L::sStage);
+    for (int i = n.tid; i < 2 * (kIn + 1) * kRows; i += kThreads) {
+        const int f = (i / kRows) % (kIn + 1);
+        if (f >= F && f < kIn) stg[i] = 0.f;
+    }
     if (zero_a) {
         uint4 *a = reinterpret_cast<uint4 *>(n.smem + n.offA());
         for (int i = n.row; i < 32768 / 16; i += kRows) a[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -535,7 +603,7 @@ __device__ void net_setup(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const f
 template <int U>
 __device__ void net_teardown(Net<U> &n)
 {
-    umma::cp_async_wait_all();
+    if (n.pending) (void)umma::mbar_wait(n.sbar, n.sphase, kMbarPolls);   // no copy outlives the CTA
     umma::fence_before_sync();
     __syncthreads();
     if (n.warp == 0) umma::tmem_dealloc(n.tmem, Layout<U>::tmem_cols);
@@ -545,24 +613,33 @@ __device__ void net_teardown(Net<U> &n)
 // Batch b covers paths [b * P, (b + 1) * P), P = tiles_per_batch * 128; in each
 // step the cluster's 2 CL slots take the batch's tiles round-robin.
 template <int U>
-__global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a)
+__global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, const __grid_constant__ CUtensorMap tm)
 {
     using L = Layout<U>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ __align__(8) uint64_t s_mbar[4];
     Net<U> n(smem, s_mbar);
     const uint32_t rank = umma::cluster_rank(), CL = umma::cluster_size();
     float *th = reinterpret_cast<float *>(smem + L::sTh);
     float *part = reinterpret_cast<float *>(smem);   // slot 0's A rows, free between steps
     float *gsl = reinterpret_cast<float *>(smem + L::sGsl);
     float *mom = reinterpret_cast<float *>(smem + L::sMom);
-    const int S = (L::NP + (int)CL - 1) / (int)CL, lo = (int)rank * S, hi = min(L::NP, lo + S);
+    // owned slice [lo, hi) of the padded parameter vector: a multiple of 4 entries
+    const int S = L::NPpad / (int)CL, lo = (int)rank * S, hi = lo + S;
 
-    net_setup<U>(n, &s_tmem, s_mbar, a.params, a.stats, false);
+    // the previous kernel of the stream has completed and its writes are visible;
+    // from here on the next train launch may become resident
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    net_setup<U>(n, &s_tmem, s_mbar, a.init, a.stats, a.F, false);
     for (int q = lo + n.tid; q < hi; q += kThreads) {
-        mom[q - lo] = a.adam_m[q];
-        mom[L::kSliceMax + q - lo] = a.adam_v[q];
+        mom[q - lo] = a.step0 == 0 ? 0.f : a.adam_m[q];
+        mom[L::kSliceMax + q - lo] = a.step0 == 0 ? 0.f : a.adam_v[q];
+    }
+    if (a.step0 == 0 && rank == 0) {   // start of a date: the starting parameters are the best so far
+        for (int p = n.tid; p < L::NP; p += kThreads) a.best[p] = __ldg(a.init + p);
+        if (n.tid == 0) *a.best_loss = 1e300;
     }
 
     const uint32_t per_batch = (uint32_t)a.tiles_per_batch * kRows;
@@ -574,13 +651,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a)
     float *my_gsl = gsl + n.warp * (U + 2);
 
     bool ok = true;
-    if (my_rounds > 0) n.prefetch(a.feat, a.targ, a.M, a.F, path_of(0, 0) + n.row);
+    if (my_rounds > 0) n.prefetch(&tm, a.targ, a.F, path_of(0, 0));
     for (int st = 0; st < a.n_steps; ++st) {
         for (int rd = 0; rd < my_rounds && ok; ++rd) {
             const bool last = rd + 1 == my_rounds;
             const bool has_next = !last || st + 1 < a.n_steps;
             const uint32_t next = last ? path_of(st + 1, 0) : path_of(st, rd + 1);
-            ok = n.train_tile(a, rd == 0, inv_batch, has_next, next, my_gsl);
+            ok = n.train_tile(a, &tm, rd == 0, inv_batch, has_next, next, my_gsl);
             if (!ok && n.row == 0) atomicExch(a.err, 2);
         }
         umma::fence_before_sync();
@@ -589,26 +666,36 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a)
         n.write_partial(part, gsl, h0, h1);
         umma::cluster_sync();   // every CTA's partial is complete
 
-        // the owned slice: sum over the cluster (CTA order), Adam, new values everywhere
+        // the owned slice: 16-byte remote loads of the cluster's partials (all in
+        // flight), sums in CTA order, Adam, 16-byte remote stores of the new values
+        // into every CTA's copy of the parameters
         const int step = a.step0 + st + 1;
         const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
         const uint32_t part_s = umma::smem_u32(part), th_s = umma::smem_u32(th);
-        for (int q = lo + n.tid; q < hi; q += kThreads) {
-            float gv[kMaxCluster];
-#pragma unroll
-            for (int c = 0; c < kMaxCluster; ++c)
-                gv[c] = (uint32_t)c < CL ? umma::ld_cluster_f32(umma::map_rank(part_s + 4u * (uint32_t)q, (uint32_t)c))
-                                         : 0.f;
-            float g = 0.f;
-#pragma unroll
-            for (int c = 0; c < kMaxCluster; ++c) g += gv[c];
-            if (step == 1 && a.grad_out) a.grad_out[L::p_of(q)] = g;
-            if (q < L::ob1 && q / U >= a.F) continue;   // padded inputs stay zero
+        auto adam = [&](int q, float g) -> float {
+            if (step == 1 && a.grad_out && q < L::NP) a.grad_out[L::p_of(q)] = g;
+            if (q >= L::NP || (q < L::ob1 && q / U >= a.F)) return 0.f;   // padding stays zero
             float &m = mom[q - lo], &v = mom[L::kSliceMax + q - lo];
             m = a.beta1 * m + (1.f - a.beta1) * g;
             v = a.beta2 * v + (1.f - a.beta2) * g * g;
-            const float t = th[q] - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
-            for (uint32_t c = 0; c < CL; ++c) umma::st_cluster_f32(umma::map_rank(th_s + 4u * (uint32_t)q, c), t);
+            return th[q] - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
+        };
+        for (int q0 = lo + 4 * n.tid; q0 < hi; q0 += 4 * kThreads) {
+            float4 gv[kMaxCluster];
+#pragma unroll
+            for (int c = 0; c < kMaxCluster; ++c)
+                gv[c] = (uint32_t)c < CL ? umma::ld_cluster_f32x4(umma::map_rank(part_s + 4u * (uint32_t)q0, (uint32_t)c))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < kMaxCluster; ++c) {
+                g.x += gv[c].x;
+                g.y += gv[c].y;
+                g.z += gv[c].z;
+                g.w += gv[c].w;
+            }
+            const float4 t = make_float4(adam(q0, g.x), adam(q0 + 1, g.y), adam(q0 + 2, g.z), adam(q0 + 3, g.w));
+            for (uint32_t c = 0; c < CL; ++c) umma::st_cluster_f32x4(umma::map_rank(th_s + 4u * (uint32_t)q0, c), t);
         }
         umma::cluster_sync();   // new parameters everywhere; partials read
         n.build_images();
@@ -616,7 +703,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a)
         __syncthreads();
     }
     for (int q = lo + n.tid; q < hi; q += kThreads) {
-        a.params[L::p_of(q)] = th[q];
+        if (q < L::NP) {
+            a.params[L::p_of(q)] = th[q];
+            if (a.snap) a.snap[L::p_of(q)] = th[q];
+        }
         a.adam_m[q] = mom[q - lo];
         a.adam_v[q] = mom[L::kSliceMax + q - lo];
     }
@@ -627,29 +717,31 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a)
 // Full-sample passes with fixed parameters, output ReLU on: the loss (mode 0), the
 // refit's Gram matrix of Z = [h2 | 1 | y - mu] (mode 1), the predictions (mode 2).
 template <int U>
-__global__ void __launch_bounds__(kThreads, 1) mlp_sweep_kernel(SweepArgs a)
+__global__ void __launch_bounds__(kThreads, 1) mlp_sweep_kernel(SweepArgs a, const __grid_constant__ CUtensorMap tm)
 {
     using L = Layout<U>;
     constexpr int Z = L::Z;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ __align__(8) uint64_t s_mbar[4];
     __shared__ double s_red[8];
     __shared__ int s_flag[2];
     Net<U> n(smem, s_mbar);
-    net_setup<U>(n, &s_tmem, s_mbar, a.theta, a.stats, a.mode == 1);
+    net_setup<U>(n, &s_tmem, s_mbar, a.theta, a.stats, a.F, a.mode == 1);
 
     const uint32_t tiles = a.M / kRows, stride = 2u * gridDim.x;
     uint32_t t = 2u * blockIdx.x + (uint32_t)n.slot;
     double acc = 0.0;
     bool ok = true, first = true;
-    if (t < tiles) n.prefetch(a.feat, a.targ, a.M, a.F, t * kRows + n.row);
+    if (t < tiles) n.prefetch(&tm, a.targ, a.F, t * kRows);
     for (; t < tiles && ok; t += stride) {
         const uint32_t nt = t + stride;
-        const float y = n.stage_x(a.F);
-        if (nt < tiles) n.prefetch(a.feat, a.targ, a.M, a.F, nt * kRows + n.row);
+        float y;
+        const bool in_ok = n.stage_x(y);
         uint32_t m1[U / 32];
-        ok = n.forward12(m1);
+        ok = n.forward12(m1, in_ok, [&] {
+            if (nt < tiles) n.prefetch(&tm, a.targ, a.F, nt * kRows);
+        });
         if (ok && a.mode != 1) {
             float out;
             const float pred = n.output(1, out);
@@ -661,17 +753,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_sweep_kernel(SweepArgs a)
         } else if (ok) {
             // row of Z into A: [relu(D + b2) | 1 | y - mu | 0 ...]
             unsigned char *ar = smem + n.offA();
-            const float *b2 = n.th + L::ob2;
+            float v[64];
+            (void)n.layer2(v);
 #pragma unroll
-            for (int c = 0; c < U / 16; ++c) {
-                float v[16];
-                n.ld16(n.dcol() + 16 * c, v);
-                umma::tmem_wait_ld();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + b2[16 * c + i], 0.f);
-                *reinterpret_cast<uint4 *>(ar + row_off(n.row, 16 * c)) = pack8(v);
-                *reinterpret_cast<uint4 *>(ar + row_off(n.row, 16 * c + 8)) = pack8(v + 8);
-            }
+            for (int g = 0; g < 8; ++g) *reinterpret_cast<uint4 *>(ar + row_off(n.row, 8 * g)) = pack8(v + 8 * g);
             *reinterpret_cast<uint4 *>(ar + row_off(n.row, U)) =
                 make_uint4(pack2(1.f, y - n.th[L::omu]), 0u, 0u, 0u);
             // G (+)= Z^T Z: M = the 128 columns of the rows (Z in the first U + 2), N = U + 16
@@ -741,23 +826,29 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_sweep_kernel(SweepArgs a)
 
 // Refit of (w3, b3) at epoch floor(E/2): block i sums row i of the CTAs' Gram
 // partials (fixed order); the last block solves the Jacobi-scaled normal
-// equations of [h2 | 1] (w3, b3) = y - mu by FP64 Cholesky. A numerically
-// singular system keeps the old (w3, b3).
+// equations of [h2 | 1] (w3, b3) = y - mu by FP64 Cholesky (right-looking, the
+// trailing update spread over the block) and two triangular solves. A
+// numerically singular system keeps the old (w3, b3). The new values go to
+// params and, when not null, to params2.
 template <int U>
-__global__ void __launch_bounds__(128) mlp_refit_kernel(const double *part, int nparts, double *G, unsigned *count,
-                                                        float *params)
+__global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int nparts, double *G, unsigned *count,
+                                                        float *params, float *params2)
 {
     using L = Layout<U>;
     constexpr int Z = L::Z, n1 = U + 1;
     __shared__ double A[Z * Z];
-    __shared__ double sc[n1], xv[n1];
-    __shared__ int s_last;
+    __shared__ double sc[n1], xv[n1], inv_d[n1], half[Z];
+    __shared__ int s_last, s_singular;
     const int tid = threadIdx.x, lane = tid & 31;
     const int i = blockIdx.x;
-    for (int c = tid; c < Z; c += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nparts; ++b) s += __ldg(part + (size_t)b * Z * Z + i * Z + c);
-        G[i * Z + c] = s;
+    {   // row i of the total Gram matrix: two fixed halves of the partials per column
+        const int c = tid % Z, h = tid / Z, mid = nparts / 2;
+        double sum = 0.0;
+        if (h < 2)
+            for (int b = h ? mid : 0; b < (h ? nparts : mid); ++b) sum += __ldg(part + (size_t)b * Z * Z + i * Z + c);
+        if (h == 1) half[c] = sum;
+        __syncthreads();
+        if (h == 0) G[i * Z + c] = sum + half[c];
     }
     __threadfence();
     __syncthreads();
@@ -766,7 +857,10 @@ __global__ void __launch_bounds__(128) mlp_refit_kernel(const double *part, int 
     if (!s_last) return;
     __threadfence();
     for (int e = tid; e < Z * Z; e += blockDim.x) A[e] = __ldcg(G + e);
-    if (tid == 0) *count = 0u;
+    if (tid == 0) {
+        *count = 0u;
+        s_singular = 0;
+    }
     __syncthreads();
     for (int j = tid; j < n1; j += blockDim.x) sc[j] = A[j * Z + j] > 0.0 ? 1.0 / sqrt(A[j * Z + j]) : 0.0;
     __syncthreads();
@@ -775,111 +869,108 @@ __global__ void __launch_bounds__(128) mlp_refit_kernel(const double *part, int 
         A[r * Z + c] *= sc[r] * (c < n1 ? sc[c] : 1.0);
     }
     __syncthreads();
-    bool singular = false;
+    // lower Cholesky factor in place: column j, then the trailing lower triangle;
+    // thread t updates column j + 1 + (t mod 64), rows c + (t / 64) + 4k
     for (int j = 0; j < n1; ++j) {
-        double d = A[j * Z + j];
-        if (!(d > 1e-12)) {
-            singular = true;
-            d = 1.0;
+        if (tid == 0) {
+            double d = A[j * Z + j];
+            if (!(d > 1e-12)) {
+                s_singular = 1;
+                d = 1.0;
+            }
+            d = sqrt(d);
+            A[j * Z + j] = d;
+            inv_d[j] = 1.0 / d;
         }
-        d = sqrt(d);
         __syncthreads();
-        if (tid == 0) A[j * Z + j] = d;
-        for (int r = j + 1 + tid; r < n1; r += blockDim.x) A[r * Z + j] /= d;
+        const double r_d = inv_d[j];
+        for (int r = j + 1 + tid; r < n1; r += blockDim.x) A[r * Z + j] *= r_d;
         __syncthreads();
-        const int m = n1 - j - 1;
-        for (int e = tid; e < m * m; e += blockDim.x) {
-            const int r = j + 1 + e / m, c = j + 1 + e % m;
-            if (c <= r) A[r * Z + c] -= A[r * Z + j] * A[c * Z + j];
+        const int c = j + 1 + (tid & 63);
+        if (c < n1) {
+            const double lcj = A[c * Z + j];
+            for (int r = c + (tid >> 6); r < n1; r += (int)blockDim.x / 64) A[r * Z + c] -= A[r * Z + j] * lcj;
         }
         __syncthreads();
     }
-    if (tid < 32) {
-        for (int r = 0; r < n1; ++r) {   // L y = b
-            double s = 0.0;
-            for (int p = lane; p < r; p += 32) s += A[r * Z + p] * xv[p];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) xv[r] = (A[r * Z + n1] - s) / A[r * Z + r];
+    if (tid < 32) {   // L y = b, then L^T x = y (column-oriented, one warp)
+        for (int r = lane; r < n1; r += 32) xv[r] = A[r * Z + n1];
+        __syncwarp();
+        for (int j = 0; j < n1; ++j) {
+            const double yj = xv[j] * inv_d[j];
+            __syncwarp();
+            if (lane == 0) xv[j] = yj;
+            for (int r = j + 1 + lane; r < n1; r += 32) xv[r] -= A[r * Z + j] * yj;
             __syncwarp();
         }
-        for (int r = n1 - 1; r >= 0; --r) {   // L^T x = y
-            double s = 0.0;
-            for (int p = r + 1 + lane; p < n1; p += 32) s += A[p * Z + r] * xv[p];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) xv[r] = (xv[r] - s) / A[r * Z + r];
+        for (int j = n1 - 1; j >= 0; --j) {
+            const double xj = xv[j] * inv_d[j];
+            __syncwarp();
+            if (lane == 0) xv[j] = xj;
+            for (int r = lane; r < j; r += 32) xv[r] -= A[j * Z + r] * xj;
             __syncwarp();
         }
-        if (!singular)
-            for (int r = lane; r < n1; r += 32) params[r < U ? L::ow3 + r : L::ob3] = (float)(xv[r] * sc[r]);
+        if (!s_singular)
+            for (int r = lane; r < n1; r += 32) {
+                const float v = (float)(xv[r] * sc[r]);
+                const int p = r < U ? L::ow3 + r : L::ob3;
+                params[p] = v;
+                if (params2) params2[p] = v;
+            }
     }
 }
 
-// Start of a date: FP64 feature sums -> mean and 1/std (population), Adam state
-// zero, best loss +inf, best parameters = the starting ones.
-__global__ void __launch_bounds__(256) mlp_stats_kernel(const float *feat, int F, uint32_t M, double *part,
-                                                        unsigned *count, float *stats, float *adam, int n_adam,
-                                                        const float *params, float *best, int np, double *best_loss)
+// Input standardisation of every date: block (f, d) computes the mean and
+// 1/std (population) of factor f at date d from FP32 sums of the values less the
+// date's first value (per thread), gathered in FP64 over the block. Factors
+// f >= F get zeros. stats: [n_dates][mean[32] | 1/std[32]].
+__global__ void __launch_bounds__(256) mlp_stats_kernel(const float *feat, int F, uint32_t M, size_t date_stride,
+                                                        float *stats)
 {
     __shared__ double red[2][8];
-    __shared__ int s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int f = 0; f < F; ++f) {
-        double s1 = 0.0, s2 = 0.0;
-        for (uint32_t r = blockIdx.x * 256u + tid; r < M; r += gridDim.x * 256u) {
-            const double x = (double)__ldg(feat + (size_t)f * M + r);
-            s1 += x;
-            s2 += x * x;
-        }
+    const int f = blockIdx.x, d = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *out = stats + (size_t)d * 2 * kIn;
+    if (f >= F) {
+        if (tid == 0) out[f] = out[kIn + f] = 0.f;
+        return;
+    }
+    const float *x = feat + (size_t)d * date_stride + (size_t)f * M;
+    const float c = __ldg(x);
+    float s1 = 0.f, s2 = 0.f;
+    for (uint32_t r = 4u * tid; r < M; r += 4u * blockDim.x) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(x + r));
+        const float a0 = v.x - c, a1 = v.y - c, a2 = v.z - c, a3 = v.w - c;
+        s1 += (a0 + a1) + (a2 + a3);
+        s2 += (a0 * a0 + a1 * a1) + (a2 * a2 + a3 * a3);
+    }
+    double t1 = s1, t2 = s2;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
-        if (lane == 0) {
-            red[0][warp] = s1;
-            red[1][warp] = s2;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double t1 = 0.0, t2 = 0.0;
-            for (int w = 0; w < 8; ++w) {
-                t1 += red[0][w];
-                t2 += red[1][w];
-            }
-            part[blockIdx.x * 64 + f] = t1;
-            part[blockIdx.x * 64 + 32 + f] = t2;
-        }
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, o);
     }
-    for (int i = blockIdx.x * 256 + tid; i < n_adam; i += gridDim.x * 256) adam[i] = 0.f;
-    for (int i = blockIdx.x * 256 + tid; i < np; i += gridDim.x * 256) best[i] = __ldg(params + i);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(count, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (tid < kIn) {
-        const int f = tid;
-        double t1 = 0.0, t2 = 0.0;
-        if (f < F)
-            for (uint32_t b = 0; b < gridDim.x; ++b) {
-                t1 += __ldcg(part + b * 64 + f);
-                t2 += __ldcg(part + b * 64 + 32 + f);
-            }
-        const double mu = t1 / M, var = t2 / M - mu * mu;
-        stats[f] = f < F ? (float)mu : 0.f;
-        stats[kIn + f] = (f < F && var > 0.0) ? (float)(1.0 / sqrt(var)) : 0.f;
+    if (lane == 0) {
+        red[0][warp] = t1;
+        red[1][warp] = t2;
     }
+    __syncthreads();
     if (tid == 0) {
-        *best_loss = 1e300;
-        *count = 0u;
+        double u1 = 0.0, u2 = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            u1 += red[0][w];
+            u2 += red[1][w];
+        }
+        const double m1 = u1 / M, var = u2 / M - m1 * m1;
+        out[f] = (float)(c + m1);
+        out[kIn + f] = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.f;
     }
 }
 
 // ---- host side ----
+// Per-device state: the workspace, counters and status word, and two internal
+// streams. Training runs on the high-priority one; the full-sample loss of each
+// epoch and the predictions run on the low-priority one, beside the next epoch's
+// training (the train kernel occupies one cluster; the passes use the other SMs).
 struct MlpWork {
     void *buf = nullptr;
     size_t cap = 0;          // bytes
@@ -887,18 +978,20 @@ struct MlpWork {
     int *err = nullptr;
     bool attrs = false;
     int max_cluster = 0;     // 16 when a 16-CTA cluster of the train kernel fits, else 8
+    cudaStream_t main = nullptr, side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_train = nullptr, ev_side = nullptr, ev_join = nullptr;
 };
 std::mutex g_mlp_mu;
 MlpWork g_mlp[64];
 
 struct MlpPlan {
-    float *adam, *best, *stats;
-    double *best_loss, *part, *G;
-    int sweep_grid, stats_grid, cluster;
+    float *adam, *best[2], *stats, *snaps;
+    double *best_loss[2], *part_loss, *part_gram, *G;
+    int sweep_grid, cluster;
 };
 
-cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, cudaStream_t st, MlpWork *&wout,
-                       MlpPlan &pl)
+cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, int n_dates, int epochs, cudaStream_t st,
+                       MlpWork *&wout, MlpPlan &pl)
 {
     using L = Layout<64>;
     MlpWork &w = g_mlp[dev];
@@ -925,25 +1018,31 @@ cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, cudaSt
             n16 = 0;
         }
         w.max_cluster = n16 >= 1 ? 16 : 8;
+        int least = 0, greatest = 0;
+        CVA_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CVA_CUDA_TRY(cudaStreamCreateWithPriority(&w.main, cudaStreamNonBlocking, greatest));
+        CVA_CUDA_TRY(cudaStreamCreateWithPriority(&w.side, cudaStreamNonBlocking, least));
+        for (cudaEvent_t *e : {&w.ev_fork, &w.ev_train, &w.ev_side, &w.ev_join})
+            CVA_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         w.attrs = true;
     }
     const uint64_t tiles = M / kRows;
     const int rounds = (int)((tiles + 2 * (uint64_t)sms - 1) / (2 * (uint64_t)sms));
     pl.sweep_grid = (int)((tiles + 2 * (uint64_t)rounds - 1) / (2 * (uint64_t)rounds));
-    pl.stats_grid = sms;
     int cl = 4;
     while (cl < w.max_cluster && 2 * cl < tiles_per_batch) cl *= 2;
     pl.cluster = cl;
     constexpr int Z = L::Z;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t b_adam = al(2 * (size_t)L::NPpad * 4), b_best = al((size_t)L::NPpad * 4), b_stats = al(64 * 4),
-                 b_bl = al(8), b_G = al((size_t)Z * Z * 8);
-    size_t nparts = (size_t)pl.sweep_grid * Z * Z;
-    if ((size_t)pl.stats_grid * 64 > nparts) nparts = (size_t)pl.stats_grid * 64;
-    const size_t b_part = al(nparts * 8);
-    const size_t need = b_adam + b_best + b_stats + b_bl + b_G + b_part;
+    const size_t b_adam = al(2 * (size_t)L::NPpad * 4), b_best = al((size_t)L::NPpad * 4),
+                 b_stats = al((size_t)n_dates * 2 * kIn * 4), b_snaps = al((size_t)epochs * L::NPpad * 4), b_bl = al(8),
+                 b_G = al((size_t)Z * Z * 8), b_pl = al((size_t)pl.sweep_grid * 8),
+                 b_pg = al((size_t)pl.sweep_grid * Z * Z * 8);
+    const size_t need = b_adam + 2 * b_best + b_stats + b_snaps + 2 * b_bl + b_G + b_pl + b_pg;
     if (w.cap < need) {
         CVA_CUDA_TRY(cudaStreamSynchronize(st));
+        CVA_CUDA_TRY(cudaStreamSynchronize(w.main));
+        CVA_CUDA_TRY(cudaStreamSynchronize(w.side));
         if (w.buf) cudaFree(w.buf);
         w.buf = nullptr;
         w.cap = 0;
@@ -955,18 +1054,46 @@ cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, cudaSt
         if (cudaMalloc(&w.err, sizeof(int)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: status");
     }
     char *p = static_cast<char *>(w.buf);
-    pl.adam = reinterpret_cast<float *>(p);
-    p += b_adam;
-    pl.best = reinterpret_cast<float *>(p);
-    p += b_best;
-    pl.stats = reinterpret_cast<float *>(p);
-    p += b_stats;
-    pl.best_loss = reinterpret_cast<double *>(p);
-    p += b_bl;
-    pl.G = reinterpret_cast<double *>(p);
-    p += b_G;
-    pl.part = reinterpret_cast<double *>(p);
+    auto take = [&](size_t b) {
+        char *r = p;
+        p += b;
+        return r;
+    };
+    pl.adam = reinterpret_cast<float *>(take(b_adam));
+    pl.best[0] = reinterpret_cast<float *>(take(b_best));
+    pl.best[1] = reinterpret_cast<float *>(take(b_best));
+    pl.stats = reinterpret_cast<float *>(take(b_stats));
+    pl.snaps = reinterpret_cast<float *>(take(b_snaps));
+    pl.best_loss[0] = reinterpret_cast<double *>(take(b_bl));
+    pl.best_loss[1] = reinterpret_cast<double *>(take(b_bl));
+    pl.G = reinterpret_cast<double *>(take(b_G));
+    pl.part_loss = reinterpret_cast<double *>(take(b_pl));
+    pl.part_gram = reinterpret_cast<double *>(take(b_pg));
     wout = &w;
+    return CVA_OK;
+}
+
+// 2-D tensor map of one date's feature array [F][M] (FP32, path index innermost):
+// boxes of 128 paths x F features. The encoder is the driver's, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cva_status features_map(CUtensorMap *tm, const float *feat, int F, uint64_t M)
+{
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        CVA_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (!fn || q != cudaDriverEntryPointSuccess) return fail(CVA_ECUDA, "mlp: cuTensorMapEncodeTiled not available");
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)F};
+    const cuuint64_t strides[1] = {(cuuint64_t)M * 4u};
+    const cuuint32_t box[2] = {(cuuint32_t)kRows, (cuuint32_t)F};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(feat), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CVA_ECUDA, "mlp: tensor map encoding failed (" + std::to_string((int)r) + ")");
     return CVA_OK;
 }
 
@@ -1018,12 +1145,26 @@ cva_status mlp_finish(cudaStream_t st)
     return CVA_OK;
 }
 
-cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t M, int U, int n_batches,
-                          int epochs, float lr, int max_steps, float *params_dev, float *pred_dev,
-                          float *grad_out_dev, float *loss_out_dev, cudaStream_t st)
+// Algorithm 2 over dates n_dates-1 .. 0 of date-major arrays (Algorithm 1 when
+// n_dates = 1). Per date, on the internal streams (forked from and joined back
+// to st):
+//   main: E train launches (one per epoch; epoch E/2 followed by the Gram pass
+//         and the closed-form refit), the date's last loss pass gating the next
+//         date, whose first launch starts from the best parameters;
+//   side: the full-sample loss of every epoch (deciding the best parameters, in
+//         epoch order) and the predictions of the best network.
+// Each epoch's parameters are snapshotted for its loss pass; the best parameters
+// and best loss alternate between two buffers by date parity, so that a date's
+// prediction pass can overlap the next date's training.
+cva_status mlp_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride, int n_dates,
+                         int F, uint64_t M, int U, int n_batches, int epochs, float lr, int max_steps,
+                         float *params_dev, float *pred0, float *grad_out_dev, float *loss_out_dev, cudaStream_t st)
 {
     cva_status r = mlp_check_args(F, M, U, n_batches, epochs);
     if (r != CVA_OK) return r;
+    if (n_dates < 1) return fail(CVA_EINVAL, "mlp: no dates");
+    if ((reinterpret_cast<uintptr_t>(feat0) | reinterpret_cast<uintptr_t>(targ0)) & 15u)
+        return fail(CVA_EINVAL, "mlp: features and targets must be 16-byte aligned (TMA and bulk copies)");
     using L = Layout<64>;
     constexpr int Z = L::Z;
     const int tiles_per_batch = (int)(M / n_batches / kRows);
@@ -1034,30 +1175,18 @@ cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t 
     std::lock_guard<std::mutex> lk(g_mlp_mu);
     MlpWork *w = nullptr;
     MlpPlan pl;
-    r = mlp_prepare(dev, sms, M, tiles_per_batch, st, w, pl);
+    r = mlp_prepare(dev, sms, M, tiles_per_batch, n_dates, epochs, st, w, pl);
     if (r != CVA_OK) return r;
-    float *adam_m = pl.adam, *adam_v = pl.adam + L::NPpad;
+    const cudaStream_t mst = w->main, sst = w->side;
 
-    mlp_stats_kernel<<<pl.stats_grid, 256, 0, st>>>(feat, F, (uint32_t)M, pl.part, w->count + 0, pl.stats, pl.adam,
-                                                     2 * L::NPpad, params_dev, pl.best, L::NP, pl.best_loss);
+    CVA_CUDA_TRY(cudaEventRecord(w->ev_fork, st));
+    CVA_CUDA_TRY(cudaStreamWaitEvent(mst, w->ev_fork, 0));
+    CVA_CUDA_TRY(cudaStreamWaitEvent(sst, w->ev_fork, 0));
+
+    mlp_stats_kernel<<<dim3(kIn, (unsigned)n_dates), 256, 0, mst>>>(feat0, F, (uint32_t)M, feat_stride, pl.stats);
     CVA_CUDA_TRY(cudaGetLastError());
 
-    SweepArgs sw = {};
-    sw.feat = feat;
-    sw.targ = targ;
-    sw.F = F;
-    sw.M = (uint32_t)M;
-    sw.stats = pl.stats;
-    sw.part = pl.part;
-    sw.count = w->count + 1;
-    sw.best_loss = pl.best_loss;
-    sw.best = pl.best;
-    sw.loss_out = loss_out_dev;
-    sw.err = w->err;
-
     TrainArgs ta = {};
-    ta.feat = feat;
-    ta.targ = targ;
     ta.F = F;
     ta.M = (uint32_t)M;
     ta.tiles_per_batch = tiles_per_batch;
@@ -1066,58 +1195,105 @@ cva_status mlp_train_date(const float *feat, int F, const float *targ, uint64_t 
     ta.beta2 = 0.999f;
     ta.eps = 1e-8f;
     ta.params = params_dev;
-    ta.adam_m = adam_m;
-    ta.adam_v = adam_v;
-    ta.stats = pl.stats;
+    ta.adam_m = pl.adam;
+    ta.adam_v = pl.adam + L::NPpad;
     ta.grad_out = grad_out_dev;
     ta.err = w->err;
 
+    SweepArgs sw = {};
+    sw.F = F;
+    sw.M = (uint32_t)M;
+    sw.count = w->count + 1;
+    sw.part = pl.part_loss;
+    sw.loss_out = loss_out_dev;
+    sw.err = w->err;
+
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)pl.cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3((unsigned)pl.cluster);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = L::bytes_train;
-    cfg.stream = st;
+    cfg.stream = mst;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
 
+    bool stopped = false;
     int steps_left = max_steps > 0 ? max_steps : INT_MAX;
-    for (int e = 1; e <= epochs; ++e) {
-        ta.n_steps = n_batches < steps_left ? n_batches : steps_left;
-        ta.step0 = (e - 1) * n_batches;
-        ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;   // on once the refit of epoch floor(E/2) ran
-        CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, mlp_train_kernel<64>, ta));
-        steps_left -= ta.n_steps;
-        if (max_steps > 0 && steps_left <= 0) return CVA_OK;
-        if (e == epochs / 2) {
-            sw.mode = 1;
-            sw.theta = params_dev;
-            mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, st>>>(sw);
-            CVA_CUDA_TRY(cudaGetLastError());
-            mlp_refit_kernel<64><<<Z, 128, 0, st>>>(pl.part, pl.sweep_grid, pl.G, w->count + 2, params_dev);
+    for (int d = n_dates - 1; d >= 0 && !stopped; --d) {
+        const int par = d & 1;
+        const float *feat = feat0 + (size_t)d * feat_stride, *targ = targ0 + (size_t)d * targ_stride;
+        CUtensorMap tm;
+        r = features_map(&tm, feat, F, M);
+        if (r != CVA_OK) return r;
+        ta.feat = sw.feat = feat;
+        ta.targ = sw.targ = targ;
+        ta.stats = sw.stats = pl.stats + (size_t)d * 2 * kIn;
+        ta.best = pl.best[par];
+        ta.best_loss = pl.best_loss[par];
+        sw.best = pl.best[par];
+        sw.best_loss = pl.best_loss[par];
+        for (int e = 1; e <= epochs; ++e) {
+            float *snap = pl.snaps + (size_t)(e - 1) * L::NPpad;
+            ta.init = (e == 1 && d < n_dates - 1) ? pl.best[par ^ 1] : params_dev;   // Algorithm 2's warm start
+            ta.snap = snap;
+            ta.n_steps = n_batches < steps_left ? n_batches : steps_left;
+            ta.step0 = (e - 1) * n_batches;
+            ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;   // on once the refit of epoch floor(E/2) ran
+            CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, mlp_train_kernel<64>, ta, tm));
+            steps_left -= ta.n_steps;
+            if (max_steps > 0 && steps_left <= 0) {
+                stopped = true;
+                break;
+            }
+            if (e == epochs / 2) {
+                SweepArgs g = sw;
+                g.mode = 1;
+                g.theta = params_dev;
+                g.part = pl.part_gram;
+                g.loss_out = nullptr;
+                mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, mst>>>(g, tm);
+                CVA_CUDA_TRY(cudaGetLastError());
+                mlp_refit_kernel<64><<<Z, 256, 0, mst>>>(pl.part_gram, pl.sweep_grid, pl.G, w->count + 2, params_dev,
+                                                         snap);
+                CVA_CUDA_TRY(cudaGetLastError());
+            }
+            // the epoch's loss on the side stream, from its snapshot
+            CVA_CUDA_TRY(cudaEventRecord(w->ev_train, mst));
+            CVA_CUDA_TRY(cudaStreamWaitEvent(sst, w->ev_train, 0));
+            sw.mode = 0;
+            sw.theta = snap;
+            sw.epoch = e;
+            mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, sst>>>(sw, tm);
             CVA_CUDA_TRY(cudaGetLastError());
         }
-        sw.mode = 0;
-        sw.theta = params_dev;
-        sw.epoch = e;
-        mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, st>>>(sw);
-        CVA_CUDA_TRY(cudaGetLastError());
+        if (stopped) break;
+        // the best parameters are known once the last loss pass ran: the next date
+        // (main) starts from them; the predictions (side) overlap its training
+        CVA_CUDA_TRY(cudaEventRecord(w->ev_side, sst));
+        CVA_CUDA_TRY(cudaStreamWaitEvent(mst, w->ev_side, 0));
+        if (pred0) {
+            SweepArgs pv = sw;
+            pv.mode = 2;
+            pv.theta = pl.best[par];
+            pv.pred = pred0 + (size_t)d * M;
+            pv.params_out = nullptr;
+            mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, sst>>>(pv, tm);
+            CVA_CUDA_TRY(cudaGetLastError());
+        }
+        if (d == 0)
+            CVA_CUDA_TRY(cudaMemcpyAsync(params_dev, pl.best[par], L::NP * sizeof(float), cudaMemcpyDeviceToDevice,
+                                         mst));
     }
-    // the best parameters become the current ones; predictions with them
-    if (pred_dev) {
-        sw.mode = 2;
-        sw.theta = pl.best;
-        sw.pred = pred_dev;
-        sw.params_out = params_dev;
-        mlp_sweep_kernel<64><<<pl.sweep_grid, kThreads, L::bytes_sweep, st>>>(sw);
-        CVA_CUDA_TRY(cudaGetLastError());
-    } else {
-        CVA_CUDA_TRY(cudaMemcpyAsync(params_dev, pl.best, L::NP * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    }
+    CVA_CUDA_TRY(cudaEventRecord(w->ev_join, sst));
+    CVA_CUDA_TRY(cudaStreamWaitEvent(mst, w->ev_join, 0));
+    CVA_CUDA_TRY(cudaEventRecord(w->ev_join, mst));
+    CVA_CUDA_TRY(cudaStreamWaitEvent(st, w->ev_join, 0));
     return CVA_OK;
 }
 

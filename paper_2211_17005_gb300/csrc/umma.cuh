@@ -135,6 +135,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 64 consecutive columns (four x16 loads in flight, one wait). The empty asm
+// statements after the wait tie every value to it, so that no use of a loaded
+// register can be scheduled before the load has completed.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
+{
+    float a[16], b[16], c[16], d[16];
+    tmem_ld16(taddr, a);
+    tmem_ld16(taddr + 16u, b);
+    tmem_ld16(taddr + 32u, c);
+    tmem_ld16(taddr + 48u, d);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = a[i];
+        v[16 + i] = b[i];
+        v[32 + i] = c[i];
+        v[48 + i] = d[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 64; ++i) asm volatile("" : "+f"(v[i]));
+}
+
+// ---- bulk asynchronous copies global -> shared, completing on an mbarrier ----
+// the mbarrier's current phase expects `bytes` more transaction bytes (one arrival)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// `bytes` (a multiple of 16) from 16-byte aligned global `src` to 16-byte aligned
+// shared address `dst` of this CTA; completes `bytes` transactions on `bar`
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 2-D tiled TMA load: the box of the tensor map at coordinates (x, y) (x innermost;
+// x * element size a multiple of 16 bytes) into 128-byte aligned shared address
+// `dst`; completes the box's bytes on `bar`. `tmap` is the generic address of a
+// CUtensorMap in kernel-parameter (grid-constant) memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int32_t x, int32_t y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ---- thread-block clusters: rank, size, barrier, distributed shared memory ----
 __device__ __forceinline__ uint32_t cluster_rank()
 {
@@ -177,6 +229,23 @@ __device__ __forceinline__ float ld_cluster_f32(uint32_t addr)
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
 {
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// 16-byte forms (addr 16-byte aligned)
+__device__ __forceinline__ float4 ld_cluster_f32x4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ void st_cluster_f32x4(uint32_t addr, float4 v)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
 }
 
 // ---- asynchronous global -> shared copies of 4 bytes (per-thread staging) ----
