@@ -161,6 +161,12 @@ cva_status mlp_finish(cudaStream_t st);
 cva_status mlp_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride, int n_dates,
                          int F, uint64_t M, int U, int n_batches, int epochs, float lr, int max_steps,
                          float *params_dev, float *pred0, float *grad_out_dev, float *loss_out_dev, cudaStream_t st);
+// The same at hidden width 128 on a cooperative grid (mlp_wide.cu); count and err
+// are the device counters and status word that mlp_begin cleared.
+cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride,
+                              int n_dates, int F, uint64_t M, int n_batches, int epochs, float lr, int max_steps,
+                              float *params_dev, float *pred0, float *grad_out_dev, float *loss_out_dev,
+                              unsigned *count, int *err, cudaStream_t st);
 
 // CVA_0 reduction (reduce.cu).
 cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);

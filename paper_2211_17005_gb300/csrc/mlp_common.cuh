@@ -1,0 +1,257 @@
+// Pieces shared by the neural-regression kernels of both hidden widths (mlp.cu,
+// mlp_wide.cu): tile constants, BF16 packing, warp reductions, the input
+// standardisation of every date, the closed-form output-layer refit (FP64
+// Cholesky) and the TMA descriptor of a date's feature array. Each translation
+// unit that includes this file gets its own copy (internal linkage).
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <string>
+
+#include "cva_internal.h"
+
+namespace cva {
+namespace {
+
+constexpr int kRows = 128;        // rows per tile (tcgen05 M)
+constexpr int kIn = 32;           // padded input width
+constexpr uint32_t kMbarPolls = 1u << 26;
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    return (uint32_t)bf16_bits(a) | ((uint32_t)bf16_bits(b) << 16);
+}
+
+__device__ __forceinline__ uint4 pack8(const float *v)
+{
+    return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums of 64 columns over the 32 lanes of a warp by recursive halving (levels
+// 16, 8, 4, 2, 1): lane l ends with the totals of columns 2l and 2l + 1.
+__device__ __forceinline__ float2 column_sums64(const float (&v)[64], int lane)
+{
+    float a32[32], a16[16], a8[8], a4[4];
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2, u1 = lane & 1;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const float send = u16 ? v[i] : v[32 + i], keep = u16 ? v[32 + i] : v[i];
+        a32[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float send = u8 ? a32[i] : a32[16 + i], keep = u8 ? a32[16 + i] : a32[i];
+        a16[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float send = u4 ? a16[i] : a16[8 + i], keep = u4 ? a16[8 + i] : a16[i];
+        a8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = u2 ? a8[i] : a8[4 + i], keep = u2 ? a8[4 + i] : a8[i];
+        a4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    float r[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = u1 ? a4[i] : a4[2 + i], keep = u1 ? a4[2 + i] : a4[i];
+        r[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    }
+    return make_float2(r[0], r[1]);
+}
+
+// Refit of (w3, b3) at epoch floor(E/2) for hidden width U: block i sums row i
+// of the CTAs' Gram partials of Z = [h2 | 1 | y - mu] (fixed order); the last
+// block solves the Jacobi-scaled normal equations of [h2 | 1] (w3, b3) = y - mu by
+// FP64 Cholesky (right-looking, the trailing update spread over the block) and two
+// triangular solves. A numerically singular system keeps the old (w3, b3). The
+// new values go to params and, when not null, to params2. Dynamic shared memory:
+// refit_smem_bytes(U).
+__host__ __device__ constexpr size_t refit_smem_bytes(int U)
+{
+    return ((size_t)(U + 2) * (U + 2) + 3 * (size_t)(U + 1) + 256) * sizeof(double);
+}
+
+template <int U>
+__global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int nparts, double *G, unsigned *count,
+                                                        float *params, float *params2)
+{
+    constexpr int Z = U + 2, n1 = U + 1;
+    constexpr int ow3 = 34 * U + U * U, ob3 = ow3 + U;
+    extern __shared__ double refit_smem[];
+    double *A = refit_smem, *sc = A + Z * Z, *xv = sc + n1, *inv_d = xv + n1, *half = inv_d + n1;
+    __shared__ int s_last, s_singular;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int i = blockIdx.x;
+    {   // row i of the total Gram matrix: nh fixed ranges of the partials per column,
+        // added in range order
+        const int nh = (int)blockDim.x / Z > 0 ? (int)blockDim.x / Z : 1;
+        for (int t = tid; t < nh * Z; t += blockDim.x) {
+            const int c = t % Z, h = t / Z;
+            double sum = 0.0;
+            for (int b = nparts * h / nh; b < nparts * (h + 1) / nh; ++b) sum += __ldg(part + (size_t)b * Z * Z + i * Z + c);
+            half[t] = sum;
+        }
+        __syncthreads();
+        for (int c = tid; c < Z; c += blockDim.x) {
+            double sum = 0.0;
+            for (int h = 0; h < nh; ++h) sum += half[h * Z + c];
+            G[i * Z + c] = sum;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int e = tid; e < Z * Z; e += blockDim.x) A[e] = __ldcg(G + e);
+    if (tid == 0) {
+        *count = 0u;
+        s_singular = 0;
+    }
+    __syncthreads();
+    for (int j = tid; j < n1; j += blockDim.x) sc[j] = A[j * Z + j] > 0.0 ? 1.0 / sqrt(A[j * Z + j]) : 0.0;
+    __syncthreads();
+    for (int e = tid; e < n1 * (n1 + 1); e += blockDim.x) {
+        const int r = e / (n1 + 1), c = e % (n1 + 1);
+        A[r * Z + c] *= sc[r] * (c < n1 ? sc[c] : 1.0);
+    }
+    __syncthreads();
+    // lower Cholesky factor in place: column j, then the trailing lower triangle;
+    // thread t updates column j + 1 + (t mod U), rows c + (t / U) + k (blockDim / U)
+    for (int j = 0; j < n1; ++j) {
+        if (tid == 0) {
+            double d = A[j * Z + j];
+            if (!(d > 1e-12)) {
+                s_singular = 1;
+                d = 1.0;
+            }
+            d = sqrt(d);
+            A[j * Z + j] = d;
+            inv_d[j] = 1.0 / d;
+        }
+        __syncthreads();
+        const double r_d = inv_d[j];
+        for (int r = j + 1 + tid; r < n1; r += blockDim.x) A[r * Z + j] *= r_d;
+        __syncthreads();
+        const int c = j + 1 + (tid % U);   // U >= n1 - 1 - j columns, blockDim / U row groups
+        if (c < n1) {
+            const double lcj = A[c * Z + j];
+            for (int r = c + tid / U; r < n1; r += (int)blockDim.x / U) A[r * Z + c] -= A[r * Z + j] * lcj;
+        }
+        __syncthreads();
+    }
+    if (tid < 32) {   // L y = b, then L^T x = y (column-oriented, one warp)
+        for (int r = lane; r < n1; r += 32) xv[r] = A[r * Z + n1];
+        __syncwarp();
+        for (int j = 0; j < n1; ++j) {
+            const double yj = xv[j] * inv_d[j];
+            __syncwarp();
+            if (lane == 0) xv[j] = yj;
+            for (int r = j + 1 + lane; r < n1; r += 32) xv[r] -= A[r * Z + j] * yj;
+            __syncwarp();
+        }
+        for (int j = n1 - 1; j >= 0; --j) {
+            const double xj = xv[j] * inv_d[j];
+            __syncwarp();
+            if (lane == 0) xv[j] = xj;
+            for (int r = lane; r < j; r += 32) xv[r] -= A[j * Z + r] * xj;
+            __syncwarp();
+        }
+        if (!s_singular)
+            for (int r = lane; r < n1; r += 32) {
+                const float v = (float)(xv[r] * sc[r]);
+                const int p = r < U ? ow3 + r : ob3;
+                params[p] = v;
+                if (params2) params2[p] = v;
+            }
+    }
+}
+
+// Input standardisation of every date: block (f, d) computes the mean and
+// 1/std (population) of factor f at date d from FP32 sums of the values less the
+// date's first value (per thread), gathered in FP64 over the block. Factors
+// f >= F get zeros. stats: [n_dates][mean[32] | 1/std[32]].
+__global__ void __launch_bounds__(256) mlp_stats_kernel(const float *feat, int F, uint32_t M, size_t date_stride,
+                                                        float *stats)
+{
+    __shared__ double red[2][8];
+    const int f = blockIdx.x, d = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *out = stats + (size_t)d * 2 * kIn;
+    if (f >= F) {
+        if (tid == 0) out[f] = out[kIn + f] = 0.f;
+        return;
+    }
+    const float *x = feat + (size_t)d * date_stride + (size_t)f * M;
+    const float c = __ldg(x);
+    float s1 = 0.f, s2 = 0.f;
+    for (uint32_t r = 4u * tid; r < M; r += 4u * blockDim.x) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(x + r));
+        const float a0 = v.x - c, a1 = v.y - c, a2 = v.z - c, a3 = v.w - c;
+        s1 += (a0 + a1) + (a2 + a3);
+        s2 += (a0 * a0 + a1 * a1) + (a2 * a2 + a3 * a3);
+    }
+    double t1 = s1, t2 = s2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+        t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = t1;
+        red[1][warp] = t2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double u1 = 0.0, u2 = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            u1 += red[0][w];
+            u2 += red[1][w];
+        }
+        const double m1 = u1 / M, var = u2 / M - m1 * m1;
+        out[f] = (float)(c + m1);
+        out[kIn + f] = var > 0.0 ? (float)(1.0 / sqrt(var)) : 0.f;
+    }
+}
+
+// 2-D tensor map of one date's feature array [F][M] (FP32, path index innermost):
+// boxes of 128 paths x F features. The encoder is the driver's, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cva_status features_map(CUtensorMap *tm, const float *feat, int F, uint64_t M)
+{
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        CVA_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (!fn || q != cudaDriverEntryPointSuccess) return fail(CVA_ECUDA, "mlp: cuTensorMapEncodeTiled not available");
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)F};
+    const cuuint64_t strides[1] = {(cuuint64_t)M * 4u};
+    const cuuint32_t box[2] = {(cuuint32_t)kRows, (cuuint32_t)F};
+    const cuuint32_t estr[2] = {1u, 1u};
+    const CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(feat), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CVA_ECUDA, "mlp: tensor map encoding failed (" + std::to_string((int)r) + ")");
+    return CVA_OK;
+}
+
+}  // namespace
+}  // namespace cva

@@ -1,0 +1,998 @@
+// Neural regression of Sec. 2 at hidden width 128: the NN+ network of eq. (e:nnp)
+// with two hidden ReLU layers of 128 units on the F <= 32 standardised factors,
+// trained at each date by Algorithm 1 (BaseAlg) inside Algorithm 2 (backward
+// learning), for samples large enough that one Adam batch covers many 128-path
+// tiles (2^20 paths in 32 batches: 256 tiles per step).
+//
+// Kernels of one date, in order on one stream:
+//   wide_train_kernel   one epoch of Adam steps on a cooperative grid (one CTA per
+//                       SM, at most one tile per CTA and round)
+//   wide_sweep_kernel   full-sample forward passes on all SMs: the epoch loss and
+//                       the best-parameter choice, the refit's Gram matrix, or the
+//                       predictions
+//   mlp_refit_kernel    (shared) Gram sum, FP64 Cholesky, new (w3, b3)
+//
+// Every CTA owns one 128-row tile slot worked by its two warpgroups; warpgroup h
+// takes hidden columns [64 h, 64 h + 64) in every epilogue. Per tile:
+//   GEMM1  D = X W1^T                      (K = 32 padded inputs, N = 128)
+//   GEMM2  D = H1 W2^T                     (K = 128, N = 128)
+//   GEMM3  D = dH2 W2                      (K = 128; the W2 image read MN-major)
+//   GEMMW  DW2 (+)= dH2^T [H1 | 1]          (M = 128, N = 144, K = the 128 paths)
+//          DW1 (+)= dH1^T [X | 1]           (M = 128, N = 48)
+// with the per-path rows A = [dH2 | dH1] (256 wide) and B = [H1 | 1 | X | 1]
+// (192 wide) in K-major core matrices, read MN-major by GEMMW. BF16 operands in
+// shared memory, FP32 accumulators in tensor memory (D at columns [0, 128), DW2 at
+// [128, 272), DW1 at [320, 368)); biases, ReLU, the output layer and the loss in
+// FP32 on the CUDA cores.
+//
+// One Adam step on the grid: every CTA writes its FP32 gradient partial to global
+// memory (column order q); after a grid barrier CTA c owns slice c of the
+// parameter vector: it sums the slice over all CTAs' partials (fixed order), applies
+// Adam (moments and FP32 master values in global memory) and writes the new FP32
+// values and their BF16 images; after a second grid barrier every CTA reloads the
+// images and the FP32 vectors. The grid barrier is a per-CTA generation flag with
+// bounded waits (a wait that gives up sets the status word; every other wait then
+// ends at once).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <climits>
+#include <mutex>
+#include <string>
+
+#include "cva_internal.h"
+#include "mlp_common.cuh"
+#include "umma.cuh"
+
+namespace cva {
+
+namespace {
+
+constexpr int kWThreads = 256;
+constexpr uint32_t kGridPolls = 1u << 22;
+
+struct WL {
+    static constexpr int U = 128;
+    static constexpr int NP = 35 * U + U * U + 2;
+    static constexpr int NPpad = (NP + 63) / 64 * 64;
+    static constexpr int oW1 = 0, ob1 = kIn * U, oW2 = ob1 + U, ob2 = oW2 + U * U, ow3 = ob2 + U, ob3 = ow3 + U,
+                         omu = ob3 + 1;
+    static constexpr int Z = U + 2;
+    static constexpr int wA = 2 * U, wB = U + 64;                 // row widths (elements)
+    static constexpr int cOne1 = U, cX = U + 16, cOne2 = U + 48;  // columns of B
+    // shared memory (bytes)
+    static constexpr int sA = 0;
+    static constexpr int sB = sA + kRows * wA * 2;
+    static constexpr int sW1 = sB + kRows * wB * 2;               // W1 image [U][32], K-major
+    static constexpr int sW2 = sW1 + U * kIn * 2;                 // W2 image [U][U], K-major
+    static constexpr int sVec = sW2 + U * U * 2;                  // b1 | b2 | w3 | b3, mu (FP32)
+    static constexpr int sStage = sVec + 512 * 4;                 // [kIn + 1][128] FP32 inputs, target
+    static constexpr int sStats = sStage + (kIn + 1) * kRows * 4; // mean[32], 1/std[32]
+    static constexpr int sGsl = sStats + 2 * kIn * 4;             // [8 warps][66] output-layer gradient sums
+    static constexpr int sOut = sGsl + 8 * 66 * 4;                // [2][128] half outputs
+    static constexpr int sRed = sOut + 2 * kRows * 4;             // [256] float4 owner sums
+    static constexpr int bytes = sRed + kWThreads * 16;
+    static constexpr int img_elems = U * kIn + U * U;             // BF16 images of W1 | W2
+    static constexpr uint32_t tmem_cols = 512;
+    static constexpr uint32_t cD = 0, cW2 = 128, cW1 = 320;
+    // vector offsets inside sVec
+    static constexpr int vb1 = 0, vb2 = U, vw3 = 2 * U, vb3 = 3 * U, vmu = 3 * U + 1;
+
+    // W1 and W2 in column order (q) for the partials and the master copy; global
+    // parameters keep the row order (p)
+    __host__ __device__ static int p_of(int q)
+    {
+        if (q < ob1) return oW1 + (q % U) * kIn + q / U;
+        if (q >= oW2 && q < ob2) {
+            const int t = q - oW2;
+            return oW2 + (t % U) * U + t / U;
+        }
+        return q;
+    }
+};
+static_assert(WL::sStage % 128 == 0, "TMA destination must be 128-byte aligned");
+static_assert(WL::bytes <= 227 * 1024, "shared memory");
+
+// byte offset of element c of row r in a BF16 row buffer of width w (K-major core
+// matrices of 8 rows x 16 bytes)
+__host__ __device__ constexpr uint32_t wrow_off(uint32_t r, uint32_t c, uint32_t w)
+{
+    return (r >> 3) * (w / 8u) * 128u + (c >> 3) * 128u + (r & 7u) * 16u + (c & 7u) * 2u;
+}
+
+struct WTrainArgs {
+    const float *targ;             // [M] targets (features through the tensor map)
+    int F;
+    uint32_t M;
+    int tiles_per_batch, n_steps, step0, pos;
+    float lr, beta1, beta2, eps;
+    const float *init;             // [NP] row order: parameters at the start of the launch
+    float *params;                 // [NP] row order: parameters at its end
+    float *snap;                   // [NP] row order: a second copy of them (nullable)
+    float *best;                   // step0 == 0: receives init ...
+    double *best_loss;             // ... and +inf
+    float *adam_m, *adam_v;        // [NPpad] q order; step0 == 0: start at zero
+    float *gq;                     // [NPpad] q order: FP32 master parameters
+    uint16_t *gimg;                // [img_elems] BF16 images of W1 | W2 (shared-memory layout)
+    float *gpart;                  // [grid][NPpad] q order: gradient partials
+    unsigned *flags;               // [grid] barrier generations, zero at launch
+    const float *stats;            // mean[32], 1/std[32]
+    float *grad_out;               // [NP] row order: gradient of the first step (nullable)
+    int *err;
+};
+
+struct WSweepArgs {
+    const float *targ;
+    int F;
+    uint32_t M;
+    int mode;                      // 0 loss, 1 Gram of the refit, 2 predictions
+    const float *theta;            // [NP] row order
+    const float *stats;
+    double *part;                  // per-CTA partials
+    unsigned *count;               // last-CTA ticket (mode 0)
+    double *best_loss;
+    float *best;
+    float *loss_out;               // [epochs] (nullable)
+    int epoch;
+    float *pred;                   // mode 2
+    int *err;
+};
+
+// Grid barrier: every CTA publishes its generation in its own flag and waits until
+// all flags reach it. Bounded: a wait that gives up (or sees the status word set)
+// sets the status word and returns false; all threads get the same answer.
+__device__ __forceinline__ bool grid_barrier(unsigned *flags, unsigned nblocks, unsigned &gen, int *err)
+{
+    __threadfence();
+    __syncthreads();
+    gen += 1u;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + blockIdx.x), "r"(gen) : "memory");
+    }
+    int ok = 1;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        uint32_t it = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flags + b) : "memory");
+            if ((int)(v - gen) >= 0) break;
+            if (++it > kGridPolls || *(volatile int *)err) {
+                ok = 0;
+                atomicExch(err, 3);
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    __threadfence();
+    return __syncthreads_and(ok) != 0;
+}
+
+struct WNet {
+    unsigned char *smem;
+    uint32_t tmem = 0;
+    uint64_t *mbar, *sbar;
+    uint32_t phase = 0, sphase = 0;
+    bool pending = false;
+    int tid, warp, lane, row, half;
+    float *vec, *stage;
+    const float *mean, *istd;
+
+    __device__ WNet(unsigned char *s, uint64_t *mbars) : smem(s)
+    {
+        tid = threadIdx.x;
+        warp = tid >> 5;
+        lane = tid & 31;
+        row = tid & 127;
+        half = tid >> 7;
+        mbar = mbars;
+        sbar = mbars + 1;
+        vec = reinterpret_cast<float *>(smem + WL::sVec);
+        stage = reinterpret_cast<float *>(smem + WL::sStage);
+        mean = reinterpret_cast<const float *>(smem + WL::sStats);
+        istd = mean + kIn;
+    }
+
+    __device__ uint32_t saddr(int off) const { return umma::smem_u32(smem + off); }
+    __device__ uint32_t taddr(uint32_t col) const { return tmem + ((uint32_t)((warp & 3) * 32) << 16) + col; }
+
+    // one tensor-core step of the CTA: operands written -> issue (thread 0) ->
+    // completion; side() runs in every thread after the barrier while the tensor
+    // core works
+    template <class Issue, class Side>
+    __device__ bool mma(Issue issue, bool pre_ok, Side side)
+    {
+        umma::fence_proxy_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (tid == 0) {
+            issue();
+            umma::commit(mbar);
+        }
+        side();
+        const bool done = umma::mbar_wait(mbar, phase, kMbarPolls);
+        phase ^= 1u;
+        umma::fence_after_sync();
+        return __syncthreads_and(done && pre_ok) != 0;
+    }
+    template <class Issue>
+    __device__ bool mma(Issue issue)
+    {
+        return mma(issue, true, [] {});
+    }
+
+    // D = A B^T: A = K columns of a row buffer (width w, from column c0, K-major),
+    // B = a K-major image [N][K]
+    __device__ void gemm_rows(uint32_t d, int a_off, uint32_t w, int c0, int b_off, int K, int N) const
+    {
+        const uint32_t id = umma::idesc_bf16_f32(kRows, (uint32_t)N);
+        const uint32_t a0 = saddr(a_off) + (uint32_t)(c0 / 8) * 128u, b0 = saddr(b_off);
+        const uint32_t asbo = (w / 8u) * 128u, bsbo = (uint32_t)(K / 8) * 128u;
+        for (int kk = 0; kk < K / 16; ++kk)
+            umma::mma_bf16(tmem + d, umma::smem_desc(a0 + kk * 256u, 128u, asbo), umma::smem_desc(b0 + kk * 256u, 128u, bsbo),
+                           id, kk > 0 ? 1u : 0u);
+    }
+
+    // D = dH2 W2: A = the dH2 columns of A (K = U), B = the W2 image read MN-major
+    __device__ void gemm_w2t(uint32_t d) const
+    {
+        const uint32_t id = umma::idesc_bf16_f32(kRows, WL::U) | umma::kMnMajorB;
+        const uint32_t a0 = saddr(WL::sA), b0 = saddr(WL::sW2), lbo = (WL::U / 8) * 128u;
+        const uint32_t asbo = (WL::wA / 8u) * 128u;
+        for (int kk = 0; kk < WL::U / 16; ++kk)
+            umma::mma_bf16(tmem + d, umma::smem_desc(a0 + kk * 256u, 128u, asbo),
+                           umma::smem_desc(b0 + kk * 2u * lbo, lbo, 128u), id, kk > 0 ? 1u : 0u);
+    }
+
+    // D (+)= X^T Y over the tile's 128 rows: X = 128 columns of a row buffer from
+    // column xc (width xw), Y = N columns of a row buffer from column yc (width yw),
+    // both read MN-major
+    __device__ void gemm_paths(uint32_t d, int x_off, uint32_t xw, int xc, int y_off, uint32_t yw, int yc, int N,
+                               bool acc) const
+    {
+        const uint32_t id = umma::idesc_bf16_f32(kRows, (uint32_t)N) | umma::kMnMajorA | umma::kMnMajorB;
+        const uint32_t x0 = saddr(x_off) + (uint32_t)(xc / 8) * 128u, y0 = saddr(y_off) + (uint32_t)(yc / 8) * 128u;
+        const uint32_t xl = (xw / 8u) * 128u, yl = (yw / 8u) * 128u;
+        for (int kk = 0; kk < kRows / 16; ++kk)
+            umma::mma_bf16(tmem + d, umma::smem_desc(x0 + kk * 2u * xl, xl, 128u), umma::smem_desc(y0 + kk * 2u * yl, yl, 128u),
+                           id, (acc || kk > 0) ? 1u : 0u);
+    }
+
+    // ---- inputs ----
+    // request the tile of paths [path0, path0 + 128): F feature rows (one TMA box)
+    // and the target row; called by every thread once all are done reading the
+    // staging area
+    __device__ void prefetch(const CUtensorMap *tm, const float *targ, int F, uint32_t path0)
+    {
+        if (tid == 32) {
+            umma::mbar_arrive_expect_tx(sbar, (uint32_t)(F + 1) * kRows * 4u);
+            umma::tma_load_2d(umma::smem_u32(stage), tm, (int32_t)path0, 0, sbar);
+            umma::bulk_g2s(umma::smem_u32(stage + kIn * kRows), targ + path0, kRows * 4u, sbar);
+        }
+        pending = true;
+    }
+
+    // wait for the staged tile; this thread's 16 standardised inputs into the X
+    // columns of B; y receives the target
+    __device__ bool stage_x(float &y)
+    {
+        const bool ok = umma::mbar_wait(sbar, sphase, kMbarPolls);
+        sphase ^= 1u;
+        pending = false;
+        const float4 *mv = reinterpret_cast<const float4 *>(mean), *iv = reinterpret_cast<const float4 *>(istd);
+        float x[16];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int f0 = 16 * half + 4 * g;
+            const float4 m = mv[f0 / 4], r = iv[f0 / 4];
+            x[4 * g + 0] = (stage[(f0 + 0) * kRows + row] - m.x) * r.x;
+            x[4 * g + 1] = (stage[(f0 + 1) * kRows + row] - m.y) * r.y;
+            x[4 * g + 2] = (stage[(f0 + 2) * kRows + row] - m.z) * r.z;
+            x[4 * g + 3] = (stage[(f0 + 3) * kRows + row] - m.w) * r.w;
+        }
+        unsigned char *b = smem + WL::sB;
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, WL::cX + 16 * half, WL::wB)) = pack8(x);
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, WL::cX + 16 * half + 8, WL::wB)) = pack8(x + 8);
+        y = stage[kIn * kRows + row];
+        return ok;
+    }
+
+    // ---- epilogues: thread = (row, half), 64 hidden columns each ----
+    // H1 = relu(D + b1) into B; the mask of h1 > 0 in m1
+    __device__ void epi1(uint32_t (&m1)[2]) const
+    {
+        unsigned char *b = smem + WL::sB;
+        const float4 *b1 = reinterpret_cast<const float4 *>(vec + WL::vb1 + 64 * half);
+        float v[64];
+        umma::tmem_ld64(taddr(WL::cD + 64u * half), v);
+        m1[0] = m1[1] = 0u;
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const float4 c = b1[g];
+            v[4 * g + 0] = fmaxf(v[4 * g + 0] + c.x, 0.f);
+            v[4 * g + 1] = fmaxf(v[4 * g + 1] + c.y, 0.f);
+            v[4 * g + 2] = fmaxf(v[4 * g + 2] + c.z, 0.f);
+            v[4 * g + 3] = fmaxf(v[4 * g + 3] + c.w, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 64; ++i) m1[i / 32] |= (v[i] > 0.f ? 1u : 0u) << (i % 32);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) *reinterpret_cast<uint4 *>(b + wrow_off(row, 64 * half + 8 * g, WL::wB)) = pack8(v + 8 * g);
+    }
+
+    // h2 = relu(D + b2) of this thread's 64 columns in place; returns their share of
+    // w3 . h2 (four partial sums)
+    __device__ float layer2(float (&v)[64]) const
+    {
+        const float4 *b2 = reinterpret_cast<const float4 *>(vec + WL::vb2 + 64 * half),
+                     *w3 = reinterpret_cast<const float4 *>(vec + WL::vw3 + 64 * half);
+        umma::tmem_ld64(taddr(WL::cD + 64u * half), v);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const float4 c = b2[g], w = w3[g];
+            v[4 * g + 0] = fmaxf(v[4 * g + 0] + c.x, 0.f);
+            v[4 * g + 1] = fmaxf(v[4 * g + 1] + c.y, 0.f);
+            v[4 * g + 2] = fmaxf(v[4 * g + 2] + c.z, 0.f);
+            v[4 * g + 3] = fmaxf(v[4 * g + 3] + c.w, 0.f);
+            acc[0] = fmaf(v[4 * g + 0], w.x, acc[0]);
+            acc[1] = fmaf(v[4 * g + 1], w.y, acc[1]);
+            acc[2] = fmaf(v[4 * g + 2], w.z, acc[2]);
+            acc[3] = fmaf(v[4 * g + 3], w.w, acc[3]);
+        }
+        return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }
+
+    // zeta = w3 . h2 + b3 of this thread's row: the two halves' shares added in order
+    __device__ float zeta(float share) const
+    {
+        float *so = reinterpret_cast<float *>(smem + WL::sOut);
+        so[half * kRows + row] = share;
+        __syncthreads();
+        const float z = (so[row] + so[kRows + row]) + vec[WL::vb3];
+        __syncthreads();
+        return z;
+    }
+
+    // output, loss derivative and the output-layer backward of this thread's row:
+    // dH2 = dout w3 (h2 > 0) into A; column sums of h2 dout over the warp's rows
+    // (dw3) and, in the first warpgroup, of dout (db3) and dpred (dmu)
+    __device__ void out_back2(int pos, float y, float inv_batch, float *gsl) const
+    {
+        unsigned char *a = smem + WL::sA;
+        const float4 *w3 = reinterpret_cast<const float4 *>(vec + WL::vw3 + 64 * half);
+        float v[64];
+        const float out = zeta(layer2(v));
+        const float pred = (pos ? fmaxf(out, 0.f) : out) + vec[WL::vmu];
+        const float dpred = 2.f * (pred - y) * inv_batch;
+        const float dout = pos ? (out > 0.f ? dpred : 0.f) : dpred;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const float4 w0 = w3[2 * g], w1 = w3[2 * g + 1];
+            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            float d[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) d[i] = v[8 * g + i] > 0.f ? dout * wv[i] : 0.f;
+            *reinterpret_cast<uint4 *>(a + wrow_off(row, 64 * half + 8 * g, WL::wA)) = pack8(d);
+        }
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] *= dout;
+        const float2 cs = column_sums64(v, lane);
+        gsl[2 * lane] += cs.x;
+        gsl[2 * lane + 1] += cs.y;
+        if (half == 0) {
+            const float s3 = warp_sum(dout), smu = warp_sum(dpred);
+            if (lane == 0) {
+                gsl[64] += s3;
+                gsl[65] += smu;
+            }
+        }
+    }
+
+    // dH1 = D (h1 > 0) into A
+    __device__ void back1(const uint32_t (&m1)[2]) const
+    {
+        unsigned char *a = smem + WL::sA;
+        float v[64];
+        umma::tmem_ld64(taddr(WL::cD + 64u * half), v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) v[i] = ((m1[i / 32] >> (i % 32)) & 1u) ? v[i] : 0.f;
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            *reinterpret_cast<uint4 *>(a + wrow_off(row, WL::U + 64 * half + 8 * g, WL::wA)) = pack8(v + 8 * g);
+    }
+
+    // first two layers of the staged tile; D holds the second-layer pre-activation
+    template <class Side>
+    __device__ bool forward12(uint32_t (&m1)[2], bool in_ok, Side side)
+    {
+        if (!mma([&] { gemm_rows(WL::cD, WL::sB, WL::wB, WL::cX, WL::sW1, kIn, WL::U); }, in_ok, side)) return false;
+        epi1(m1);
+        return mma([&] { gemm_rows(WL::cD, WL::sB, WL::wB, 0, WL::sW2, WL::U, WL::U); });
+    }
+
+    // constant columns of B: ones after H1 (first warpgroup) and after X (second)
+    __device__ void init_constants()
+    {
+        const uint4 one = make_uint4((uint32_t)bf16_bits(1.f), 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+        unsigned char *b = smem + WL::sB;
+        const int c = half ? WL::cOne2 : WL::cOne1;
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, c, WL::wB)) = one;
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, c + 8, WL::wB)) = zero;
+    }
+};
+
+// common start: TMEM, mbarriers, standardisation, zero staging rows >= F, the
+// constant columns of B, optionally a zeroed A
+__device__ void wide_setup(WNet &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *stats, int F, bool zero_a)
+{
+    if (n.warp == 0) {
+        umma::tmem_alloc(s_tmem, WL::tmem_cols);
+        umma::tmem_relinquish();
+    }
+    if (n.tid == 0) {
+        umma::mbar_init(&s_mbar[0], 1);
+        umma::mbar_init(&s_mbar[1], 1);
+        umma::fence_mbar_init();
+    }
+    float *st = reinterpret_cast<float *>(n.smem + WL::sStats);
+    if (n.tid < 2 * kIn) st[n.tid] = __ldg(stats + n.tid);
+    for (int i = n.tid; i < (kIn + 1) * kRows; i += kWThreads) {
+        const int f = i / kRows;
+        if (f >= F && f < kIn) n.stage[i] = 0.f;
+    }
+    float *gsl = reinterpret_cast<float *>(n.smem + WL::sGsl);
+    for (int i = n.tid; i < 8 * 66; i += kWThreads) gsl[i] = 0.f;
+    if (zero_a) {
+        uint4 *a = reinterpret_cast<uint4 *>(n.smem + WL::sA);
+        for (int i = n.tid; i < kRows * WL::wA * 2 / 16; i += kWThreads) a[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    n.init_constants();
+}
+
+// images and FP32 vectors of the parameters theta (global, row order)
+__device__ void wide_load_params(WNet &n, const float *theta)
+{
+    for (int i = n.tid; i < WL::U * (kIn / 8); i += kWThreads) {   // W1: row o, 8 inputs from k
+        const int o = i / (kIn / 8), k = (i % (kIn / 8)) * 8;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ldg(theta + WL::oW1 + o * kIn + k + j);
+        *reinterpret_cast<uint4 *>(n.smem + WL::sW1 + umma::kmajor_offset(o, k, kIn)) = pack8(v);
+    }
+    for (int i = n.tid; i < WL::U * (WL::U / 8); i += kWThreads) {  // W2: row o, 8 inputs from k
+        const int o = i / (WL::U / 8), k = (i % (WL::U / 8)) * 8;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = __ldg(theta + WL::oW2 + o * WL::U + k + j);
+        *reinterpret_cast<uint4 *>(n.smem + WL::sW2 + umma::kmajor_offset(o, k, WL::U)) = pack8(v);
+    }
+    for (int i = n.tid; i < WL::U; i += kWThreads) {
+        n.vec[WL::vb1 + i] = __ldg(theta + WL::ob1 + i);
+        n.vec[WL::vb2 + i] = __ldg(theta + WL::ob2 + i);
+        n.vec[WL::vw3 + i] = __ldg(theta + WL::ow3 + i);
+    }
+    if (n.tid == 0) {
+        n.vec[WL::vb3] = __ldg(theta + WL::ob3);
+        n.vec[WL::vmu] = __ldg(theta + WL::omu);
+    }
+}
+
+__device__ void wide_finish_setup(WNet &n, uint32_t *s_tmem)
+{
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    n.tmem = *s_tmem;
+}
+
+__device__ void wide_teardown(WNet &n)
+{
+    if (n.pending) (void)umma::mbar_wait(n.sbar, n.sphase, kMbarPolls);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (n.warp == 0) umma::tmem_dealloc(n.tmem, WL::tmem_cols);
+}
+
+// One epoch (or its first n_steps batches) of Adam on a cooperative grid. Batch b
+// covers paths [b P, (b + 1) P), P = tiles_per_batch * 128; in each step the
+// grid's CTAs take the batch's tiles round-robin.
+__global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, const __grid_constant__ CUtensorMap tm)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    WNet n(smem, s_mbar);
+    const int G = (int)gridDim.x, cta = (int)blockIdx.x;
+    // owned slice [lo, hi) of the padded parameter vector (multiples of 4 entries)
+    const int S = ((WL::NPpad + 4 * G - 1) / (4 * G)) * 4;
+    const int lo = min(WL::NPpad, cta * S), hi = min(WL::NPpad, lo + S);
+
+    wide_setup(n, &s_tmem, s_mbar, a.stats, a.F, false);
+    wide_load_params(n, a.init);
+    for (int q = lo + n.tid; q < hi; q += kWThreads) {
+        a.gq[q] = q < WL::NP ? __ldg(a.init + WL::p_of(q)) : 0.f;
+        if (a.step0 == 0) a.adam_m[q] = a.adam_v[q] = 0.f;
+    }
+    if (a.step0 == 0 && cta == 0) {   // start of a date: the starting parameters are the best so far
+        for (int p = n.tid; p < WL::NP; p += kWThreads) a.best[p] = __ldg(a.init + p);
+        if (n.tid == 0) *a.best_loss = 1e300;
+    }
+    wide_finish_setup(n, &s_tmem);
+
+    const uint32_t per_batch = (uint32_t)a.tiles_per_batch * kRows;
+    const float inv_batch = 1.f / (float)per_batch;
+    const int my_rounds = cta < a.tiles_per_batch ? (a.tiles_per_batch - 1 - cta) / G + 1 : 0;
+    auto path_of = [&](int st, int rd) { return (uint32_t)st * per_batch + (uint32_t)(rd * G + cta) * kRows; };
+    float *gsl = reinterpret_cast<float *>(smem + WL::sGsl);
+    float *my_gsl = gsl + n.warp * 66;
+    float4 *red = reinterpret_cast<float4 *>(smem + WL::sRed);
+    unsigned gen = 0;
+    bool ok = true;
+
+    if (my_rounds > 0) n.prefetch(&tm, a.targ, a.F, path_of(0, 0));
+    for (int st = 0; st < a.n_steps; ++st) {
+        for (int rd = 0; rd < my_rounds && ok; ++rd) {
+            const bool last = rd + 1 == my_rounds;
+            const bool has_next = !last || st + 1 < a.n_steps;
+            const uint32_t next = last ? path_of(st + 1, 0) : path_of(st, rd + 1);
+            float y;
+            const bool in_ok = n.stage_x(y);
+            uint32_t m1[2];
+            ok = n.forward12(m1, in_ok, [&] {
+                if (has_next) n.prefetch(&tm, a.targ, a.F, next);
+            });
+            if (ok) {
+                n.out_back2(a.pos, y, inv_batch, my_gsl);
+                ok = n.mma([&] { n.gemm_w2t(WL::cD); });
+            }
+            if (ok) {
+                n.back1(m1);
+                const bool acc = rd > 0;
+                ok = n.mma([&] {
+                    n.gemm_paths(WL::cW2, WL::sA, WL::wA, 0, WL::sB, WL::wB, 0, WL::U + 16, acc);
+                    n.gemm_paths(WL::cW1, WL::sA, WL::wA, WL::U, WL::sB, WL::wB, WL::cX, kIn + 16, acc);
+                });
+            }
+            if (!ok && n.tid == 0) atomicExch(a.err, 2);
+        }
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+
+        // this CTA's partial (zero when it had no tile) to global memory, q order
+        float *P = a.gpart + (size_t)cta * WL::NPpad;
+        {
+            const uint32_t lanes = (uint32_t)((n.warp & 3) * 32) << 16;
+            const int r = (n.warp & 3) * 32 + n.lane;
+            const bool have = my_rounds > 0;
+            const int k0 = n.half ? 5 : 0, k1 = n.half ? 9 : 5;   // DW2 | db2: 9 chunks of 16 columns
+            for (int k = k0; k < k1; ++k) {
+                float v[16];
+                umma::tmem_ld16(n.tmem + lanes + WL::cW2 + 16u * k, v);
+                umma::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = 16 * k + i;
+                    const float g = have ? v[i] : 0.f;
+                    if (c < WL::U) P[WL::oW2 + c * WL::U + r] = g;
+                    else if (c == WL::U) P[WL::ob2 + r] = g;
+                }
+            }
+            const int j0 = n.half ? 1 : 0, j1 = n.half ? 3 : 1;   // DW1 | db1: 3 chunks
+            for (int k = j0; k < j1; ++k) {
+                float v[16];
+                umma::tmem_ld16(n.tmem + lanes + WL::cW1 + 16u * k, v);
+                umma::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = 16 * k + i;
+                    const float g = have ? v[i] : 0.f;
+                    if (c < kIn) P[WL::oW1 + c * WL::U + r] = g;
+                    else if (c == kIn) P[WL::ob1 + r] = g;
+                }
+            }
+            if (n.tid < WL::U + 2) {   // w3 from the warps of the column's half; b3, mu from the first half
+                const int j = n.tid;
+                const int h = j < WL::U ? j >> 6 : 0, c = j < WL::U ? (j & 63) : j - WL::U + 64;
+                float s = 0.f;
+                for (int w = 4 * h; w < 4 * h + 4; ++w) s += gsl[w * 66 + c];
+                P[j < WL::U ? WL::ow3 + j : (j == WL::U ? WL::ob3 : WL::omu)] = s;
+            }
+            __syncthreads();
+            for (int i = n.tid; i < 8 * 66; i += kWThreads) gsl[i] = 0.f;
+        }
+        if (!grid_barrier(a.flags, (unsigned)G, gen, a.err)) ok = false;
+
+        // the owned slice: partials summed over the grid (nsub fixed interleaved
+        // ranges of CTAs per group of four parameters, added in range order), Adam,
+        // new FP32 values and their BF16 images
+        {
+            const int step = a.step0 + st + 1;
+            const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
+            const int NG = (hi - lo) / 4;
+            const int nsub = NG >= kWThreads ? 1 : (NG > 0 ? kWThreads / NG : 1);
+            const int Pg = kWThreads / nsub;
+            for (int g0 = 0; g0 < NG; g0 += Pg) {
+                const int gi = g0 + n.tid % Pg, j = n.tid / Pg;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gi < NG && j < nsub)
+                    for (int c = j; c < G; c += nsub) {
+                        const float4 v = __ldcg(reinterpret_cast<const float4 *>(a.gpart + (size_t)c * WL::NPpad + lo + 4 * gi));
+                        acc.x += v.x;
+                        acc.y += v.y;
+                        acc.z += v.z;
+                        acc.w += v.w;
+                    }
+                red[n.tid] = acc;
+                __syncthreads();
+                if (j == 0 && gi < NG) {
+                    float4 g = red[n.tid];
+                    for (int jj = 1; jj < nsub; ++jj) {
+                        const float4 v = red[jj * Pg + n.tid];
+                        g.x += v.x;
+                        g.y += v.y;
+                        g.z += v.z;
+                        g.w += v.w;
+                    }
+                    const float gv[4] = {g.x, g.y, g.z, g.w};
+                    for (int e = 0; e < 4; ++e) {
+                        const int q = lo + 4 * gi + e;
+                        if (step == 1 && a.grad_out && q < WL::NP) a.grad_out[WL::p_of(q)] = gv[e];
+                        float t = 0.f;   // padding stays zero
+                        if (q < WL::NP && !(q < WL::ob1 && q / WL::U >= a.F)) {
+                            const float m = a.beta1 * a.adam_m[q] + (1.f - a.beta1) * gv[e];
+                            const float v = a.beta2 * a.adam_v[q] + (1.f - a.beta2) * gv[e] * gv[e];
+                            a.adam_m[q] = m;
+                            a.adam_v[q] = v;
+                            t = a.gq[q] - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
+                        }
+                        a.gq[q] = t;
+                        if (q < WL::ob1) {
+                            const int o = q % WL::U, f = q / WL::U;
+                            a.gimg[umma::kmajor_offset(o, f, kIn) / 2] = bf16_bits(t);
+                        } else if (q >= WL::oW2 && q < WL::ob2) {
+                            const int o = (q - WL::oW2) % WL::U, k = (q - WL::oW2) / WL::U;
+                            a.gimg[(WL::U * kIn * 2 + umma::kmajor_offset(o, k, WL::U)) / 2] = bf16_bits(t);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (!grid_barrier(a.flags, (unsigned)G, gen, a.err)) ok = false;
+
+        // every CTA: the new images and FP32 vectors
+        {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.gimg);
+            uint4 *dst = reinterpret_cast<uint4 *>(smem + WL::sW1);
+            for (int i = n.tid; i < WL::img_elems * 2 / 16; i += kWThreads) dst[i] = __ldcg(src + i);
+            for (int i = n.tid; i < WL::U; i += kWThreads) {
+                n.vec[WL::vb1 + i] = __ldcg(a.gq + WL::ob1 + i);
+                n.vec[WL::vb2 + i] = __ldcg(a.gq + WL::ob2 + i);
+                n.vec[WL::vw3 + i] = __ldcg(a.gq + WL::ow3 + i);
+            }
+            if (n.tid == 0) {
+                n.vec[WL::vb3] = __ldcg(a.gq + WL::ob3);
+                n.vec[WL::vmu] = __ldcg(a.gq + WL::omu);
+            }
+            umma::fence_proxy_async();
+            __syncthreads();
+        }
+    }
+    for (int q = lo + n.tid; q < hi; q += kWThreads)
+        if (q < WL::NP) {
+            const float t = a.gq[q];
+            a.params[WL::p_of(q)] = t;
+            if (a.snap) a.snap[WL::p_of(q)] = t;
+        }
+    wide_teardown(n);
+}
+
+// Full-sample passes with fixed parameters, output ReLU on: the loss (mode 0), the
+// refit's Gram matrix of Z = [h2 | 1 | y - mu] (mode 1), the predictions (mode 2).
+__global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, const __grid_constant__ CUtensorMap tm)
+{
+    constexpr int Z = WL::Z;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ double s_red[8][3];
+    __shared__ int s_flag[2];
+    WNet n(smem, s_mbar);
+    wide_setup(n, &s_tmem, s_mbar, a.stats, a.F, a.mode == 1);
+    wide_load_params(n, a.theta);
+    wide_finish_setup(n, &s_tmem);
+
+    const uint32_t tiles = a.M / kRows, stride = gridDim.x;
+    uint32_t t = blockIdx.x;
+    double acc[3] = {0.0, 0.0, 0.0};
+    bool ok = true, first = true;
+    if (t < tiles) n.prefetch(&tm, a.targ, a.F, t * kRows);
+    for (; t < tiles && ok; t += stride) {
+        const uint32_t nt = t + stride;
+        float y;
+        const bool in_ok = n.stage_x(y);
+        uint32_t m1[2];
+        ok = n.forward12(m1, in_ok, [&] {
+            if (nt < tiles) n.prefetch(&tm, a.targ, a.F, nt * kRows);
+        });
+        if (!ok) break;
+        float v[64];
+        const float share = n.layer2(v);
+        if (a.mode != 1) {
+            const float pred = fmaxf(n.zeta(share), 0.f) + n.vec[WL::vmu];
+            if (n.half == 0) {
+                if (a.mode == 2) {
+                    if (a.pred) a.pred[t * kRows + n.row] = pred;
+                } else {
+                    acc[0] += (double)((pred - y) * (pred - y));
+                }
+            }
+        } else {
+            // row of Z into A: [h2 | 1 | y - mu | 0 ...]; the corner sums (1, y - mu,
+            // (y - mu)^2 with y - mu rounded as the tensor core sees it) in FP64
+            unsigned char *ar = smem + WL::sA;
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+                *reinterpret_cast<uint4 *>(ar + wrow_off(n.row, 64 * n.half + 8 * g, WL::wA)) = pack8(v + 8 * g);
+            if (n.half == 1) {
+                const float d = y - n.vec[WL::vmu];
+                *reinterpret_cast<uint4 *>(ar + wrow_off(n.row, WL::U, WL::wA)) = make_uint4(pack2(1.f, d), 0u, 0u, 0u);
+                const double db = (double)__bfloat162float(__float2bfloat16_rn(d));
+                acc[0] += 1.0;
+                acc[1] += db;
+                acc[2] += db * db;
+            }
+            // G (+)= Z^T Z: M = the 128 h2 columns, N = the first 144 columns of the rows
+            ok = n.mma([&] { n.gemm_paths(WL::cW2, WL::sA, WL::wA, 0, WL::sA, WL::wA, 0, WL::U + 16, !first); });
+        }
+        if (!ok && n.tid == 0) atomicExch(a.err, 2);
+        first = false;
+    }
+    if (!ok && n.tid == 0) atomicExch(a.err, 2);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+
+    // block sums of acc[0..2]
+    for (int k = 0; k < 3; ++k) {
+        double s = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (n.lane == 0) s_red[n.warp][k] = s;
+    }
+    __syncthreads();
+    if (a.mode == 0) {
+        if (n.tid == 0) {
+            double b = 0.0;
+            for (int w = 0; w < 8; ++w) b += s_red[w][0];
+            a.part[blockIdx.x] = b;
+            __threadfence();
+            s_flag[0] = atomicAdd(a.count, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_flag[0]) {   // the last CTA: total loss, best parameters so far
+            __threadfence();
+            if (n.tid == 0) {
+                double tot = 0.0;
+                for (uint32_t b = 0; b < gridDim.x; ++b) tot += __ldcg(a.part + b);
+                tot /= (double)a.M;
+                if (a.loss_out) a.loss_out[a.epoch - 1] = (float)tot;
+                s_flag[1] = tot < *a.best_loss;
+                if (s_flag[1]) *a.best_loss = tot;
+                *a.count = 0u;
+            }
+            __syncthreads();
+            if (s_flag[1])
+                for (int p = n.tid; p < WL::NP; p += kWThreads) a.best[p] = __ldg(a.theta + p);
+        }
+    } else if (a.mode == 1) {   // this CTA's Gram as FP64, [Z][Z]
+        double *P = a.part + (size_t)blockIdx.x * Z * Z;
+        const bool have = blockIdx.x < tiles;
+        const uint32_t lanes = (uint32_t)((n.warp & 3) * 32) << 16;
+        const int r = (n.warp & 3) * 32 + n.lane;
+        const int k0 = n.half ? 5 : 0, k1 = n.half ? 9 : 5;
+        for (int k = k0; k < k1; ++k) {
+            float v[16];
+            umma::tmem_ld16(n.tmem + lanes + WL::cW2 + 16u * k, v);
+            umma::tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int c = 16 * k + i;
+                if (c < Z) {
+                    const double g = have ? (double)v[i] : 0.0;
+                    P[r * Z + c] = g;
+                    if (c >= WL::U) P[c * Z + r] = g;   // rows U, U + 1 by symmetry
+                }
+            }
+        }
+        if (n.tid == 0) {
+            double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+            for (int w = 4; w < 8; ++w) {
+                c0 += s_red[w][0];
+                c1 += s_red[w][1];
+                c2 += s_red[w][2];
+            }
+            P[WL::U * Z + WL::U] = c0;
+            P[WL::U * Z + WL::U + 1] = P[(WL::U + 1) * Z + WL::U] = c1;
+            P[(WL::U + 1) * Z + WL::U + 1] = c2;
+        }
+    }
+    wide_teardown(n);
+}
+
+// ---- host side ----
+struct WideWork {
+    void *buf = nullptr;
+    size_t cap = 0;
+    bool attrs = false;
+};
+std::mutex g_wide_mu;
+WideWork g_wide[64];
+
+}  // namespace
+
+cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride,
+                              int n_dates, int F, uint64_t M, int n_batches, int epochs, float lr, int max_steps,
+                              float *params_dev, float *pred0, float *grad_out_dev, float *loss_out_dev,
+                              unsigned *count, int *err, cudaStream_t st)
+{
+    constexpr int Z = WL::Z;
+    const int tiles_per_batch = (int)(M / n_batches / kRows);
+    int dev = 0, sms = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    CVA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_wide_mu);
+    WideWork &w = g_wide[dev];
+    if (!w.attrs) {
+        CVA_CUDA_TRY(cudaFuncSetAttribute(wide_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WL::bytes));
+        CVA_CUDA_TRY(cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WL::bytes));
+        CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_refit_kernel<WL::U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)refit_smem_bytes(WL::U)));
+        w.attrs = true;
+    }
+    int per_sm = 0;
+    CVA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide_train_kernel, kWThreads, WL::bytes));
+    if (per_sm < 1) return fail(CVA_ENOTSUP, "mlp: the width-128 trainer does not fit on an SM");
+    // grid of the trainer: at most one CTA per SM, about two tiles per CTA and round
+    int G = tiles_per_batch >= 2 ? (tiles_per_batch + 1) / 2 : 1;
+    if (G > sms) G = sms;
+    const uint64_t tiles = M / kRows;
+    const int sweep_grid = (int)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
+
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_vec = al((size_t)WL::NPpad * 4), b_img = al((size_t)WL::img_elems * 2),
+                 b_stats = al((size_t)n_dates * 2 * kIn * 4), b_snaps = al((size_t)epochs * WL::NPpad * 4),
+                 b_part = al((size_t)G * WL::NPpad * 4), b_flags = al((size_t)G * 4), b_bl = al(8),
+                 b_G = al((size_t)Z * Z * 8), b_pl = al((size_t)sweep_grid * 8),
+                 b_pg = al((size_t)sweep_grid * Z * Z * 8);
+    const size_t need = 5 * b_vec + b_img + b_stats + b_snaps + b_part + b_flags + 2 * b_bl + b_G + b_pl + b_pg;
+    if (w.cap < need) {
+        CVA_CUDA_TRY(cudaStreamSynchronize(st));
+        if (w.buf) cudaFree(w.buf);
+        w.buf = nullptr;
+        w.cap = 0;
+        if (cudaMalloc(&w.buf, need) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: workspace (width 128)");
+        w.cap = need;
+    }
+    char *p = static_cast<char *>(w.buf);
+    auto take = [&](size_t b) {
+        char *r = p;
+        p += b;
+        return r;
+    };
+    float *adam_m = reinterpret_cast<float *>(take(b_vec)), *adam_v = reinterpret_cast<float *>(take(b_vec));
+    float *gq = reinterpret_cast<float *>(take(b_vec));
+    float *best[2] = {reinterpret_cast<float *>(take(b_vec)), reinterpret_cast<float *>(take(b_vec))};
+    uint16_t *gimg = reinterpret_cast<uint16_t *>(take(b_img));
+    float *stats = reinterpret_cast<float *>(take(b_stats));
+    float *snaps = reinterpret_cast<float *>(take(b_snaps));
+    float *gpart = reinterpret_cast<float *>(take(b_part));
+    unsigned *flags = reinterpret_cast<unsigned *>(take(b_flags));
+    double *best_loss[2] = {reinterpret_cast<double *>(take(b_bl)), reinterpret_cast<double *>(take(b_bl))};
+    double *Gm = reinterpret_cast<double *>(take(b_G));
+    double *part_loss = reinterpret_cast<double *>(take(b_pl));
+    double *part_gram = reinterpret_cast<double *>(take(b_pg));
+
+    mlp_stats_kernel<<<dim3(kIn, (unsigned)n_dates), 256, 0, st>>>(feat0, F, (uint32_t)M, feat_stride, stats);
+    CVA_CUDA_TRY(cudaGetLastError());
+
+    WTrainArgs ta = {};
+    ta.F = F;
+    ta.M = (uint32_t)M;
+    ta.tiles_per_batch = tiles_per_batch;
+    ta.lr = lr;
+    ta.beta1 = 0.9f;
+    ta.beta2 = 0.999f;
+    ta.eps = 1e-8f;
+    ta.params = params_dev;
+    ta.adam_m = adam_m;
+    ta.adam_v = adam_v;
+    ta.gq = gq;
+    ta.gimg = gimg;
+    ta.gpart = gpart;
+    ta.flags = flags;
+    ta.grad_out = grad_out_dev;
+    ta.err = err;
+
+    WSweepArgs sw = {};
+    sw.F = F;
+    sw.M = (uint32_t)M;
+    sw.count = count + 1;
+    sw.part = part_loss;
+    sw.loss_out = loss_out_dev;
+    sw.err = err;
+
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(kWThreads);
+    cfg.dynamicSmemBytes = WL::bytes;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+
+    int steps_left = max_steps > 0 ? max_steps : INT_MAX;
+    for (int d = n_dates - 1; d >= 0; --d) {
+        const int par = d & 1;
+        const float *feat = feat0 + (size_t)d * feat_stride, *targ = targ0 + (size_t)d * targ_stride;
+        CUtensorMap tm;
+        cva_status r = features_map(&tm, feat, F, M);
+        if (r != CVA_OK) return r;
+        ta.targ = sw.targ = targ;
+        ta.stats = sw.stats = stats + (size_t)d * 2 * kIn;
+        ta.best = sw.best = best[par];
+        ta.best_loss = sw.best_loss = best_loss[par];
+        for (int e = 1; e <= epochs; ++e) {
+            float *snap = snaps + (size_t)(e - 1) * WL::NPpad;
+            ta.init = (e == 1 && d < n_dates - 1) ? best[par ^ 1] : params_dev;   // Algorithm 2's warm start
+            ta.snap = snap;
+            ta.n_steps = n_batches < steps_left ? n_batches : steps_left;
+            ta.step0 = (e - 1) * n_batches;
+            ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;
+            CVA_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)G * 4, st));
+            CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, wide_train_kernel, ta, tm));
+            steps_left -= ta.n_steps;
+            if (max_steps > 0 && steps_left <= 0) return CVA_OK;
+            if (e == epochs / 2) {
+                WSweepArgs g = sw;
+                g.mode = 1;
+                g.theta = params_dev;
+                g.part = part_gram;
+                g.loss_out = nullptr;
+                wide_sweep_kernel<<<sweep_grid, kWThreads, WL::bytes, st>>>(g, tm);
+                CVA_CUDA_TRY(cudaGetLastError());
+                mlp_refit_kernel<WL::U><<<Z, 256, refit_smem_bytes(WL::U), st>>>(part_gram, sweep_grid, Gm, count + 2,
+                                                                                 params_dev, snap);
+                CVA_CUDA_TRY(cudaGetLastError());
+            }
+            sw.mode = 0;
+            sw.theta = snap;
+            sw.epoch = e;
+            wide_sweep_kernel<<<sweep_grid, kWThreads, WL::bytes, st>>>(sw, tm);
+            CVA_CUDA_TRY(cudaGetLastError());
+        }
+        if (pred0) {
+            WSweepArgs pv = sw;
+            pv.mode = 2;
+            pv.theta = best[par];
+            pv.pred = pred0 + (size_t)d * M;
+            wide_sweep_kernel<<<sweep_grid, kWThreads, WL::bytes, st>>>(pv, tm);
+            CVA_CUDA_TRY(cudaGetLastError());
+        }
+        if (d == 0)
+            CVA_CUDA_TRY(cudaMemcpyAsync(params_dev, best[par], WL::NP * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    return CVA_OK;
+}
+
+}  // namespace cva
