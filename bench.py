@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--lsq", action="store_true", help="least-squares regression instead of the workload's MLP")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     p.add_argument("--no-batched", action="store_true", help="skip the 6-portfolio CUDA-graph measurement")
+    p.add_argument("--no-precision", action="store_true",
+                   help="skip the 2^20-path width-128 network measurement")
     p.add_argument("--paths", type=int, default=None,
                    help="override the number of outer paths (small cases for profiling captures)")
     return p.parse_args()
@@ -91,6 +93,16 @@ def price_instr_per_path_date(wl):
     (portfolio, counterparty) for the exposure and 6 for the discount factor."""
     E, C, CS, F, G, NPF, S = _shape(wl)
     return 20 * E + 12 * E * G + NPF * C * E * (2 * G + 1) + 3 * NPF * C + 6
+
+
+def mlp_flops_per_date(M, d, u, epochs):
+    """Algorithmic FLOPs of Algorithm 1 at one date for the NN+ network d -> u -> u -> 1:
+    per sample and epoch a forward pass 2(d u + u^2) and a backward pass 2(u^2 + u^2 + d u)
+    (dH1, dW2, dW1), plus full-sample forward passes for the epoch losses, the refit's
+    Gram matrix and the predictions (epochs + 2)."""
+    fwd = 2 * (d * u + u * u)
+    bwd = 2 * (u * u + u * u + d * u)
+    return M * (epochs * (fwd + bwd) + (epochs + 2) * fwd)
 
 
 def inner_bytes_per_path(wl):
@@ -346,10 +358,7 @@ def main():
     reg_gbs = reg_bytes / (np.mean(reg_ms) / 1e3) / 1e9
     mlp_roof = None
     if use_mlp:
-        d, u = wl.model.F, hidden
-        fwd = 2 * (d * u + u * u)                 # forward GEMM flops per sample
-        bwd = 2 * (u * u + u * u + d * u)         # dH1, dW2, dW1 GEMM flops per sample
-        per_date = wl.M * (epochs * (fwd + bwd) + (epochs + 2) * fwd)   # training + loss, refit, predict sweeps
+        per_date = mlp_flops_per_date(wl.M, wl.model.F, hidden, epochs)
         flops = per_date * (n - 1)
         tf = flops / (np.mean(reg_ms) / 1e3) / 1e12
         peak_tf = pk.get("bf16_tflops_sustained", 1720.9)
@@ -417,6 +426,38 @@ def main():
         bsim.close()
         del bpred, graph
 
+    # ---- the 2^20-path workload with the width-128 network (rank 0) ----
+    precision = None
+    if rank == 0 and not args.no_precision and args.workload != "precision":
+        pwl = workload.make("precision", M=args.paths)
+        psim = api.Simulation(pwl.model, pwl.portfolios, pwl.grid, pwl.M, pwl.N)
+        pinit = api.mlp_pack(workload.mlp_init(pwl.model.F, pwl.hidden), pwl.hidden)
+        pn = pwl.grid.n_steps
+        psim.run(pwl.seed)
+        api.mlp_regress_all(psim, pinit.clone(), hidden=pwl.hidden)   # warm-up
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        psim.run(pwl.seed)
+        e1.record(stream)
+        api.mlp_regress_all(psim, pinit.clone(), hidden=pwl.hidden)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        p_sim, p_reg = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        pflops = mlp_flops_per_date(pwl.M, pwl.model.F, pwl.hidden, epochs) * (pn - 1)
+        ptf = pflops / (p_reg / 1e3) / 1e12
+        peak_tf = pk.get("bf16_tflops_sustained", 1720.9)
+        precision = {"workload": describe(pwl) + f", NN+ {pwl.model.F}->{pwl.hidden}->{pwl.hidden}->1, Algorithm 2 "
+                                                 f"over {pn - 1} dates (E={epochs}, |B|={n_batches})",
+                     "sim_ms": p_sim, "regression_ms": p_reg, "step_ms": p_sim + p_reg,
+                     "value": pwl.M * pwl.N * pn / ((p_sim + p_reg) / 1e3), "unit": UNIT,
+                     "regression_samples_per_s": pwl.M * (pn - 1) / (p_reg / 1e3),
+                     "roofline": {"bound": "tensor", "kernel": "wide_train_kernel + wide_sweep_kernel",
+                                  "achieved": ptf, "peak": peak_tf, "unit": "TFLOP/s", "frac": ptf / peak_tf,
+                                  "traffic": None, "algorithmic_flops": pflops,
+                                  "peak_source": "measured bf16 cuBLAS, sustained"}}
+        psim.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         M_sample = 2048 if wl.name != "small" else wl.M
@@ -442,7 +483,8 @@ def main():
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
-               "mlp_roofline": mlp_roof, "adjoint_forward": adj, "batched": batched, "cpu_baseline": cpu,
+               "mlp_roofline": mlp_roof, "adjoint_forward": adj, "batched": batched, "precision": precision,
+               "cpu_baseline": cpu,
                "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},

@@ -30,9 +30,9 @@
 // parameter vector: it sums the slice over all CTAs' partials (fixed order), applies
 // Adam (moments and FP32 master values in global memory) and writes the new FP32
 // values and their BF16 images; after a second grid barrier every CTA reloads the
-// images and the FP32 vectors. The grid barrier is a per-CTA generation flag with
-// bounded waits (a wait that gives up sets the status word; every other wait then
-// ends at once).
+// images and the FP32 vectors. The grid barrier is an arrival counter and a
+// generation word with bounded waits (a wait that gives up sets the status word;
+// every other wait then ends at once).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -117,7 +117,7 @@ struct WTrainArgs {
     float *gq;                     // [NPpad] q order: FP32 master parameters
     uint16_t *gimg;                // [img_elems] BF16 images of W1 | W2 (shared-memory layout)
     float *gpart;                  // [grid][NPpad] q order: gradient partials
-    unsigned *flags;               // [grid] barrier generations, zero at launch
+    unsigned *flags;               // [2] grid barrier: arrivals, generation (zero at launch)
     const float *stats;            // mean[32], 1/std[32]
     float *grad_out;               // [NP] row order: gradient of the first step (nullable)
     int *err;
@@ -140,34 +140,41 @@ struct WSweepArgs {
     int *err;
 };
 
-// Grid barrier: every CTA publishes its generation in its own flag and waits until
-// all flags reach it. Bounded: a wait that gives up (or sees the status word set)
-// sets the status word and returns false; all threads get the same answer.
-__device__ __forceinline__ bool grid_barrier(unsigned *flags, unsigned nblocks, unsigned &gen, int *err)
+// Grid barrier of generation gen: bar[0] counts arrivals over the launch (one per
+// CTA and barrier), bar[1] holds the last completed generation. Thread 0 of every
+// CTA arrives with one atomic; the CTA completing the count publishes the
+// generation, the others poll that one word. Bounded: a wait that gives up (or sees
+// the status word set) sets the status word and returns false; all threads of the
+// CTA get the same answer. Every thread's global writes before the barrier are
+// visible to every thread of the grid after it.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned &gen, int *err)
 {
     __threadfence();
     __syncthreads();
     gen += 1u;
+    int ok = 1;
     if (threadIdx.x == 0) {
         __threadfence();
-        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flags + blockIdx.x), "r"(gen) : "memory");
-    }
-    int ok = 1;
-    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        uint32_t it = 0;
-        for (;;) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flags + b) : "memory");
-            if ((int)(v - gen) >= 0) break;
-            if (++it > kGridPolls || *(volatile int *)err) {
-                ok = 0;
-                atomicExch(err, 3);
-                break;
+        const unsigned t = atomicAdd(bar, 1u);
+        if (t == gen * nblocks - 1u) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen) : "memory");
+        } else {
+            uint32_t it = 0;
+            for (;;) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar + 1) : "memory");
+                if ((int)(v - gen) >= 0) break;
+                if (++it > kGridPolls || *(volatile int *)err) {
+                    ok = 0;
+                    atomicExch(err, 3);
+                    break;
+                }
+                __nanosleep(32);
             }
-            __nanosleep(64);
         }
+        __threadfence();
     }
-    __threadfence();
     return __syncthreads_and(ok) != 0;
 }
 
@@ -620,18 +627,34 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
             const int Pg = kWThreads / nsub;
             for (int g0 = 0; g0 < NG; g0 += Pg) {
                 const int gi = g0 + n.tid % Pg, j = n.tid / Pg;
+                const bool upd = j == 0 && gi < NG;   // this thread updates the group
+                float4 m4 = make_float4(0.f, 0.f, 0.f, 0.f), v4 = m4, t4 = m4;
+                if (upd) {   // Adam state of the group, requested together with the partials
+                    m4 = *reinterpret_cast<const float4 *>(a.adam_m + lo + 4 * gi);
+                    v4 = *reinterpret_cast<const float4 *>(a.adam_v + lo + 4 * gi);
+                    t4 = *reinterpret_cast<const float4 *>(a.gq + lo + 4 * gi);
+                }
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (gi < NG && j < nsub)
-                    for (int c = j; c < G; c += nsub) {
-                        const float4 v = __ldcg(reinterpret_cast<const float4 *>(a.gpart + (size_t)c * WL::NPpad + lo + 4 * gi));
-                        acc.x += v.x;
-                        acc.y += v.y;
-                        acc.z += v.z;
-                        acc.w += v.w;
+                    for (int c0 = j; c0 < G; c0 += 16 * nsub) {   // sixteen loads in flight, added in CTA order
+                        float4 v[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int c = c0 + u * nsub;
+                            v[u] = c < G ? __ldcg(reinterpret_cast<const float4 *>(a.gpart + (size_t)c * WL::NPpad + lo + 4 * gi))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            acc.x += v[u].x;
+                            acc.y += v[u].y;
+                            acc.z += v[u].z;
+                            acc.w += v[u].w;
+                        }
                     }
                 red[n.tid] = acc;
                 __syncthreads();
-                if (j == 0 && gi < NG) {
+                if (upd) {
                     float4 g = red[n.tid];
                     for (int jj = 1; jj < nsub; ++jj) {
                         const float4 v = red[jj * Pg + n.tid];
@@ -641,18 +664,18 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
                         g.w += v.w;
                     }
                     const float gv[4] = {g.x, g.y, g.z, g.w};
+                    float mv[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w},
+                          tv[4] = {t4.x, t4.y, t4.z, t4.w};
                     for (int e = 0; e < 4; ++e) {
                         const int q = lo + 4 * gi + e;
                         if (step == 1 && a.grad_out && q < WL::NP) a.grad_out[WL::p_of(q)] = gv[e];
                         float t = 0.f;   // padding stays zero
                         if (q < WL::NP && !(q < WL::ob1 && q / WL::U >= a.F)) {
-                            const float m = a.beta1 * a.adam_m[q] + (1.f - a.beta1) * gv[e];
-                            const float v = a.beta2 * a.adam_v[q] + (1.f - a.beta2) * gv[e] * gv[e];
-                            a.adam_m[q] = m;
-                            a.adam_v[q] = v;
-                            t = a.gq[q] - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
+                            mv[e] = a.beta1 * mv[e] + (1.f - a.beta1) * gv[e];
+                            vv[e] = a.beta2 * vv[e] + (1.f - a.beta2) * gv[e] * gv[e];
+                            t = tv[e] - a.lr * (mv[e] / bc1) / (sqrtf(vv[e] / bc2) + a.eps);
                         }
-                        a.gq[q] = t;
+                        tv[e] = t;
                         if (q < WL::ob1) {
                             const int o = q % WL::U, f = q / WL::U;
                             a.gimg[umma::kmajor_offset(o, f, kIn) / 2] = bf16_bits(t);
@@ -661,6 +684,9 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
                             a.gimg[(WL::U * kIn * 2 + umma::kmajor_offset(o, k, WL::U)) / 2] = bf16_bits(t);
                         }
                     }
+                    *reinterpret_cast<float4 *>(a.adam_m + lo + 4 * gi) = make_float4(mv[0], mv[1], mv[2], mv[3]);
+                    *reinterpret_cast<float4 *>(a.adam_v + lo + 4 * gi) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    *reinterpret_cast<float4 *>(a.gq + lo + 4 * gi) = make_float4(tv[0], tv[1], tv[2], tv[3]);
                 }
                 __syncthreads();
             }
@@ -870,7 +896,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_vec = al((size_t)WL::NPpad * 4), b_img = al((size_t)WL::img_elems * 2),
                  b_stats = al((size_t)n_dates * 2 * kIn * 4), b_snaps = al((size_t)epochs * WL::NPpad * 4),
-                 b_part = al((size_t)G * WL::NPpad * 4), b_flags = al((size_t)G * 4), b_bl = al(8),
+                 b_part = al((size_t)G * WL::NPpad * 4), b_flags = al(2 * 4), b_bl = al(8),
                  b_G = al((size_t)Z * Z * 8), b_pl = al((size_t)sweep_grid * 8),
                  b_pg = al((size_t)sweep_grid * Z * Z * 8);
     const size_t need = 5 * b_vec + b_img + b_stats + b_snaps + b_part + b_flags + 2 * b_bl + b_G + b_pl + b_pg;
@@ -959,7 +985,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
             ta.n_steps = n_batches < steps_left ? n_batches : steps_left;
             ta.step0 = (e - 1) * n_batches;
             ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;
-            CVA_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)G * 4, st));
+            CVA_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), st));
             CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, wide_train_kernel, ta, tm));
             steps_left -= ta.n_steps;
             if (max_steps > 0 && steps_left <= 0) return CVA_OK;
