@@ -232,7 +232,7 @@ CVA_API cva_status cva_par_rates(const cva_model_desc *model, const cva_portfoli
 CVA_API int cva_grad_num_params(int E, int C);
 
 /* Neural regression of Sec. 2 (eq. (e:regrkappo)) at one date: the NN+ network of
- * eq. (e:nnp) with two hidden ReLU layers of width `hidden` (64 is compiled) on
+ * eq. (e:nnp) with two hidden ReLU layers of width `hidden` (64 or 128) on
  * the F <= 32 standardised factors, trained by Algorithm 1 (BaseAlg): mini-batch
  * Adam (beta = 0.9, 0.999, eps = 1e-8, step size lr) over n_batches contiguous
  * path ranges for `epochs` epochs, no output ReLU for the first floor(epochs/2)
@@ -245,8 +245,10 @@ CVA_API int cva_grad_num_params(int E, int C);
  * (columns >= F zero), b1 [hidden], W2 [hidden][hidden], b2 [hidden],
  * w3 [hidden], b3, mu. pred_dev (float [M], nullable) receives the best
  * network's predictions, loss_dev (float [epochs], nullable) the loss after each
- * epoch. M must be a multiple of 128 * n_batches. Synchronises `stream`.
- * CVA_ETIMEOUT if a bounded device-side wait gave up. */
+ * epoch. M must be a multiple of 128 * n_batches; features_dev and targets_dev
+ * must be 16-byte aligned (tiles arrive by TMA and bulk copies). Width 64 trains
+ * on one thread-block cluster, width 128 on a cooperative grid of one CTA per SM.
+ * Synchronises `stream`. CVA_ETIMEOUT if a bounded device-side wait gave up. */
 CVA_API cva_status cva_mlp_fit(const float *targets_dev, const float *features_dev, int F, uint64_t M,
                                int hidden, int n_batches, int epochs, float lr, float *params_dev,
                                float *pred_dev, float *loss_dev, void *stream);

@@ -132,26 +132,31 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
         A[r * Z + c] *= sc[r] * (c < n1 ? sc[c] : 1.0);
     }
     __syncthreads();
-    // lower Cholesky factor in place: column j, then the trailing lower triangle;
-    // thread t updates column j + 1 + (t mod U), rows c + (t / U) + k (blockDim / U)
+    // lower Cholesky factor in place, one barrier per column. Every thread takes
+    // column j's pivot d and 1/sqrt(d) by two Newton-Raphson steps
+    // y <- y (3 - d y^2) / 2 from an FP32 seed (relative error 2^-22 -> 2^-44 ->
+    // below FP64 rounding); the trailing lower triangle is updated from the
+    // unscaled column (A[r][c] -= A[r][j] A[c][j] / d) and column j is scaled by
+    // 1/sqrt(d) during the next column's step, which does not read it. Thread t
+    // updates column j + 1 + (t mod U), rows c + (t / U) + k (blockDim / U). The
+    // diagonal of the factor is kept as its reciprocal inv_d.
     for (int j = 0; j < n1; ++j) {
+        double d = A[j * Z + j];
+        const bool bad = !(d > 1e-12);
+        if (bad) d = 1.0;
+        double y = (double)rsqrtf((float)d);
+        y = y * (1.5 - 0.5 * d * y * y);
+        y = y * (1.5 - 0.5 * d * y * y);
         if (tid == 0) {
-            double d = A[j * Z + j];
-            if (!(d > 1e-12)) {
-                s_singular = 1;
-                d = 1.0;
-            }
-            d = sqrt(d);
-            A[j * Z + j] = d;
-            inv_d[j] = 1.0 / d;
+            inv_d[j] = y;
+            if (bad) s_singular = 1;
         }
-        __syncthreads();
-        const double r_d = inv_d[j];
-        for (int r = j + 1 + tid; r < n1; r += blockDim.x) A[r * Z + j] *= r_d;
-        __syncthreads();
-        const int c = j + 1 + (tid % U);   // U >= n1 - 1 - j columns, blockDim / U row groups
+        if (j > 0)
+            for (int r = j + tid; r < n1; r += blockDim.x) A[r * Z + j - 1] *= inv_d[j - 1];
+        const double id = y * y;
+        const int c = j + 1 + (tid % U);
         if (c < n1) {
-            const double lcj = A[c * Z + j];
+            const double lcj = A[c * Z + j] * id;
             for (int r = c + tid / U; r < n1; r += (int)blockDim.x / U) A[r * Z + c] -= A[r * Z + j] * lcj;
         }
         __syncthreads();
