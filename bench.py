@@ -295,7 +295,7 @@ def main():
         torch.cuda.synchronize()
         start.record(stream)
         for s in range(args.steps):
-            c0, evs, _ = step(s + 1)
+            c0, evs, last_pred = step(s + 1)
             a_ms, p_ms, i_ms = sim.kernel_ms()
             sim_ms.append(a_ms)
             price_ms.append(p_ms)
@@ -314,6 +314,27 @@ def main():
         t_max = float(t.item())
     units_per_step = wl.M * wl.N * n * world
     value = units_per_step * args.steps / (t_max / 1e3)
+
+    # ---- twin Monte Carlo validation of the last step's regression at the middle date ----
+    twin = None
+    if rank == 0:
+        i_tw = n // 2
+        phi = last_pred[i_tw].clone()
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        xs = []
+        for cpy in (1, 2):
+            sim.run_twin(args.steps, i_tw, cpy, k0=k0)
+            xs.append(sim.targets()[0, i_tw].clone())
+        est, se = api.twin_l2(phi, xs[0], xs[1])
+        t1e.record(stream)
+        torch.cuda.synchronize()
+        scale = float(torch.mean(xs[0].double() * xs[1].double()))   # estimates E[(E[xi | state])^2]
+        twin = {"date": i_tw, "regression": "the step's" + (" NN+ network" if use_mlp else " least squares"),
+                "l2_error": est, "l2_se": se,
+                "relative_rmse": (max(est, 0.0) ** 0.5) / (scale ** 0.5) if scale > 0 else None,
+                "ms": t0e.elapsed_time(t1e),
+                "estimator": "mean of phi^2 - (xi1 + xi2) phi + xi1 xi2 over two copies branched at the date"}
 
     # ---- end to end through the public API: host inputs in, host results out ----
     pinned = torch.empty((n, wl.M), dtype=torch.float32, pin_memory=True)
@@ -483,7 +504,8 @@ def main():
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
-               "mlp_roofline": mlp_roof, "adjoint_forward": adj, "batched": batched, "precision": precision,
+               "mlp_roofline": mlp_roof, "twin_validation": twin, "adjoint_forward": adj, "batched": batched,
+               "precision": precision,
                "cpu_baseline": cpu,
                "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -119,6 +119,28 @@ CVA_API cva_status cva_sim_create(const cva_model_desc *model, const cva_portfol
  * kernel (default steps, averaged targets) on `stream`. */
 CVA_API cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *stream);
 
+/* Twin Monte Carlo validation (Sec. ss:twin, eqs. (e:val1)-(e:val2)): run the
+ * same simulation as twin copy `copy` (>= 1) branching at pricing date `date`
+ * (0 <= date <= n). Outer paths follow the simulation itself up to t_date (the
+ * same Philox counters, so the states up to t_date are bit-identical) and draw
+ * their Euler increments after t_date, and all their inner default clocks, with
+ * `copy` as the third counter word. Two copies b != b' are therefore
+ * independent given the state of every path at t_date, and the targets of date
+ * `date` they leave in the simulation's buffers (cva_sim_view) are the
+ * conditionally independent copies xi^(1), xi^(2) of eq. (e:val1). Arguments and
+ * asynchrony as cva_simulate; CVA_EINVAL for a date outside [0, n] or copy 0. */
+CVA_API cva_status cva_simulate_twin(cva_sim *sim, uint64_t seed, uint64_t k0, int date, uint32_t copy,
+                                     void *stream);
+
+/* The twin estimator of eq. (e:val1): the mean over M paths of
+ * phi^2 - (xi1 + xi2) phi + xi1 xi2, an unbiased estimate of the L2 error
+ * E[(phi - E[xi | state at the branch date])^2] of any estimate phi computed from
+ * that state, with its Monte Carlo standard error. phi_dev, xi1_dev, xi2_dev:
+ * device float [M]. out2 (host double [2]) receives (estimate, standard error).
+ * FP64 sums in a fixed two-stage order. Synchronises `stream`. */
+CVA_API cva_status cva_twin_l2(const float *phi_dev, const float *xi1_dev, const float *xi2_dev, uint64_t M,
+                               double *out2, void *stream);
+
 /* What cva_sim_view can return; shapes use n = n_steps, F factors, C
  * counterparties, P = n_pf portfolios:
  *   CVA_VIEW_FEATURES  float [n+1][F][M]   state Y_j (r^e, log chi^e, gamma^c)

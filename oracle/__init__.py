@@ -9,6 +9,8 @@ path never imports it. It shares no code with the CUDA library.
   clocks of eq. (e:tau) and assembles the averaged target of eq. (eq:CVA_portfolio).
 * ``lsq`` solves the per-date least-squares problem of eq. (e:forw) by Householder
   QR (numpy), on the standardised feature map.
+* ``twin_l2`` is the twin Monte Carlo estimator of eq. (e:val1) (Sec. ss:twin), and
+  ``simulate(..., copy=(date, b))`` runs twin copy b branching at a pricing date.
 """
 from __future__ import annotations
 
@@ -77,6 +79,13 @@ def _load(path: str):
                                   ctypes.POINTER(_Grid), ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                   ctypes.POINTER(_Out)]
+    L.oracle_simulate_copy.restype = ctypes.c_int
+    L.oracle_simulate_copy.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Portfolio),
+                                       ctypes.POINTER(_Grid), ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32,
+                                       ctypes.c_int, ctypes.POINTER(_Out)]
+    L.oracle_exp_clocks_copy.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                         ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]
     L.oracle_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
     L.oracle_uniform.restype = ctypes.c_double
     L.oracle_uniform.argtypes = [ctypes.c_uint32]
@@ -188,10 +197,11 @@ def exp_clock(seed: int, k: int, l: int, c: int) -> float:
     return float(lib().oracle_exp_clock(seed, k, l, c))
 
 
-def exp_clocks(seed: int, k0: int, k1: int, N: int, C: int) -> np.ndarray:
-    """Standard exponential clocks epsilon of every inner draw: [k1-k0, N, C]."""
+def exp_clocks(seed: int, k0: int, k1: int, N: int, C: int, copy: int = 0) -> np.ndarray:
+    """Standard exponential clocks epsilon of every inner draw: [k1-k0, N, C] (of twin
+    copy `copy` when >= 1)."""
     out = np.zeros((k1 - k0, N, C))
-    lib().oracle_exp_clocks(seed, k0, k1, N, C, _dp(out))
+    lib().oracle_exp_clocks_copy(seed, k0, k1, N, C, copy, _dp(out))
     return out
 
 
@@ -220,8 +230,9 @@ def n_factors(model) -> int:
 
 def simulate(model, pf, grid, k0: int, k1: int, N: int, seed: int,
              want=("features", "I0", "Lambda", "mtm", "idx", "xi_bar"),
-             n_threads: int = 0) -> Dict[str, np.ndarray]:
-    """Run the oracle on outer paths [k0, k1); return the requested arrays.
+             n_threads: int = 0, copy=None) -> Dict[str, np.ndarray]:
+    """Run the oracle on outer paths [k0, k1); return the requested arrays. With
+    copy = (date, b) the run is twin copy b >= 1 branching at that pricing date.
 
     Shapes: features [n+1, F, M], I0 [n+1, M], Lambda [n+1, C, M], mtm [n+1, C, M],
     swap_pv [n+1, S, M], idx [M, N, C] (uint16; n+1 = no default), xi_bar [n, M],
@@ -251,11 +262,23 @@ def simulate(model, pf, grid, k0: int, k1: int, N: int, seed: int,
     m = _model_struct(model, keep)
     p = _pf_struct(pf, keep)
     g = _Grid(float(grid.horizon), int(grid.n_steps), int(grid.substeps))
-    rc = lib().oracle_simulate(ctypes.byref(m), ctypes.byref(p), ctypes.byref(g),
-                               k0, k1, N, seed, n_threads, ctypes.byref(out))
+    branch_date, b = (1 << 30, 0) if copy is None else (int(copy[0]), int(copy[1]))
+    rc = lib().oracle_simulate_copy(ctypes.byref(m), ctypes.byref(p), ctypes.byref(g),
+                                    k0, k1, N, seed, branch_date, b, n_threads, ctypes.byref(out))
     if rc != 0:
         raise ValueError(f"oracle_simulate failed with code {rc}")
     return res
+
+
+def twin_l2(phi: np.ndarray, xi1: np.ndarray, xi2: np.ndarray):
+    """Twin Monte Carlo estimate of the L2 error E[(phi - E[xi | state])^2] (eq.
+    (e:val1)): the mean over paths of phi^2 - (xi1 + xi2) phi + xi1 xi2, where xi1
+    and xi2 are two copies of the target that are independent given the state phi
+    is computed from; returns (estimate, standard error)."""
+    f, a, b = (np.asarray(v, dtype=np.float64) for v in (phi, xi1, xi2))
+    t = f * f - (a + b) * f + a * b
+    se = float(t.std(ddof=1) / np.sqrt(t.size)) if t.size > 1 else 0.0
+    return float(t.mean()), se
 
 
 def cva0(xi_bar: np.ndarray):

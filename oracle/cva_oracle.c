@@ -68,7 +68,9 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
 }
 
-/* Counter layout: (path k, fine step q or inner index l, 0, stream<<24 | block). */
+/* Counter layout: (path k, fine step q or inner index l, copy, stream<<24 | block);
+ * copy = 0 for the simulation itself, b >= 1 for twin copy b of the twin Monte
+ * Carlo validation (Sec. ss:twin) after its branch date. */
 #define STREAM_OUTER 1u
 #define STREAM_INNER 2u
 
@@ -78,20 +80,21 @@ double oracle_uniform(uint32_t x)
     return ((double)(x >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
-static void draw(uint64_t seed, uint32_t k, uint32_t c1, uint32_t stream, uint32_t blk,
+static void draw(uint64_t seed, uint32_t k, uint32_t c1, uint32_t c2, uint32_t stream, uint32_t blk,
                  uint32_t out[4])
 {
-    const uint32_t ctr[4] = {k, c1, 0u, (stream << 24) | blk};
+    const uint32_t ctr[4] = {k, c1, c2, (stream << 24) | blk};
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     oracle_philox4x32_10(ctr, key, out);
 }
 
-/* F standard normals for path k at fine step q: Box-Muller on consecutive pairs. */
-void oracle_normals(uint64_t seed, uint32_t k, uint32_t q, int F, double *z)
+/* F standard normals for path k at fine step q (copy word c2): Box-Muller on
+ * consecutive pairs. */
+static void normals_c(uint64_t seed, uint32_t k, uint32_t q, uint32_t c2, int F, double *z)
 {
     for (int b = 0; 4 * b < F; ++b) {
         uint32_t x[4];
-        draw(seed, k, q, STREAM_OUTER, (uint32_t)b, x);
+        draw(seed, k, q, c2, STREAM_OUTER, (uint32_t)b, x);
         for (int p = 0; p < 2; ++p) {
             const double u1 = oracle_uniform(x[2 * p]);
             const double u2 = oracle_uniform(x[2 * p + 1]);
@@ -103,22 +106,33 @@ void oracle_normals(uint64_t seed, uint32_t k, uint32_t q, int F, double *z)
     }
 }
 
-/* Standard exponential clock epsilon^{c} of inner draw l of path k (eq. (e:tau)). */
-double oracle_exp_clock(uint64_t seed, uint32_t k, uint32_t l, int c)
+void oracle_normals(uint64_t seed, uint32_t k, uint32_t q, int F, double *z) { normals_c(seed, k, q, 0u, F, z); }
+
+/* Standard exponential clock epsilon^{c} of inner draw l of path k (eq. (e:tau)),
+ * copy word c2. */
+double oracle_exp_clock_copy(uint64_t seed, uint32_t k, uint32_t l, uint32_t c2, int c)
 {
     uint32_t x[4];
-    draw(seed, k, l, STREAM_INNER, (uint32_t)(c / 4), x);
+    draw(seed, k, l, c2, STREAM_INNER, (uint32_t)(c / 4), x);
     const double w = oracle_uniform(x[c % 4]);
     return -log1p(-w);
 }
 
-/* All default clocks of paths [k0, k1): out[(k-k0)][l][c], for tie accounting. */
-void oracle_exp_clocks(uint64_t seed, uint64_t k0, uint64_t k1, uint32_t N, int C, double *out)
+double oracle_exp_clock(uint64_t seed, uint32_t k, uint32_t l, int c) { return oracle_exp_clock_copy(seed, k, l, 0u, c); }
+
+/* All default clocks of paths [k0, k1) with copy word c2: out[(k-k0)][l][c], for
+ * tie accounting. */
+void oracle_exp_clocks_copy(uint64_t seed, uint64_t k0, uint64_t k1, uint32_t N, int C, uint32_t c2, double *out)
 {
     for (uint64_t k = k0; k < k1; ++k)
         for (uint32_t l = 0; l < N; ++l)
             for (int c = 0; c < C; ++c)
-                out[((k - k0) * N + l) * (uint64_t)C + c] = oracle_exp_clock(seed, (uint32_t)k, l, c);
+                out[((k - k0) * N + l) * (uint64_t)C + c] = oracle_exp_clock_copy(seed, (uint32_t)k, l, c2, c);
+}
+
+void oracle_exp_clocks(uint64_t seed, uint64_t k0, uint64_t k1, uint32_t N, int C, double *out)
+{
+    oracle_exp_clocks_copy(seed, k0, k1, N, C, 0u, out);
 }
 
 /* ---------------- model, portfolio, grid --------------------------------- */
@@ -255,10 +269,13 @@ static int steps_per_period(double Delta, double delta)
 /*
  * Simulate outer paths k in [k0, k1) and, for each, N inner default draws per
  * counterparty; fill whichever outputs are non-NULL. Returns 0 on success.
+ * With copy >= 1 the run is twin copy `copy` branching at date branch_date: the
+ * Euler increments of steps j > branch_date and all inner clocks draw with copy
+ * as the third counter word (copy 0: the simulation itself).
  */
-int oracle_simulate(const om_model *m, const om_portfolio *pf, const om_grid *g,
-                    uint64_t k0, uint64_t k1, uint32_t N, uint64_t seed,
-                    int n_threads, const om_out *out)
+int oracle_simulate_copy(const om_model *m, const om_portfolio *pf, const om_grid *g,
+                         uint64_t k0, uint64_t k1, uint32_t N, uint64_t seed,
+                         int branch_date, uint32_t copy, int n_threads, const om_out *out)
 {
     const int E = m->E, C = m->C, F = n_factors(m), n = g->n_steps, S = g->substeps;
     const int NS = pf->n_swaps;
@@ -313,7 +330,7 @@ int oracle_simulate(const om_model *m, const om_portfolio *pf, const om_grid *g,
                     for (int s = 0; s < S; ++s) {
                         const int q = (j - 1) * S + s;
                         const double t = q * ds;
-                        oracle_normals(seed, k, (uint32_t)q, F, z);
+                        normals_c(seed, k, (uint32_t)q, j > branch_date ? copy : 0u, F, z);
                         for (int a = 0; a < F; ++a) {
                             double acc = 0.0;
                             for (int b = 0; b <= a; ++b) acc += L[a * F + b] * z[b];
@@ -387,7 +404,7 @@ int oracle_simulate(const om_model *m, const om_portfolio *pf, const om_grid *g,
                 for (int i = 0; i < n; ++i) out->xi_bar[(size_t)i * Mloc + kk] = 0.0;
             for (uint32_t l = 0; l < N; ++l) {
                 for (int c = 0; c < C; ++c) {
-                    const double eps = oracle_exp_clock(seed, k, l, c);
+                    const double eps = oracle_exp_clock_copy(seed, k, l, copy, c);
                     int idx = n + 1;
                     for (int j = 1; j <= n; ++j)
                         if (Lam[c * (n + 1) + j] >= eps) { idx = j; break; }
@@ -414,4 +431,11 @@ int oracle_simulate(const om_model *m, const om_portfolio *pf, const om_grid *g,
     }
     free(L); free(pos_r); free(pos_x); free(pos_g); free(Sigma);
     return 0;
+}
+
+int oracle_simulate(const om_model *m, const om_portfolio *pf, const om_grid *g,
+                    uint64_t k0, uint64_t k1, uint32_t N, uint64_t seed,
+                    int n_threads, const om_out *out)
+{
+    return oracle_simulate_copy(m, pf, g, k0, k1, N, seed, 1 << 30, 0u, n_threads, out);
 }

@@ -47,6 +47,10 @@ SIGNATURES = {
                                       ctypes.POINTER(GridDesc), ctypes.c_uint64, ctypes.c_uint32,
                                       ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
     "cva_simulate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]),
+    "cva_simulate_twin": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.c_uint32, ctypes.c_void_p]),
+    "cva_twin_l2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _dp,
+                                   ctypes.c_void_p]),
     "cva_sim_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                     ctypes.POINTER(ctypes.c_size_t)]),
     "cva_sim_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),

@@ -99,6 +99,14 @@ class Simulation:
         nat.check(N_lib().cva_simulate(self._h, int(seed), int(k0), _stream_handle(stream)), "cva_simulate")
         return self
 
+    def run_twin(self, seed: int, date: int, copy: int, k0: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        """Run the simulation as twin copy `copy` (>= 1) branching at pricing date `date`
+        (twin Monte Carlo validation); its targets of that date are one conditionally
+        independent copy of the target given the state at t_date."""
+        nat.check(N_lib().cva_simulate_twin(self._h, int(seed), int(k0), int(date), int(copy),
+                                            _stream_handle(stream)), "cva_simulate_twin")
+        return self
+
     def kernel_ms(self) -> Tuple[float, float, float]:
         """(path simulation, pricing, inner defaults) device milliseconds of the last run."""
         out = (ctypes.c_float * 3)()
@@ -183,6 +191,19 @@ def cva0(xi0: torch.Tensor, stream=None) -> Tuple[float, float]:
     nat.check(N_lib().cva_cva0(ctypes.c_void_p(xi0.data_ptr()), xi0.numel(),
                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)),
             "cva_cva0")
+    return float(out[0]), float(out[1])
+
+
+def twin_l2(phi: torch.Tensor, xi1: torch.Tensor, xi2: torch.Tensor, stream=None) -> Tuple[float, float]:
+    """Twin estimate of the L2 error of phi (eq. (e:val1)) from two conditionally
+    independent copies of the target, with its standard error (device float [M] each)."""
+    for t in (phi, xi1, xi2):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == phi.numel()
+    out = np.zeros(2)
+    nat.check(N_lib().cva_twin_l2(ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(xi1.data_ptr()),
+                                  ctypes.c_void_p(xi2.data_ptr()), phi.numel(),
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)),
+              "cva_twin_l2")
     return float(out[0]), float(out[1])
 
 

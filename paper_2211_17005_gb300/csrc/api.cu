@@ -363,6 +363,26 @@ cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *stream)
     return CVA_OK;
 }
 
+cva_status cva_simulate_twin(cva_sim *sim, uint64_t seed, uint64_t k0, int date, uint32_t copy, void *stream)
+{
+    if (!sim) return fail(CVA_EINVAL, "sim is NULL");
+    Sim &s = *reinterpret_cast<Sim *>(sim);
+    if (date < 0 || date > s.n) return fail(CVA_EINVAL, "twin: branch date outside [0, n]");
+    if (copy < 1 || copy >= (1u << 24)) return fail(CVA_EINVAL, "twin: copy must be in [1, 2^24)");
+    s.branch_date = date;
+    s.branch = copy;
+    const cva_status r = cva_simulate(sim, seed, k0, stream);
+    s.branch_date = 1 << 30;
+    s.branch = 0;
+    return r;
+}
+
+cva_status cva_twin_l2(const float *phi_dev, const float *xi1_dev, const float *xi2_dev, uint64_t M, double *out2,
+                       void *stream)
+{
+    return twin_l2_fp64(phi_dev, xi1_dev, xi2_dev, M, out2, reinterpret_cast<cudaStream_t>(stream));
+}
+
 cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[3])
 {
     if (!sim || !out_ms) return fail(CVA_EINVAL, "NULL argument");

@@ -92,6 +92,11 @@ struct Sim {
     // profiling events: before the simulation kernel, after it, after the pricing
     // kernel, after the inner-default kernel
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // twin copy being simulated (Sec. ss:twin): outer normals of the steps after
+    // branch_date and all inner clocks draw with the copy id as the third counter
+    // word; 0 (and no branch date) for the simulation itself
+    int branch_date = 1 << 30;
+    uint32_t branch = 0;
 };
 
 // Device buffers of the adjoint sweep (adjoint.cuh).
@@ -171,5 +176,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
 // CVA_0 reduction (reduce.cu).
 cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);
 cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st);
+cva_status twin_l2_fp64(const float *phi, const float *xi1, const float *xi2, uint64_t M, double *out2,
+                        cudaStream_t st);
 
 }  // namespace cva

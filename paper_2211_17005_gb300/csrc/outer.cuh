@@ -48,6 +48,8 @@ __device__ __forceinline__ float expm1_small(float x)
 
 struct OuterArgs {
     uint32_t M, k0, seed_lo, seed_hi;
+    int branch_date;                   // steps j > branch_date draw with counter word `branch`
+    uint32_t branch;
     const float4 *__restrict__ zc;     // [n+1][E][G] (lnA, B, dlnA, dB)
     const float2 *__restrict__ fix;    // [periods+1][E] (lnA, B)
     const int *__restrict__ date_p;    // [n+1]
@@ -104,8 +106,9 @@ __global__ void __launch_bounds__(128) sim_kernel(OuterArgs a)
             for (int i = 0; i < F; ++i) W[i] = 0.f;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                const uint4 x = philox4x32_10(make_uint4(k, q, 0u, (kStreamOuter << 24) | (uint32_t)b),
-                                              a.seed_lo, a.seed_hi);
+                const uint4 x = philox4x32_10(
+                    make_uint4(k, q, j > a.branch_date ? a.branch : 0u, (kStreamOuter << 24) | (uint32_t)b), a.seed_lo,
+                    a.seed_hi);
                 float z[4];
                 box_muller(x.x, x.y, z[0], z[1]);
                 box_muller(x.z, x.w, z[2], z[3]);
@@ -282,6 +285,8 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.M = (uint32_t)s.M;
     args.k0 = (uint32_t)k0;
     args.seed_lo = (uint32_t)seed;
+    args.branch_date = s.branch_date;
+    args.branch = s.branch;
     args.seed_hi = (uint32_t)(seed >> 32);
     args.zc = s.d_zc;
     args.fix = s.d_fix;

@@ -67,6 +67,27 @@ __global__ void philox_fill(const uint4 *__restrict__ ctr, uint4 *__restrict__ o
     if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
 }
 
+// Twin Monte Carlo validation (Sec. ss:twin, eq. (e:val1)): per path the FP64
+// term phi^2 - (xi1 + xi2) phi + xi1 xi2 of two conditionally independent copies;
+// block sums of the terms and of their squares.
+__global__ void __launch_bounds__(kRedThreads) twin_stage1(const float *__restrict__ phi,
+                                                           const float *__restrict__ xi1,
+                                                           const float *__restrict__ xi2, uint64_t M,
+                                                           double2 *__restrict__ part)
+{
+    __shared__ double2 sh[kRedThreads];
+    double s = 0.0, q = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const double f = (double)__ldg(phi + i), a = (double)__ldg(xi1 + i), b = (double)__ldg(xi2 + i);
+        const double t = f * f - (a + b) * f + a * b;
+        s += t;
+        q = fma(t, t, q);
+    }
+    block_sum2(s, q, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(s, q);
+}
+
 // out[c] = sum over rows r of part[r][c], in row order (one thread per column)
 __global__ void sum_cols(const double *__restrict__ part, int rows, int cols, double *__restrict__ out)
 {
@@ -99,6 +120,35 @@ cva_status sum_columns_fp64(const double *part, int rows, int cols, double *out,
 {
     sum_cols<<<(cols + 127) / 128, 128, 0, st>>>(part, rows, cols, out);
     CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
+}
+
+// mean and standard error of the per-path twin terms (two fixed-order stages)
+cva_status twin_l2_fp64(const float *phi, const float *xi1, const float *xi2, uint64_t M, double *out2,
+                        cudaStream_t st)
+{
+    if (!phi || !xi1 || !xi2 || !out2 || M == 0) return fail(CVA_EINVAL, "twin: null pointer or M == 0");
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_red_mu);
+    if (!g_red_buf[dev]) {
+        cudaError_t e = cudaMalloc(&g_red_buf[dev], sizeof(double2) * (kRedBlocks + 1));
+        if (e != cudaSuccess) return fail(CVA_ENOMEM, "twin: scratch allocation failed");
+    }
+    double2 *part = g_red_buf[dev];
+    twin_stage1<<<kRedBlocks, kRedThreads, 0, st>>>(phi, xi1, xi2, M, part);
+    CVA_CUDA_TRY(cudaGetLastError());
+    sum_stage2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, part + kRedBlocks);
+    CVA_CUDA_TRY(cudaGetLastError());
+    double2 h;
+    CVA_CUDA_TRY(cudaMemcpyAsync(&h, part + kRedBlocks, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CVA_CUDA_TRY(cudaStreamSynchronize(st));
+    const double mean = h.x / (double)M;
+    double var = (M > 1) ? (h.y - (double)M * mean * mean) / (double)(M - 1) : 0.0;
+    if (var < 0.0) var = 0.0;
+    out2[0] = mean;
+    out2[1] = sqrt(var / (double)M);
     return CVA_OK;
 }
 

@@ -2,10 +2,12 @@
 // numbers: as easy as 1, 2, 3", SC'11) and the transforms used by the kernels.
 //
 // Counter layout shared with the CPU oracle (which has its own implementation):
-//   (path k, fine step q or inner index l, 0, stream << 24 | block)
+//   (path k, fine step q or inner index l, copy, stream << 24 | block)
 // key = (seed low 32 bits, seed high 32 bits). Stream 1 feeds the outer-path
 // normals (four per block), stream 2 the inner default clocks (four
-// counterparties per block).
+// counterparties per block). copy is 0 for the simulation itself; a twin copy b
+// of the twin Monte Carlo validation draws its outer normals after the branch date
+// and all its inner clocks with copy = b.
 #pragma once
 #include <stdint.h>
 

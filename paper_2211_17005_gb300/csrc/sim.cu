@@ -20,6 +20,7 @@ namespace {
 
 struct InnerArgs {
     uint32_t M, k0, seed_lo, seed_hi, N;
+    uint32_t branch;                  // third counter word of the clocks (twin copy id, 0 otherwise)
     int n, NPF, P;
     const float *__restrict__ thr;    // [n+1][C][M]
     const float *__restrict__ expo;   // [NPF][n+1][C][M]
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256) inner_kernel(InnerArgs a)
         for (uint32_t l = lane; l < a.N; l += 32) {
 #pragma unroll
             for (int cb = 0; cb < (C + 3) / 4; ++cb) {
-                const uint4 x = philox4x32_10(make_uint4(k, l, 0u, (kStreamInner << 24) | (uint32_t)cb),
+                const uint4 x = philox4x32_10(make_uint4(k, l, a.branch, (kStreamInner << 24) | (uint32_t)cb),
                                               a.seed_lo, a.seed_hi);
                 const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -215,6 +216,7 @@ cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.seed_lo = (uint32_t)seed;
     args.seed_hi = (uint32_t)(seed >> 32);
     args.N = s.N;
+    args.branch = s.branch;
     args.n = s.n;
     args.NPF = s.NPF;
     int P = (s.tune_inner_P >= 1 && s.tune_inner_P <= 8) ? s.tune_inner_P : 8;
