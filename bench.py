@@ -336,6 +336,33 @@ def main():
                 "ms": t0e.elapsed_time(t1e),
                 "estimator": "mean of phi^2 - (xi1 + xi2) phi + xi1 xi2 over two copies branched at the date"}
 
+    # ---- oversimulation factor (Prop. 1, Heuristic 1) for the step's regression ----
+    oversim = None
+    if rank == 0:
+        sim.run(args.steps, k0=k0)   # the buffers hold twin copy 2: the step's own paths again
+        torch.cuda.synchronize()
+        Qs, Rs = sim.oversim_stats(last_pred, args.steps)
+        N_small = 8
+        sim_small = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, N_small)
+        def sim_time(sx, reps=5):
+            sx.run(1, k0=k0)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                sx.run(1, k0=k0)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / reps
+        t_big, t_small = sim_time(sim), sim_time(sim_small)
+        sim_small.close()
+        kappa = api.inner_cost_ratio(t_small, N_small, t_big, wl.N)
+        Ni, N_star, M_star = api.oversimulation_choice(Qs[1:n], Rs[1:n], kappa, budget=wl.M * (wl.N + kappa))
+        oversim = {"kappa": kappa, "timings_ms": {f"N={N_small}": t_small, f"N={wl.N}": t_big},
+                   "N_heuristic1": N_star, "M_for_the_same_budget": M_star,
+                   "N_i_median": float(np.nanmedian(Ni)), "Q_over_R_median": float(np.nanmedian(Qs[1:n] / Rs[1:n])),
+                   "regression": "the step's" + (" NN+ network" if use_mlp else " least squares"),
+                   "note": "kappa: cost of an outer path in inner draws from two simulations of the same M (eq. (l:ratio))"}
+
     # ---- end to end through the public API: host inputs in, host results out ----
     pinned = torch.empty((n, wl.M), dtype=torch.float32, pin_memory=True)
     e2e_steps = max(1, min(args.steps, 5))
@@ -504,7 +531,8 @@ def main():
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
-               "mlp_roofline": mlp_roof, "twin_validation": twin, "adjoint_forward": adj, "batched": batched,
+               "mlp_roofline": mlp_roof, "twin_validation": twin, "oversimulation": oversim,
+               "adjoint_forward": adj, "batched": batched,
                "precision": precision,
                "cpu_baseline": cpu,
                "clocks": clk,

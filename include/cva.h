@@ -132,6 +132,21 @@ CVA_API cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *
 CVA_API cva_status cva_simulate_twin(cva_sim *sim, uint64_t seed, uint64_t k0, int date, uint32_t copy,
                                      void *stream);
 
+/* Sampling statistics of Prop. 1 (Sec. ss:choice1) for choosing the
+ * oversimulation factor N. With the pointwise loss g = (xi_i - phi_i(Y_i))^2 of a
+ * single inner draw (X) on an outer path (Y), and phi_i the regression of date i
+ * (pred_dev: device float [n][M], e.g. the predictions of cva_regress_all or
+ * cva_mlp_regress_all), qr_host (host double [n][2]) receives per date
+ *   Q_i = E[Var(g | Y)] = E[g^2] - E[g(X^1) g(X^2)],
+ *   R_i = Var(E[g | Y]) = E[g(X^1) g(X^2)] - E[g]^2,
+ * estimated over the M outer paths from their first two inner draws (the same
+ * default clocks as the simulation's draws 0 and 1, seed = the key of the last
+ * cva_simulate; the simulation must have N >= 2). Dates 0 and n get zeros. The
+ * optimal factor under the budget M (N + kappa) is N_i = sqrt(Q_i kappa / R_i)
+ * (eq. (e:optom)). FP64 sums in a fixed order; synchronises `stream`. */
+CVA_API cva_status cva_oversim_stats(const cva_sim *sim, int pf, const float *pred_dev, uint64_t seed,
+                                     double *qr_host, void *stream);
+
 /* The twin estimator of eq. (e:val1): the mean over M paths of
  * phi^2 - (xi1 + xi2) phi + xi1 xi2, an unbiased estimate of the L2 error
  * E[(phi - E[xi | state at the branch date])^2] of any estimate phi computed from

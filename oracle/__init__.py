@@ -270,6 +270,33 @@ def simulate(model, pf, grid, k0: int, k1: int, N: int, seed: int,
     return res
 
 
+def oversim_stats(o: Dict[str, np.ndarray], recovery: np.ndarray, pred: np.ndarray):
+    """Q_i and R_i of Prop. 1 from the first two inner draws of every path (oracle
+    outputs `idx`, `mtm`, `I0`; pred [n, M]): with the single-draw target
+    xi^l_i = e^{I0_i} sum_c (1 - R_c) e^{-I0_j} MtM_c(j)^+ at j = idx_c^l if i < j <= n,
+    and g_l = (xi^l_i - pred_i)^2, Q_i = mean(g^2) - mean(g_0 g_1) and
+    R_i = mean(g_0 g_1) - mean(g)^2 (mean(g), mean(g^2) over both draws); dates 0
+    and n are zero."""
+    idx, mtm, I0 = o["idx"].astype(np.int64), o["mtm"], o["I0"]
+    n1, C, M = mtm.shape
+    n = n1 - 1
+    V = (1.0 - np.asarray(recovery))[None, :, None] * np.exp(-I0)[:, None, :] * np.maximum(mtm, 0.0)  # [n+1, C, M]
+    Q, R = np.zeros(n), np.zeros(n)
+    kk = np.arange(M)
+    for i in range(1, n):
+        g = []
+        for l in range(2):
+            j = idx[:, l, :].T                                              # [C, M]
+            v = np.where(j <= n, V[np.minimum(j, n), np.arange(C)[:, None], kk[None, :]], 0.0)
+            xi = np.exp(I0[i]) * np.sum(np.where(j > i, v, 0.0), axis=0)
+            g.append((xi - pred[i]) ** 2)
+        m1 = 0.5 * (g[0].mean() + g[1].mean())
+        m2 = 0.5 * ((g[0] ** 2).mean() + (g[1] ** 2).mean())
+        m12 = (g[0] * g[1]).mean()
+        Q[i], R[i] = m2 - m12, m12 - m1 * m1
+    return Q, R
+
+
 def twin_l2(phi: np.ndarray, xi1: np.ndarray, xi2: np.ndarray):
     """Twin Monte Carlo estimate of the L2 error E[(phi - E[xi | state])^2] (eq.
     (e:val1)): the mean over paths of phi^2 - (xi1 + xi2) phi + xi1 xi2, where xi1

@@ -107,6 +107,17 @@ class Simulation:
                                             _stream_handle(stream)), "cva_simulate_twin")
         return self
 
+    def oversim_stats(self, pred: torch.Tensor, seed: int, pf: int = 0, stream=None):
+        """Q_i and R_i of Prop. 1 per date (numpy [n] each) for the regression `pred`
+        ([n, M] device float) of the simulation run with key `seed`."""
+        assert pred.is_cuda and pred.dtype == torch.float32 and pred.is_contiguous()
+        assert pred.shape == (self.n, self.M) and self.N >= 2
+        out = np.zeros((self.n, 2))
+        nat.check(N_lib().cva_oversim_stats(self._h, pf, ctypes.c_void_p(pred.data_ptr()), int(seed),
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            _stream_handle(stream)), "cva_oversim_stats")
+        return out[:, 0], out[:, 1]
+
     def kernel_ms(self) -> Tuple[float, float, float]:
         """(path simulation, pricing, inner defaults) device milliseconds of the last run."""
         out = (ctypes.c_float * 3)()
@@ -192,6 +203,25 @@ def cva0(xi0: torch.Tensor, stream=None) -> Tuple[float, float]:
                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)),
             "cva_cva0")
     return float(out[0]), float(out[1])
+
+
+def inner_cost_ratio(t1: float, N1: int, t2: float, N2: int) -> float:
+    """The cost kappa of an outer path in units of inner draws, from the times t1, t2
+    of two runs with the same M and N1 != N2 inner draws (time proportional to
+    M (kappa + N), eq. (l:ratio))."""
+    return (t1 * N2 - t2 * N1) / (t2 - t1)
+
+
+def oversimulation_choice(Q, R, kappa: float, budget: Optional[float] = None):
+    """Prop. 1 and Heuristic 1: per date N_i = sqrt(Q_i kappa / R_i) (dates with
+    R_i <= 0 or Q_i < 0 skipped), N = their mean, and M = budget / (N + kappa) when a
+    budget (in inner-draw units) is given. Returns (N_i array, N, M or None)."""
+    Q, R = np.asarray(Q, dtype=np.float64), np.asarray(R, dtype=np.float64)
+    ok = (R > 0) & (Q >= 0)
+    Ni = np.full(Q.shape, np.nan)
+    Ni[ok] = np.sqrt(Q[ok] * kappa / R[ok])
+    N = float(np.nanmean(Ni)) if ok.any() else float("nan")
+    return Ni, N, (budget / (N + kappa) if budget is not None else None)
 
 
 def twin_l2(phi: torch.Tensor, xi1: torch.Tensor, xi2: torch.Tensor, stream=None) -> Tuple[float, float]:

@@ -383,6 +383,38 @@ cva_status cva_twin_l2(const float *phi_dev, const float *xi1_dev, const float *
     return twin_l2_fp64(phi_dev, xi1_dev, xi2_dev, M, out2, reinterpret_cast<cudaStream_t>(stream));
 }
 
+cva_status cva_oversim_stats(const cva_sim *sim, int pf, const float *pred_dev, uint64_t seed, double *qr_host,
+                             void *stream)
+{
+    if (!sim || !pred_dev || !qr_host) return fail(CVA_EINVAL, "oversim: NULL argument");
+    const Sim &s = *reinterpret_cast<const Sim *>(sim);
+    if (pf < 0 || pf >= s.NPF) return fail(CVA_EINVAL, "portfolio index out of range");
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const unsigned blocks = (unsigned)((s.M + 255) / 256);
+    const int cols = 3 * s.n;
+    double *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * ((size_t)blocks * cols + cols)) != cudaSuccess)
+        return fail(CVA_ENOMEM, "oversim: scratch allocation failed");
+    cva_status r = launch_oversim(s, pf, pred_dev, seed, buf, blocks, st);
+    if (r == CVA_OK) r = sum_columns_fp64(buf, (int)blocks, cols, buf + (size_t)blocks * cols, st);
+    std::vector<double> h(cols, 0.0);
+    if (r == CVA_OK) {
+        cudaError_t e = cudaMemcpyAsync(h.data(), buf + (size_t)blocks * cols, sizeof(double) * cols,
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "oversim: copy back");
+    }
+    cudaFree(buf);
+    if (r != CVA_OK) return r;
+    const double M = (double)s.M;
+    for (int i = 0; i < s.n; ++i) {
+        const double m1 = h[3 * i] / M, m2 = h[3 * i + 1] / M, m12 = h[3 * i + 2] / M;
+        qr_host[2 * i] = m2 - m12;           // Q_i = E[g^2] - E[g0 g1] = E[Var(g | Y)]
+        qr_host[2 * i + 1] = m12 - m1 * m1;  // R_i = E[g0 g1] - E[g]^2 = Var(E[g | Y])
+    }
+    return CVA_OK;
+}
+
 cva_status cva_sim_kernel_ms(const cva_sim *sim, float out_ms[3])
 {
     if (!sim || !out_ms) return fail(CVA_EINVAL, "NULL argument");

@@ -129,6 +129,9 @@ void forget_const_owner(const Sim *s);
 bool outer_supported(int E, int C, int CS, int G, int NPF, int *Ginst);
 cva_status launch_adjoint(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st);
 cva_status sum_columns_fp64(const double *part, int rows, int cols, double *out, cudaStream_t st);
+// Block sums of the Prop. 1 statistics (sim.cu): part [blocks][n][3].
+cva_status launch_oversim(const Sim &s, int pf, const float *pred, uint64_t seed, double *part, unsigned blocks,
+                          cudaStream_t st);
 
 // One grouped least-squares job: group g reads features feat0 + g*feat_stride ([F][M])
 // and target t of it at targ0 + g*targ_stride + t*targ_tstride (nt targets share

@@ -137,7 +137,129 @@ __global__ void __launch_bounds__(256) inner_kernel(InnerArgs a)
     }
 }
 
+// Sampling statistics of Prop. 1 (Sec. ss:choice1). For the pointwise loss
+// g_l = (xi^{k,l}_i - phi_i(Y^k))^2 of the first two inner draws l = 0, 1 of path
+// k (single-draw targets of eq. (eq:CVA_portfolio): the same clocks as the
+// simulation's draws 0 and 1), block sums over paths, per date i in [1, n-1], of
+// (g0 + g1)/2, (g0^2 + g1^2)/2 and g0 g1, in FP64: part[block][n][3] (date 0 zero).
+struct OversimArgs {
+    uint32_t M, k0, seed_lo, seed_hi;
+    int n, pf;
+    const float *__restrict__ thr;    // [n+1][C][M]
+    const float *__restrict__ expo;   // [NPF][n+1][C][M]
+    const float *__restrict__ disc;   // [n+1][M]
+    const float *__restrict__ pred;   // [n][M]
+    double *part;
+};
+
+template <int C>
+__global__ void __launch_bounds__(256) oversim_kernel(OversimArgs a)
+{
+    __shared__ double red[8][3];
+    const uint32_t M = a.M, kl = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = kl < M;
+    const int n = a.n, np1 = n + 1, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int idx[2][C];
+    float vs[2][C];
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            idx[l][c] = n + 1;
+            vs[l][c] = 0.f;
+        }
+    if (live) {
+        const uint32_t k = a.k0 + kl;
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+#pragma unroll
+            for (int cb = 0; cb < (C + 3) / 4; ++cb) {
+                const uint4 x = philox4x32_10(make_uint4(k, (uint32_t)l, 0u, (kStreamInner << 24) | (uint32_t)cb),
+                                              a.seed_lo, a.seed_hi);
+                const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int c = 4 * cb + t;
+                    if (c < C) {
+                        const float w = uniform23(xs[t]);
+                        int lo = 1, len = n;   // first j in [1, n] with T(j) >= w, else n+1
+                        while (len > 0) {
+                            const int h = len >> 1;
+                            if (__ldg(a.thr + ((size_t)(lo + h) * C + c) * M + kl) < w) {
+                                lo += h + 1;
+                                len -= h + 1;
+                            } else {
+                                len = h;
+                            }
+                        }
+                        idx[l][c] = lo;
+                        if (lo <= n) vs[l][c] = __ldg(a.expo + ((size_t)(a.pf * np1 + lo) * C + c) * M + kl);
+                    }
+                }
+            }
+    }
+    for (int i = 1; i < n; ++i) {
+        double s[3] = {0.0, 0.0, 0.0};
+        if (live) {
+            float h0 = 0.f, h1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                if (idx[0][c] > i) h0 += vs[0][c];
+                if (idx[1][c] > i) h1 += vs[1][c];
+            }
+            const float e = expf(__ldg(a.disc + (size_t)i * M + kl));
+            const double f = (double)__ldg(a.pred + (size_t)i * M + kl);
+            const double g0 = ((double)(h0 * e) - f) * ((double)(h0 * e) - f),
+                         g1 = ((double)(h1 * e) - f) * ((double)(h1 * e) - f);
+            s[0] = 0.5 * (g0 + g1);
+            s[1] = 0.5 * (g0 * g0 + g1 * g1);
+            s[2] = g0 * g1;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+            if (lane == 0) red[warp][q] = s[q];
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w][threadIdx.x];
+            a.part[((size_t)blockIdx.x * n + i) * 3 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) a.part[(size_t)blockIdx.x * n * 3 + threadIdx.x] = 0.0;
+}
+
 }  // namespace
+
+cva_status launch_oversim(const Sim &s, int pf, const float *pred, uint64_t seed, double *part, unsigned blocks,
+                          cudaStream_t st)
+{
+    OversimArgs a;
+    a.M = (uint32_t)s.M;
+    a.k0 = 0;
+    a.seed_lo = (uint32_t)seed;
+    a.seed_hi = (uint32_t)(seed >> 32);
+    a.n = s.n;
+    a.pf = pf;
+    a.thr = s.d_thr;
+    a.expo = s.d_expo;
+    a.disc = s.d_disc;
+    a.pred = pred;
+    a.part = part;
+    switch (s.C) {
+    case 1: oversim_kernel<1><<<blocks, 256, 0, st>>>(a); break;
+    case 2: oversim_kernel<2><<<blocks, 256, 0, st>>>(a); break;
+    case 4: oversim_kernel<4><<<blocks, 256, 0, st>>>(a); break;
+    case 8: oversim_kernel<8><<<blocks, 256, 0, st>>>(a); break;
+    case 16: oversim_kernel<16><<<blocks, 256, 0, st>>>(a); break;
+    default: return fail(CVA_ENOTSUP, "oversimulation statistics compiled for C in {1, 2, 4, 8, 16}");
+    }
+    CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
+}
 
 // Registry of the compiled outer-kernel shapes (one translation unit each).
 int outer_insts_small(const OuterInst **out);
