@@ -363,6 +363,24 @@ def main():
                    "regression": "the step's" + (" NN+ network" if use_mlp else " least squares"),
                    "note": "kappa: cost of an outer path in inner draws from two simulations of the same M (eq. (l:ratio))"}
 
+    # ---- nested Monte Carlo reference at the middle date (first 16384 paths, 1024 copies) ----
+    nested = None
+    if rank == 0:
+        Mv, K = min(16384, wl.M), 1024
+        i_n = n // 2
+        sim_v = api.Simulation(wl.model, wl.portfolios, wl.grid, Mv, wl.N)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        ref_n = sim_v.nested_reference(args.steps, i_n, K, k0=k0)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        rr, cnt = api.relative_rmse(last_pred[i_n, :Mv].contiguous(), ref_n)
+        sim_v.close()
+        nested = {"date": i_n, "paths": Mv, "copies": K, "relative_rmse": rr, "paths_with_nonzero_reference": cnt,
+                  "ms": q0.elapsed_time(q1),
+                  "regression": "the step's" + (" NN+ network" if use_mlp else " least squares"),
+                  "measure": "sqrt(mean(((pred - nested) / nested)^2)) over paths with a nonzero nested value"}
+
     # ---- end to end through the public API: host inputs in, host results out ----
     pinned = torch.empty((n, wl.M), dtype=torch.float32, pin_memory=True)
     e2e_steps = max(1, min(args.steps, 5))
@@ -532,6 +550,7 @@ def main():
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
                "mlp_roofline": mlp_roof, "twin_validation": twin, "oversimulation": oversim,
+               "nested_validation": nested,
                "adjoint_forward": adj, "batched": batched,
                "precision": precision,
                "cpu_baseline": cpu,

@@ -132,6 +132,24 @@ CVA_API cva_status cva_simulate(cva_sim *sim, uint64_t seed, uint64_t k0, void *
 CVA_API cva_status cva_simulate_twin(cva_sim *sim, uint64_t seed, uint64_t k0, int date, uint32_t copy,
                                      void *stream);
 
+/* Nested Monte Carlo reference of the conditional CVA at a date (the benchmark of
+ * Sec. 4.3, with copies inner paths per outer path): out_dev (device float [M])
+ * receives, for every outer path, the mean over twin copies b = 1..copies
+ * (cva_simulate_twin, branched at `date`) of the averaged target of portfolio pf
+ * at that date, an estimate of E[xi_bar_date | state at t_date] whose error falls
+ * as 1/sqrt(copies). Runs `copies` full simulations on `stream` and leaves the
+ * last copy in the simulation's buffers. CVA_EINVAL for date outside [0, n),
+ * copies outside [1, 2^24) or a bad portfolio index. */
+CVA_API cva_status cva_nested_reference(cva_sim *sim, uint64_t seed, uint64_t k0, int pf, int date, int copies,
+                                        float *out_dev, void *stream);
+
+/* The relative error measure of the paper's nested Monte Carlo comparison:
+ * sqrt(mean over paths with ref != 0 of ((phi - ref) / ref)^2). phi_dev, ref_dev:
+ * device float [M]. out2 (host double [2]) receives (the relative RMSE, the number
+ * of paths with ref != 0). FP64 sums in a fixed order; synchronises `stream`. */
+CVA_API cva_status cva_relative_rmse(const float *phi_dev, const float *ref_dev, uint64_t M, double *out2,
+                                     void *stream);
+
 /* Sampling statistics of Prop. 1 (Sec. ss:choice1) for choosing the
  * oversimulation factor N. With the pointwise loss g = (xi_i - phi_i(Y_i))^2 of a
  * single inner draw (X) on an outer path (Y), and phi_i the regression of date i

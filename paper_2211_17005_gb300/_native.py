@@ -51,6 +51,9 @@ SIGNATURES = {
                                          ctypes.c_uint32, ctypes.c_void_p]),
     "cva_twin_l2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _dp,
                                    ctypes.c_void_p]),
+    "cva_nested_reference": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "cva_relative_rmse": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _dp, ctypes.c_void_p]),
     "cva_oversim_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, _dp,
                                          ctypes.c_void_p]),
     "cva_sim_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),

@@ -107,6 +107,17 @@ class Simulation:
                                             _stream_handle(stream)), "cva_simulate_twin")
         return self
 
+    def nested_reference(self, seed: int, date: int, copies: int, pf: int = 0, k0: int = 0,
+                         stream=None) -> torch.Tensor:
+        """Nested Monte Carlo reference of the conditional CVA at `date` for every path:
+        the mean of `copies` twin copies' targets (device float [M]). Overwrites the
+        simulation's buffers (the last copy stays)."""
+        out = torch.empty(self.M, dtype=torch.float32, device=self.device)
+        nat.check(N_lib().cva_nested_reference(self._h, int(seed), int(k0), pf, int(date), int(copies),
+                                               ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+                  "cva_nested_reference")
+        return out
+
     def oversim_stats(self, pred: torch.Tensor, seed: int, pf: int = 0, stream=None):
         """Q_i and R_i of Prop. 1 per date (numpy [n] each) for the regression `pred`
         ([n, M] device float) of the simulation run with key `seed`."""
@@ -203,6 +214,17 @@ def cva0(xi0: torch.Tensor, stream=None) -> Tuple[float, float]:
                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)),
             "cva_cva0")
     return float(out[0]), float(out[1])
+
+
+def relative_rmse(phi: torch.Tensor, ref: torch.Tensor, stream=None) -> Tuple[float, int]:
+    """sqrt(mean((phi - ref)^2 / ref^2)) over the paths where ref != 0, and their number."""
+    for t in (phi, ref):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == phi.numel()
+    out = np.zeros(2)
+    nat.check(N_lib().cva_relative_rmse(ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(ref.data_ptr()),
+                                        phi.numel(), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        _stream_handle(stream)), "cva_relative_rmse")
+    return float(out[0]), int(out[1])
 
 
 def inner_cost_ratio(t1: float, N1: int, t2: float, N2: int) -> float:

@@ -383,6 +383,29 @@ cva_status cva_twin_l2(const float *phi_dev, const float *xi1_dev, const float *
     return twin_l2_fp64(phi_dev, xi1_dev, xi2_dev, M, out2, reinterpret_cast<cudaStream_t>(stream));
 }
 
+cva_status cva_nested_reference(cva_sim *sim, uint64_t seed, uint64_t k0, int pf, int date, int copies,
+                                float *out_dev, void *stream)
+{
+    if (!sim || !out_dev) return fail(CVA_EINVAL, "nested: NULL argument");
+    Sim &s = *reinterpret_cast<Sim *>(sim);
+    if (pf < 0 || pf >= s.NPF) return fail(CVA_EINVAL, "portfolio index out of range");
+    if (date < 0 || date >= s.n) return fail(CVA_EINVAL, "nested: date outside [0, n)");
+    if (copies < 1 || copies >= (1 << 24)) return fail(CVA_EINVAL, "nested: copies must be in [1, 2^24)");
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const float *row = s.d_targets + ((size_t)pf * s.n + date) * s.M;
+    for (int b = 1; b <= copies; ++b) {
+        cva_status r = cva_simulate_twin(sim, seed, k0, date, (uint32_t)b, stream);
+        if (r == CVA_OK) r = accumulate_mean(out_dev, row, s.M, b == 1, b == copies, copies, st);
+        if (r != CVA_OK) return r;
+    }
+    return CVA_OK;
+}
+
+cva_status cva_relative_rmse(const float *phi_dev, const float *ref_dev, uint64_t M, double *out2, void *stream)
+{
+    return relative_rmse_fp64(phi_dev, ref_dev, M, out2, reinterpret_cast<cudaStream_t>(stream));
+}
+
 cva_status cva_oversim_stats(const cva_sim *sim, int pf, const float *pred_dev, uint64_t seed, double *qr_host,
                              void *stream)
 {

@@ -181,5 +181,7 @@ cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_
 cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st);
 cva_status twin_l2_fp64(const float *phi, const float *xi1, const float *xi2, uint64_t M, double *out2,
                         cudaStream_t st);
+cva_status accumulate_mean(float *acc, const float *x, uint64_t M, int first, int last, int copies, cudaStream_t st);
+cva_status relative_rmse_fp64(const float *phi, const float *ref, uint64_t M, double *out2, cudaStream_t st);
 
 }  // namespace cva

@@ -88,6 +88,38 @@ __global__ void __launch_bounds__(kRedThreads) twin_stage1(const float *__restri
     if (threadIdx.x == 0) part[blockIdx.x] = make_double2(s, q);
 }
 
+// Nested Monte Carlo reference (Sec. 4.3): acc (+)= x, and on the last copy the
+// mean acc / copies.
+__global__ void accumulate_kernel(float *__restrict__ acc, const float *__restrict__ x, uint64_t M, int first,
+                                  float scale)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float v = first ? x[i] : acc[i] + x[i];
+        acc[i] = v * scale;
+    }
+}
+
+// Relative error against a reference, over the paths where the reference is not
+// zero: block sums of ((phi - ref) / ref)^2 and of the number of such paths (FP64).
+__global__ void __launch_bounds__(kRedThreads) relerr_stage1(const float *__restrict__ phi,
+                                                             const float *__restrict__ ref, uint64_t M,
+                                                             double2 *__restrict__ part)
+{
+    __shared__ double2 sh[kRedThreads];
+    double s = 0.0, q = 0.0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const double r = (double)__ldg(ref + i);
+        if (r != 0.0) {
+            const double e = ((double)__ldg(phi + i) - r) / r;
+            s = fma(e, e, s);
+            q += 1.0;
+        }
+    }
+    block_sum2(s, q, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(s, q);
+}
+
 // out[c] = sum over rows r of part[r][c], in row order (one thread per column)
 __global__ void sum_cols(const double *__restrict__ part, int rows, int cols, double *__restrict__ out)
 {
@@ -120,6 +152,38 @@ cva_status sum_columns_fp64(const double *part, int rows, int cols, double *out,
 {
     sum_cols<<<(cols + 127) / 128, 128, 0, st>>>(part, rows, cols, out);
     CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
+}
+
+cva_status accumulate_mean(float *acc, const float *x, uint64_t M, int first, int last, int copies, cudaStream_t st)
+{
+    accumulate_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(acc, x, M, first, last ? 1.0f / (float)copies : 1.0f);
+    CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
+}
+
+// sqrt(mean over paths with ref != 0 of ((phi - ref) / ref)^2) and the number of such paths
+cva_status relative_rmse_fp64(const float *phi, const float *ref, uint64_t M, double *out2, cudaStream_t st)
+{
+    if (!phi || !ref || !out2 || M == 0) return fail(CVA_EINVAL, "relative rmse: null pointer or M == 0");
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_red_mu);
+    if (!g_red_buf[dev]) {
+        cudaError_t e = cudaMalloc(&g_red_buf[dev], sizeof(double2) * (kRedBlocks + 1));
+        if (e != cudaSuccess) return fail(CVA_ENOMEM, "relative rmse: scratch allocation failed");
+    }
+    double2 *part = g_red_buf[dev];
+    relerr_stage1<<<kRedBlocks, kRedThreads, 0, st>>>(phi, ref, M, part);
+    CVA_CUDA_TRY(cudaGetLastError());
+    sum_stage2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, part + kRedBlocks);
+    CVA_CUDA_TRY(cudaGetLastError());
+    double2 h;
+    CVA_CUDA_TRY(cudaMemcpyAsync(&h, part + kRedBlocks, sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CVA_CUDA_TRY(cudaStreamSynchronize(st));
+    out2[0] = h.y > 0.0 ? sqrt(h.x / h.y) : 0.0;
+    out2[1] = h.y;
     return CVA_OK;
 }
 
