@@ -342,9 +342,10 @@ def main():
         sim.run(args.steps, k0=k0)   # the buffers hold twin copy 2: the step's own paths again
         torch.cuda.synchronize()
         Qs, Rs = sim.oversim_stats(last_pred, args.steps)
-        N_small = 8
+        N_small, N_big = 8, 512   # a wide spread of N: the time difference is the measured quantity
         sim_small = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, N_small)
-        def sim_time(sx, reps=5):
+        sim_big = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, N_big)
+        def sim_time(sx, reps=10):
             sx.run(1, k0=k0)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
@@ -353,11 +354,12 @@ def main():
             a1.record(stream)
             torch.cuda.synchronize()
             return a0.elapsed_time(a1) / reps
-        t_big, t_small = sim_time(sim), sim_time(sim_small)
+        t_small, t_big = sim_time(sim_small), sim_time(sim_big)
         sim_small.close()
-        kappa = api.inner_cost_ratio(t_small, N_small, t_big, wl.N)
+        sim_big.close()
+        kappa = api.inner_cost_ratio(t_small, N_small, t_big, N_big)
         Ni, N_star, M_star = api.oversimulation_choice(Qs[1:n], Rs[1:n], kappa, budget=wl.M * (wl.N + kappa))
-        oversim = {"kappa": kappa, "timings_ms": {f"N={N_small}": t_small, f"N={wl.N}": t_big},
+        oversim = {"kappa": kappa, "timings_ms": {f"N={N_small}": t_small, f"N={N_big}": t_big},
                    "N_heuristic1": N_star, "M_for_the_same_budget": M_star,
                    "N_i_median": float(np.nanmedian(Ni)), "Q_over_R_median": float(np.nanmedian(Qs[1:n] / Rs[1:n])),
                    "regression": "the step's" + (" NN+ network" if use_mlp else " least squares"),
@@ -400,6 +402,13 @@ def main():
     h2d = 8 * (n + 1) * E * G + 8 * (n // 1 + 2) * E + 4 * (n + 1) + 4 * n * wl.grid.substeps * E
     d2h = 4 * n * wl.M + 16
     e2e_value = units_per_step / e2e_s
+
+    # kernels of this library launched per step: path simulation, pricing, inner defaults,
+    # the two CVA_0 reduction stages, then the regression: for Algorithm 2 one
+    # standardisation launch and per date E train launches, E loss passes, the refit's
+    # Gram pass and the prediction pass, and the refit; for least squares the grouped
+    # Gram, solve and prediction launches
+    launches_per_step = 3 + 2 + ((1 + (n - 1) * (2 * epochs + 3)) if use_mlp else 3)
 
     # ---- roofline of the dominant kernel ----
     pk, src = peaks()
@@ -557,7 +566,7 @@ def main():
                "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
-               "gpu_launches": 8 * args.steps}
+               "gpu_launches": launches_per_step * args.steps}
         print(json.dumps(out))
     sim.close()
     if world > 1:
