@@ -1,8 +1,8 @@
 // Grouped least-squares regression of eq. (e:forw), one group per pricing date:
 //   w = argmin_w sum_k (xi_k - w^T phi(Y_k))^2.
 // The augmented Gram matrix [phi, xi]^T [phi, xi] of the basis centred on path
-// 0's state is accumulated from FP32 products in FP32 runs of >= 64 rows, then
-// in FP64 (per thread, per block, then across blocks in a fixed order), and
+// 0's state is accumulated from FP32 products in FP32 runs of 512 rows per thread,
+// then in FP64 (per thread, per block, then across blocks in a fixed order), and
 // solved by a Jacobi-scaled Cholesky factorisation in FP64. The pass over the
 // features and targets is the only HBM traffic: every byte is read once.
 #include <math.h>
@@ -35,18 +35,18 @@ struct LsqArgs {
     size_t pred_tstride = 0;    // floats between a group's predictions
 };
 
-// value of augmented column `col` at row k (columns m..m+nt-1 are the targets)
+// value of augmented column `col` at row k (columns m..m+nt-1 are the targets);
+// c0[f] is path 0's value of factor f (the centring of the basis)
 __device__ __forceinline__ float basis_value(const LsqArgs &a, const float *feat, const float *targ,
-                                            int col, uint32_t k)
+                                            const float *c0, int col, uint32_t k)
 {
     if (col >= a.m) return __ldg(targ + (size_t)(col - a.m) * a.targ_tstride + k);
     if (col == 0) return 1.f;
     if (a.basis == CVA_BASIS_POLY2) {
-        const float d = __ldg(feat + k) - __ldg(feat);
+        const float d = __ldg(feat + k) - c0[0];
         return col == 1 ? d : d * d;
     }
-    const float *f = feat + (size_t)(col - 1) * a.M;
-    return __ldg(f + k) - __ldg(f);
+    return __ldg(feat + (size_t)(col - 1) * a.M + k) - c0[col - 1];
 }
 
 template <int MP, int TR>
@@ -77,6 +77,8 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram(LsqArgs a)
             t -= NBLK - i;
         }
     }
+    __shared__ float c0[40];
+    for (int f = tid; f < (a.basis == CVA_BASIS_POLY2 ? 1 : a.F); f += kGramThreads) c0[f] = __ldg(feat + (size_t)f * a.M);
     double dacc[16];
     float acc[16];
 #pragma unroll
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram(LsqArgs a)
             const int col = i / TR, r = i % TR;
             const uint32_t k = r0 + r;
             float v = 0.f;
-            if (col < mA && k < r_end) v = basis_value(a, feat, targ, col, k);
+            if (col < mA && k < r_end) v = basis_value(a, feat, targ, c0, col, k);
             tile[r * RS + col] = v;
         }
         __syncthreads();
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram(LsqArgs a)
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(xv[u], yv[v], acc[u * 4 + v]);
-                if (++since_flush == 64) {
+                if (++since_flush == 512) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         dacc[i] += (double)acc[i];
@@ -223,25 +225,43 @@ __global__ void __launch_bounds__(256) lsq_solve(LsqArgs a)
     a.status[g] = dropped;
 }
 
+// Predictions of every target column of group g (blockIdx.y) at one path per
+// thread: the features are read once per path for all nt columns, and the block
+// converts the group's FP64 coefficients to FP32 once (FP64 conversions run on
+// the slow FP64 pipe). The FMA order per column is the basis order.
 __global__ void __launch_bounds__(256) lsq_predict(LsqArgs a)
 {
-    const int g = blockIdx.y, t = blockIdx.z;
+    __shared__ float cs[40 * 40];   // [nt][m], m + nt <= 40
+    __shared__ float f0[40];        // path 0's state: the centring of the basis
+    const int g = blockIdx.y, nt = a.nt, m = a.m;
+    const double *co = a.coef + (size_t)g * nt * m;
+    const float *feat = a.feat0 + (size_t)g * a.feat_stride;
+    for (int i = threadIdx.x; i < nt * m; i += blockDim.x) cs[i] = (float)co[i];
+    const int nf = a.basis == CVA_BASIS_POLY2 ? 1 : a.F;
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) f0[f] = __ldg(feat + (size_t)f * a.M);
+    __syncthreads();
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.M) return;
-    const double *co = a.coef + ((size_t)g * a.nt + t) * a.m;
-    const float *feat = a.feat0 + (size_t)g * a.feat_stride;
-    float acc = (float)co[0];
+    float *out = a.pred0 + (size_t)g * a.pred_stride + k;
     if (a.basis == CVA_BASIS_POLY2) {
-        const float d = __ldg(feat + k) - __ldg(feat);
-        acc = fmaf((float)co[1], d, acc);
-        acc = fmaf((float)co[2], d * d, acc);
-    } else {
-        for (int f = 0; f < a.F; ++f) {
-            const float *fr = feat + (size_t)f * a.M;
-            acc = fmaf((float)co[1 + f], __ldg(fr + k) - __ldg(fr), acc);
-        }
+        const float d = __ldg(feat + k) - f0[0];
+        for (int t = 0; t < nt; ++t)
+            out[(size_t)t * a.pred_tstride] = fmaf(cs[t * m + 2], d * d, fmaf(cs[t * m + 1], d, cs[t * m]));
+        return;
     }
-    a.pred0[(size_t)g * a.pred_stride + (size_t)t * a.pred_tstride + k] = acc;
+    for (int t0 = 0; t0 < nt; t0 += 8) {
+        const int tn = nt - t0 < 8 ? nt - t0 : 8;
+        float acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = u < tn ? cs[(t0 + u) * m] : 0.f;
+        for (int f = 0; f < a.F; ++f) {
+            const float x = __ldg(feat + (size_t)f * a.M + k) - f0[f];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < tn) acc[u] = fmaf(cs[(t0 + u) * m + 1 + f], x, acc[u]);
+        }
+        for (int u = 0; u < tn; ++u) out[(size_t)(t0 + u) * a.pred_tstride] = acc[u];
+    }
 }
 
 // Library-owned scratch for the Gram partials and coefficients, per device.
@@ -322,7 +342,7 @@ cva_status lsq_launch(const LsqJob &j, double *scratch, size_t scratch_cap, doub
     }
     CVA_CUDA_TRY(cudaGetLastError());
     if (j.pred0) {
-        lsq_predict<<<dim3((unsigned)((j.M + 255) / 256), (unsigned)j.groups, (unsigned)j.nt), 256, 0, st>>>(a);
+        lsq_predict<<<dim3((unsigned)((j.M + 255) / 256), (unsigned)j.groups), 256, 0, st>>>(a);
         CVA_CUDA_TRY(cudaGetLastError());
     }
     if (coef_host) {

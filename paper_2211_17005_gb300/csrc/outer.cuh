@@ -10,8 +10,8 @@
 // int r^0 (FP64) and Lambda^c (compensated FP32). At each pricing date it
 // stores the state Y_j, int r^0 and the threshold 1 - exp(-Lambda_c(t_j)).
 //
-// price_kernel (one thread per outer path and pricing date): the portfolio MtM
-// per counterparty from the App. B swap formula, regrouped exactly by
+// price_kernel (one thread per outer path, pricing date and portfolio): the
+// portfolio MtM per counterparty from the App. B swap formula, regrouped exactly by
 // (counterparty, currency, reset date), and the exposure (1-R_c) beta_j MtM^+.
 // It reads the state of date j and the short rates of the last reset date
 // (Remark rem:pathdep) from the stored states; every (path, date) is
@@ -160,23 +160,23 @@ __global__ void __launch_bounds__(128) sim_kernel(OuterArgs a)
     }
 }
 
-template <int E, int C, int CS, int G, int NPF>
+// One portfolio per block (blockIdx.z): a block's date-bucketed weights (C E G
+// pairs) stay within the constant cache whatever the number of portfolios.
+template <int E, int C, int CS, int G>
 __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
 {
     constexpr int F = 2 * E - 1 + CS;
     const uint32_t kl = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
+    const int j = blockIdx.y, pf = blockIdx.z;
     if (kl >= a.M) return;
     const size_t M = a.M;
     const int n = c_sim.n, ppp = c_sim.ppp;
     if (j == 0) {   // no default at t_0: exposures of date 0 are never used
 #pragma unroll
-        for (int pf = 0; pf < NPF; ++pf)
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                a.expo[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
-                if (a.mtm) a.mtm[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
-            }
+        for (int c = 0; c < C; ++c) {
+            a.expo[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
+            if (a.mtm) a.mtm[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
+        }
         return;
     }
     const int p = __ldg(a.date_p + j);          // t_j in (p delta, (p+1) delta]
@@ -185,11 +185,9 @@ __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
     const float2 *fx = a.fix + (size_t)p * E;
     const float beta = expf(-__ldg(a.disc + (size_t)j * M + kl));
 
-    float mt[NPF][C];
+    float mt[C];
 #pragma unroll
-    for (int pf = 0; pf < NPF; ++pf)
-#pragma unroll
-        for (int c = 0; c < C; ++c) mt[pf][c] = 0.f;
+    for (int c = 0; c < C; ++c) mt[c] = 0.f;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const float re = __ldg(fe + (size_t)e * M);
@@ -223,26 +221,22 @@ __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
         }
         const float chi = (e == 0) ? 1.f : expf(__ldg(fe + (size_t)(E - 1 + (e > 0 ? e : 1)) * M));
 #pragma unroll
-        for (int pf = 0; pf < NPF; ++pf)
+        for (int c = 0; c < C; ++c) {
+            const int base = ((pf * C + c) * E + e) * G;
+            float acc = 0.f;
 #pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const int base = ((pf * C + c) * E + e) * G;
-                float acc = 0.f;
+            for (int h = 0; h < G; ++h) acc = fmaf(c_w.wA[base + h], D[h], acc);
 #pragma unroll
-                for (int h = 0; h < G; ++h) acc = fmaf(c_w.wA[base + h], D[h], acc);
-#pragma unroll
-                for (int g = 0; g < G; ++g) acc = fmaf(-c_w.wK[base + g], Z[g], acc);
-                mt[pf][c] = fmaf(chi, acc, mt[pf][c]);
-            }
+            for (int g = 0; g < G; ++g) acc = fmaf(-c_w.wK[base + g], Z[g], acc);
+            mt[c] = fmaf(chi, acc, mt[c]);
+        }
     }
 #pragma unroll
-    for (int pf = 0; pf < NPF; ++pf)
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const size_t o = ((size_t)(pf * (n + 1) + j) * C + c) * M + kl;
-            a.expo[o] = c_sim.lgd[c] * beta * fmaxf(mt[pf][c], 0.f);
-            if (a.mtm) a.mtm[o] = mt[pf][c];
-        }
+    for (int c = 0; c < C; ++c) {
+        const size_t o = ((size_t)(pf * (n + 1) + j) * C + c) * M + kl;
+        a.expo[o] = c_sim.lgd[c] * beta * fmaxf(mt[c], 0.f);
+        if (a.mtm) a.mtm[o] = mt[c];
+    }
 }
 
 }  // namespace
@@ -318,7 +312,7 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     sim_kernel<E, C, CS><<<(args.M + sb - 1) / sb, sb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
-    price_kernel<E, C, CS, G, NPF><<<dim3((args.M + pb - 1) / pb, (unsigned)s.n + 1u), pb, 0, st>>>(args);
+    price_kernel<E, C, CS, G><<<dim3((args.M + pb - 1) / pb, (unsigned)s.n + 1u, (unsigned)NPF), pb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     if (!capturing) CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
     return CVA_OK;
