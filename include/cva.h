@@ -257,6 +257,15 @@ CVA_API cva_status cva_regress_portfolios(cva_sim *sim, int basis, float *pred_d
 CVA_API cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, size_t report_len,
                                 void *stream);
 
+/* Sets the tile shapes of a simulation directly (e.g. a choice cva_autotune made
+ * in an earlier process): sim_block in {64, 128}, price_block in {128, 256},
+ * inner_paths_per_block in {0 (automatic), 2, 4, 8}, lsq_chunk_target in
+ * [152, 2^20], portfolios_per_price_block in {1, 2, 3} dividing the simulation's
+ * number of portfolios. None of them changes any result bit. Returns CVA_EINVAL
+ * (nothing changed) on a value outside these sets. No GPU work. */
+CVA_API cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner_paths_per_block,
+                                 int lsq_chunk_target, int portfolios_per_price_block);
+
 /* Sensitivities of CVA_0 by a hand-written adjoint (reverse-mode) sweep. The
  * sampled default indicators have zero pathwise derivative, so the function
  * differentiated is the smooth CVA_0 that the oversimulated average estimates,

@@ -189,6 +189,12 @@ class Simulation:
         nat.check(N_lib().cva_autotune(self._h, int(seed), b, buf, 512, _stream_handle(stream)), "cva_autotune")
         return json.loads(buf.value.decode())
 
+    def set_tiles(self, sim_block: int, price_block: int, inner_paths_per_block: int, lsq_chunk_target: int,
+                  portfolios_per_price_block: int = 1) -> None:
+        """Set the tile shapes directly (see cva_set_tiles), e.g. a saved autotune choice."""
+        nat.check(N_lib().cva_set_tiles(self._h, int(sim_block), int(price_block), int(inner_paths_per_block),
+                                        int(lsq_chunk_target), int(portfolios_per_price_block)), "cva_set_tiles")
+
     def regress_all(self, pf: int = 0, basis: str = "poly2", stream=None, want_coef: bool = True):
         """Least squares at every date 1..n-1 in one grouped launch; returns
         (predictions [n, M] on the device, coefficients [n, m] numpy or None)."""

@@ -572,7 +572,7 @@ cva_status cva_regress_portfolios(cva_sim *sim, int basis, float *pred_dev, doub
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::string, std::array<int, 4>> g_tune_cache;
+std::map<std::string, std::array<int, 5>> g_tune_cache;
 
 float time_once(cudaStream_t st, const std::function<cva_status()> &f, cva_status *err)
 {
@@ -603,7 +603,7 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
     char key[512];
     snprintf(key, sizeof(key), "%s|E%d C%d CS%d G%d P%d n%d S%d M%llu N%u b%d", prop.name, s.E, s.C, s.CS, s.Ginst,
              s.NPF, s.n, s.S, (unsigned long long)s.M, s.N, basis);
-    std::array<int, 4> best = {s.tune_sim_block, s.tune_price_block, s.tune_inner_P, s.tune_lsq_chunks};
+    std::array<int, 5> best = {s.tune_sim_block, s.tune_price_block, s.tune_inner_P, s.tune_lsq_chunks, s.tune_price_pf};
     bool cached = false;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -616,8 +616,10 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
     if (!cached) {
         cva_status err = CVA_OK;
         auto measure = [&](int which, int value) -> float {
-            std::array<int, 4> save = {s.tune_sim_block, s.tune_price_block, s.tune_inner_P, s.tune_lsq_chunks};
-            int *slot[4] = {&s.tune_sim_block, &s.tune_price_block, &s.tune_inner_P, &s.tune_lsq_chunks};
+            std::array<int, 5> save = {s.tune_sim_block, s.tune_price_block, s.tune_inner_P, s.tune_lsq_chunks,
+                                       s.tune_price_pf};
+            int *slot[5] = {&s.tune_sim_block, &s.tune_price_block, &s.tune_inner_P, &s.tune_lsq_chunks,
+                            &s.tune_price_pf};
             *slot[which] = value;
             auto run = [&]() -> cva_status {
                 if (which == 3) return cva_regress_portfolios(sim, basis, nullptr, nullptr, cs);
@@ -631,13 +633,18 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
             s.tune_price_block = save[1];
             s.tune_inner_P = save[2];
             s.tune_lsq_chunks = save[3];
+            s.tune_price_pf = save[4];
             return err == CVA_OK ? t : 1e30f;
         };
-        const std::vector<std::vector<int>> cand = {{64, 128}, {128, 256}, {2, 4, 8}, {1216, 2432, 4864, 9728}};
+        // portfolios per pricing block: the divisors of n_pf among 1, 2, 3
+        std::vector<int> ppf = {1};
+        for (int v : {2, 3})
+            if (s.NPF % v == 0) ppf.push_back(v);
+        const std::vector<std::vector<int>> cand = {{64, 128}, {128, 256}, {2, 4, 8}, {1216, 2432, 4864, 9728}, ppf};
         // the first pass needs valid outputs of the earlier kernels: simulate once
         cva_status r = cva_simulate(sim, seed, 0, stream);
         if (r != CVA_OK) return r;
-        for (int w = 0; w < 4; ++w) {
+        for (int w = 0; w < 5; ++w) {
             float tb = 1e30f;
             for (int v : cand[w]) {
                 const float t = measure(w, v);
@@ -646,7 +653,8 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
                     best[w] = v;
                 }
             }
-            int *slot[4] = {&s.tune_sim_block, &s.tune_price_block, &s.tune_inner_P, &s.tune_lsq_chunks};
+            int *slot[5] = {&s.tune_sim_block, &s.tune_price_block, &s.tune_inner_P, &s.tune_lsq_chunks,
+                            &s.tune_price_pf};
             *slot[w] = best[w];
         }
         if (err != CVA_OK) return err;
@@ -657,10 +665,33 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
     s.tune_price_block = best[1];
     s.tune_inner_P = best[2];
     s.tune_lsq_chunks = best[3];
+    s.tune_price_pf = best[4];
     if (report && report_len)
         snprintf(report, report_len, "{\"sim_block\": %d, \"price_block\": %d, \"inner_paths_per_block\": %d, "
-                                     "\"lsq_chunk_target\": %d, \"cached\": %s}",
-                 best[0], best[1], best[2], best[3], cached ? "true" : "false");
+                                     "\"lsq_chunk_target\": %d, \"portfolios_per_price_block\": %d, \"cached\": %s}",
+                 best[0], best[1], best[2], best[3], best[4], cached ? "true" : "false");
+    return CVA_OK;
+}
+
+cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner_paths_per_block,
+                         int lsq_chunk_target, int portfolios_per_price_block)
+{
+    if (!sim) return fail(CVA_EINVAL, "sim is NULL");
+    Sim &s = *reinterpret_cast<Sim *>(sim);
+    if (sim_block != 64 && sim_block != 128) return fail(CVA_EINVAL, "sim_block must be 64 or 128");
+    if (price_block != 128 && price_block != 256) return fail(CVA_EINVAL, "price_block must be 128 or 256");
+    if (inner_paths_per_block != 0 && inner_paths_per_block != 2 && inner_paths_per_block != 4 &&
+        inner_paths_per_block != 8)
+        return fail(CVA_EINVAL, "inner_paths_per_block must be 0, 2, 4 or 8");
+    if (lsq_chunk_target < 152 || lsq_chunk_target > (1 << 20))
+        return fail(CVA_EINVAL, "lsq_chunk_target must lie in [152, 2^20]");
+    if (portfolios_per_price_block < 1 || portfolios_per_price_block > 3 || s.NPF % portfolios_per_price_block != 0)
+        return fail(CVA_EINVAL, "portfolios_per_price_block must be 1, 2 or 3 and divide the number of portfolios");
+    s.tune_sim_block = sim_block;
+    s.tune_price_block = price_block;
+    s.tune_inner_P = inner_paths_per_block;
+    s.tune_lsq_chunks = lsq_chunk_target;
+    s.tune_price_pf = portfolios_per_price_block;
     return CVA_OK;
 }
 

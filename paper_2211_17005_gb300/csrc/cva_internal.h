@@ -86,6 +86,7 @@ struct Sim {
     unsigned char *d_const_img = nullptr;
     // tile shapes, set by cva_autotune
     int tune_sim_block = 128, tune_price_block = 256, tune_inner_P = 0, tune_lsq_chunks = 2432;
+    int tune_price_pf = 1;         // portfolios per pricing block (1, 2 or 3, dividing n_pf)
     // scratch of the portfolio-grouped regression, owned by the simulation
     double *d_lsq = nullptr;
     size_t lsq_cap = 0;

@@ -160,23 +160,26 @@ __global__ void __launch_bounds__(128) sim_kernel(OuterArgs a)
     }
 }
 
-// One portfolio per block (blockIdx.z): a block's date-bucketed weights (C E G
-// pairs) stay within the constant cache whatever the number of portfolios.
-template <int E, int C, int CS, int G>
+// NPB portfolios per block (blockIdx.z picks the group): the bond prices of a
+// (path, date) serve the group's portfolios, and the group's date-bucketed weights
+// (NPB C E G pairs) must stay within the constant cache; the autotuner chooses NPB.
+template <int E, int C, int CS, int G, int NPB>
 __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
 {
     constexpr int F = 2 * E - 1 + CS;
     const uint32_t kl = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, pf = blockIdx.z;
+    const int j = blockIdx.y, pf0 = blockIdx.z * NPB;
     if (kl >= a.M) return;
     const size_t M = a.M;
     const int n = c_sim.n, ppp = c_sim.ppp;
     if (j == 0) {   // no default at t_0: exposures of date 0 are never used
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            a.expo[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
-            if (a.mtm) a.mtm[((size_t)(pf * (n + 1)) * C + c) * M + kl] = 0.f;
-        }
+        for (int pb = 0; pb < NPB; ++pb)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                a.expo[((size_t)((pf0 + pb) * (n + 1)) * C + c) * M + kl] = 0.f;
+                if (a.mtm) a.mtm[((size_t)((pf0 + pb) * (n + 1)) * C + c) * M + kl] = 0.f;
+            }
         return;
     }
     const int p = __ldg(a.date_p + j);          // t_j in (p delta, (p+1) delta]
@@ -185,9 +188,11 @@ __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
     const float2 *fx = a.fix + (size_t)p * E;
     const float beta = expf(-__ldg(a.disc + (size_t)j * M + kl));
 
-    float mt[C];
+    float mt[NPB][C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) mt[c] = 0.f;
+    for (int pb = 0; pb < NPB; ++pb)
+#pragma unroll
+        for (int c = 0; c < C; ++c) mt[pb][c] = 0.f;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const float re = __ldg(fe + (size_t)e * M);
@@ -221,22 +226,26 @@ __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
         }
         const float chi = (e == 0) ? 1.f : expf(__ldg(fe + (size_t)(E - 1 + (e > 0 ? e : 1)) * M));
 #pragma unroll
+        for (int pb = 0; pb < NPB; ++pb)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int base = (((pf0 + pb) * C + c) * E + e) * G;
+                float acc = 0.f;
+#pragma unroll
+                for (int h = 0; h < G; ++h) acc = fmaf(c_w.wA[base + h], D[h], acc);
+#pragma unroll
+                for (int g = 0; g < G; ++g) acc = fmaf(-c_w.wK[base + g], Z[g], acc);
+                mt[pb][c] = fmaf(chi, acc, mt[pb][c]);
+            }
+    }
+#pragma unroll
+    for (int pb = 0; pb < NPB; ++pb)
+#pragma unroll
         for (int c = 0; c < C; ++c) {
-            const int base = ((pf * C + c) * E + e) * G;
-            float acc = 0.f;
-#pragma unroll
-            for (int h = 0; h < G; ++h) acc = fmaf(c_w.wA[base + h], D[h], acc);
-#pragma unroll
-            for (int g = 0; g < G; ++g) acc = fmaf(-c_w.wK[base + g], Z[g], acc);
-            mt[c] = fmaf(chi, acc, mt[c]);
+            const size_t o = ((size_t)((pf0 + pb) * (n + 1) + j) * C + c) * M + kl;
+            a.expo[o] = c_sim.lgd[c] * beta * fmaxf(mt[pb][c], 0.f);
+            if (a.mtm) a.mtm[o] = mt[pb][c];
         }
-    }
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const size_t o = ((size_t)(pf * (n + 1) + j) * C + c) * M + kl;
-        a.expo[o] = c_sim.lgd[c] * beta * fmaxf(mt[c], 0.f);
-        if (a.mtm) a.mtm[o] = mt[c];
-    }
 }
 
 }  // namespace
@@ -312,7 +321,15 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     sim_kernel<E, C, CS><<<(args.M + sb - 1) / sb, sb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
-    price_kernel<E, C, CS, G><<<dim3((args.M + pb - 1) / pb, (unsigned)s.n + 1u, (unsigned)NPF), pb, 0, st>>>(args);
+    const int ppb = ((s.tune_price_pf == 2 || s.tune_price_pf == 3) && NPF % s.tune_price_pf == 0) ? s.tune_price_pf : 1;
+    const dim3 pgrid((args.M + pb - 1) / pb, (unsigned)s.n + 1u, (unsigned)(NPF / ppb));
+    if constexpr (NPF % 3 == 0) {
+        if (ppb == 3) price_kernel<E, C, CS, G, 3><<<pgrid, pb, 0, st>>>(args);
+    }
+    if constexpr (NPF % 2 == 0) {
+        if (ppb == 2) price_kernel<E, C, CS, G, 2><<<pgrid, pb, 0, st>>>(args);
+    }
+    if (ppb == 1) price_kernel<E, C, CS, G, 1><<<pgrid, pb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     if (!capturing) CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
     return CVA_OK;

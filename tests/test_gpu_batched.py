@@ -81,6 +81,7 @@ def test_autotune_keeps_results(api):
     choice = sim.autotune(wl.seed, "linear")
     assert choice["sim_block"] in (64, 128) and choice["price_block"] in (128, 256)
     assert choice["inner_paths_per_block"] in (2, 4, 8)
+    assert choice["portfolios_per_price_block"] in (1, 2, 3)
     sim.run(wl.seed)
     p, _ = sim.regress_portfolios("linear")
     torch.cuda.synchronize()
@@ -89,4 +90,23 @@ def test_autotune_keeps_results(api):
     assert float((p - ref_p).abs().max()) <= 1e-5 * scale
     again = sim.autotune(wl.seed, "linear")
     assert again["cached"] is True
+    sim.close()
+
+
+@pytest.mark.parametrize("ppb", [1, 2, 3])
+def test_pricing_portfolio_groups_bit_identical(api, ppb):
+    """Pricing 1, 2 or 3 portfolios per block changes no exposure, MtM or target bit."""
+    wl = W.make("batched", M=8192, N=32, n_steps=20)
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N)
+    sim.set_tiles(128, 256, 0, 2432, 1)
+    sim.run(wl.seed)
+    torch.cuda.synchronize()
+    ref_t = sim.targets().clone()
+    sim.set_tiles(64, 128, 4, 1216, ppb)
+    sim.targets().zero_()
+    sim.run(wl.seed)
+    torch.cuda.synchronize()
+    assert torch.equal(sim.targets(), ref_t)
+    with pytest.raises(RuntimeError):
+        sim.set_tiles(64, 128, 4, 1216, 4)          # not one of 1, 2, 3
     sim.close()
