@@ -11,6 +11,10 @@ path never imports it. It shares no code with the CUDA library.
   QR (numpy), on the standardised feature map.
 * ``twin_l2`` is the twin Monte Carlo estimator of eq. (e:val1) (Sec. ss:twin), and
   ``simulate(..., copy=(date, b))`` runs twin copy b branching at a pricing date.
+* ``alive_lsq`` is the least-squares learner on the hierarchically simulated sample
+  (X_i^{k,l}, Y_i^k, xi_i^{k,l}) of size M N (Sec. "Learning on Hierarchically
+  Simulated Paths"; X the default indicators, Y the market state, Sec. 4.1), with
+  the M N design matrix written out row by row.
 """
 from __future__ import annotations
 
@@ -295,6 +299,59 @@ def oversim_stats(o: Dict[str, np.ndarray], recovery: np.ndarray, pred: np.ndarr
         m12 = (g[0] * g[1]).mean()
         Q[i], R[i] = m2 - m12, m12 - m1 * m1
     return Q, R
+
+
+def draw_targets(o: Dict[str, np.ndarray], recovery: np.ndarray, date: int) -> np.ndarray:
+    """The per-draw target xi_i^{k,l} at pricing date i (eq. (eq:CVA_portfolio) on one
+    inner draw): e^{I0_i} sum_c (1 - R_c) e^{-I0_j} MtM_c(j)^+ with j = idx_c^{k,l},
+    for the counterparties whose default step j satisfies i < j <= n. Oracle
+    outputs `idx` [M, N, C], `mtm`, `I0`; returns [M, N]."""
+    idx, mtm, I0 = o["idx"].astype(np.int64), o["mtm"], o["I0"]
+    n1, C, M = mtm.shape
+    n = n1 - 1
+    V = (1.0 - np.asarray(recovery))[None, :, None] * np.exp(-I0)[:, None, :] * np.maximum(mtm, 0.0)
+    kk = np.arange(M)[:, None, None]
+    cc = np.arange(C)[None, None, :]
+    v = V[np.minimum(idx, n), cc, kk]                          # [M, N, C]
+    live = (idx > date) & (idx <= n)
+    return np.exp(I0[date])[:, None] * np.sum(np.where(live, v, 0.0), axis=2)
+
+
+def default_indicators(o: Dict[str, np.ndarray], date: int) -> np.ndarray:
+    """X_i^{k,l}: 1 where counterparty c has defaulted by t_i (its default step is
+    at most i), else 0; returns [M, N, C]."""
+    return (o["idx"].astype(np.int64) <= date).astype(np.float64)
+
+
+def alive_lsq(o: Dict[str, np.ndarray], recovery: np.ndarray, date: int, with_defaults: bool = True):
+    """Least squares of the per-draw target on (X_i, Y_i) over the hierarchically
+    simulated sample of size M N: one row per (outer path k, inner draw l) with
+    Y^{k,l} = Y^k, the basis [1, z_1..z_F, X_1..X_C] (z the standardised state of
+    `linear_features`), solved by Householder QR. Columns other than the intercept
+    that are constant over the M N rows (a counterparty with no default by t_i, or
+    a state component with no spread) are left out and get coefficient 0.
+    with_defaults=False leaves out every X column (the Y-only learner).
+
+    Returns a dict: w [1 + F + C] (the basis above), alive [M] = the fitted value
+    at X = 0 (every counterparty alive), fitted [M, N], dropped (list of column
+    indices left out)."""
+    Y = o["features"][date]                                   # [F, M]
+    F, M = Y.shape
+    xi = draw_targets(o, recovery, date)                      # [M, N]
+    N = xi.shape[1]
+    X = default_indicators(o, date)                           # [M, N, C]
+    C = X.shape[2]
+    phiY = linear_features(Y)                                 # [M, 1 + F]
+    rows = np.concatenate([np.repeat(phiY[:, None, :], N, axis=1), X], axis=2).reshape(M * N, 1 + F + C)
+    if not with_defaults:
+        rows[:, 1 + F:] = 0.0
+    keep = [0] + [j for j in range(1, 1 + F + C) if np.ptp(rows[:, j]) > 0.0]
+    w_keep, _ = lsq(rows[:, keep], xi.reshape(M * N))
+    w = np.zeros(1 + F + C)
+    w[keep] = w_keep
+    fitted = (rows @ w).reshape(M, N)
+    return {"w": w, "alive": phiY @ w[:1 + F], "fitted": fitted,
+            "dropped": [j for j in range(1, 1 + F + C) if j not in keep]}
 
 
 def twin_l2(phi: np.ndarray, xi1: np.ndarray, xi2: np.ndarray):
