@@ -247,6 +247,32 @@ CVA_API cva_status cva_regress_all(const cva_sim *sim, int pf, int basis, float 
 CVA_API cva_status cva_regress_portfolios(cva_sim *sim, int basis, float *pred_dev, double *coef_host,
                                           void *stream);
 
+/* Least squares on the hierarchically simulated sample (Sec. "Learning on
+ * Hierarchically Simulated Paths"), portfolio pf, every date i = 1..n-1: one row
+ * per (outer path k, inner draw l), the features (X_i^{k,l}, Y_i^k) with X_i the
+ * default indicators 1{tau_c <= t_i} of the C counterparties and Y_i the state
+ * (Sec. 4.1), the per-draw target of eq. (eq:CVA_portfolio)
+ *   xi_i^{k,l} = beta_i^{-1} sum_c (1-R_c) beta_j MtM_c(t_j)^+ 1{i < j <= n}, j = default step of c in draw l,
+ * and the basis [1, Y_i - Y_i^0, X_i] (Y_i^0: path 0's state):
+ *   w_i = argmin_w sum_{k,l} (xi_i^{k,l} - w^T [1, Y_i^k - Y_i^0, X_i^{k,l}])^2.
+ * The M N rows are not formed: per path, exact integer counts over the N draws
+ * (defaults of c, joint defaults of c and d) and the sums of the target over the
+ * draws where c has defaulted give the normal equations (FP64 accumulation), solved
+ * by a Jacobi-scaled Cholesky factorisation in FP64; a column whose pivot vanishes
+ * (no default of c by t_i in the whole sample) is dropped, with coefficient 0.
+ * Needs a simulation created with CVA_KEEP_DEFAULTS after cva_simulate; C must be 2
+ * or 8, 1 + F + C <= 40 and N * C <= 32768 (else CVA_ENOTSUP).
+ * pred_dev: float [n][M] (nullable; date 0 untouched) receives the fit at X_i = 0
+ * (every counterparty alive). coef_host: double [n][1+F+C] (nullable; date 0
+ * untouched) receives w_i in the raw basis [1, Y_i, X_i]. dropped_host: int [n]
+ * (nullable) receives the number of dropped columns per date (0 at date 0). The
+ * scratch (n (2C + C(C-1)/2) M floats and the Gram partials) belongs to the
+ * simulation: the first call allocates it, so make one call before capturing this
+ * one in a CUDA graph. Synchronises `stream` only when coef_host or dropped_host is
+ * given. */
+CVA_API cva_status cva_regress_alive(cva_sim *sim, int pf, float *pred_dev, double *coef_host, int *dropped_host,
+                                     void *stream);
+
 /* Tile shapes of a simulation chosen by measurement: threads per block of the
  * path-simulation and pricing kernels, outer paths per block of the
  * inner-default kernel, and the number of blocks of the grouped regression

@@ -69,6 +69,8 @@ SIGNATURES = {
     "cva_regress_portfolios": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_void_p]),
     "cva_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
                                     ctypes.c_void_p]),
+    "cva_regress_alive": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, _dp,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "cva_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int]),
     "cva_grad_cva0": (ctypes.c_int, [ctypes.POINTER(ModelDesc), ctypes.POINTER(PortfolioDesc),

@@ -181,6 +181,24 @@ class Simulation:
                                                  _stream_handle(stream)), "cva_regress_portfolios")
         return pred, coef
 
+    def regress_alive(self, pf: int = 0, pred: Optional[torch.Tensor] = None, stream=None,
+                      want_coef: bool = True):
+        """Least squares on (default indicators X_i, state Y_i) over the M N
+        hierarchical sample at every date 1..n-1 (see cva_regress_alive); the
+        simulation must keep its default steps (keep_defaults=True). Returns
+        (the fit at X = 0 [n, M] on the device, coefficients [n, 1+F+C] in the raw
+        basis [1, Y, X] or None, dropped columns per date [n] or None)."""
+        if pred is None:
+            pred = torch.zeros((self.n, self.M), dtype=torch.float32, device=self.device)
+        m = self.F + 1 + self.C
+        coef = np.zeros((self.n, m)) if want_coef else None
+        dropped = np.zeros(self.n, dtype=np.int32) if want_coef else None
+        cp = coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_coef else None
+        dp = dropped.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if want_coef else None
+        nat.check(N_lib().cva_regress_alive(self._h, int(pf), ctypes.c_void_p(pred.data_ptr()), cp, dp,
+                                            _stream_handle(stream)), "cva_regress_alive")
+        return pred, coef, dropped
+
     def autotune(self, seed: int = 1, basis: str = "linear", stream=None) -> dict:
         """Pick the tile shapes by measurement (see cva_autotune); returns the choice."""
         import json

@@ -100,6 +100,8 @@ void free_sim(Sim *s)
     cudaFree(s->d_idx);
     cudaFree(s->d_const_img);
     cudaFree(s->d_lsq);
+    cudaFree(s->d_alive_stats);
+    cudaFree(s->d_alive);
     for (cudaEvent_t &e : s->ev)
         if (e) cudaEventDestroy(e);
     delete s;
@@ -671,6 +673,14 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
                                      "\"lsq_chunk_target\": %d, \"portfolios_per_price_block\": %d, \"cached\": %s}",
                  best[0], best[1], best[2], best[3], best[4], cached ? "true" : "false");
     return CVA_OK;
+}
+
+cva_status cva_regress_alive(cva_sim *sim, int pf, float *pred_dev, double *coef_host, int *dropped_host,
+                             void *stream)
+{
+    if (!sim) return fail(CVA_EINVAL, "sim is NULL");
+    return alive_regress(*reinterpret_cast<Sim *>(sim), pf, pred_dev, coef_host, dropped_host,
+                         reinterpret_cast<cudaStream_t>(stream));
 }
 
 cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner_paths_per_block,

@@ -90,6 +90,11 @@ struct Sim {
     // scratch of the portfolio-grouped regression, owned by the simulation
     double *d_lsq = nullptr;
     size_t lsq_cap = 0;
+    // scratch of the regression on (default indicators, state), owned by the simulation
+    float *d_alive_stats = nullptr;   // [n][2C + C(C-1)/2][M] per-path sums over the inner draws
+    size_t alive_stats_cap = 0;
+    double *d_alive = nullptr;        // Gram partials, coefficients, status
+    size_t alive_cap = 0;
     // profiling events: before the simulation kernel, after it, after the pricing
     // kernel, after the inner-default kernel
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -176,6 +181,10 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
                               int n_dates, int F, uint64_t M, int n_batches, int epochs, float lr, int max_steps,
                               float *params_dev, float *pred0, float *grad_out_dev, float *loss_out_dev,
                               unsigned *count, int *err, cudaStream_t st);
+
+// Least squares on (default indicators, state) over the M N hierarchical sample
+// of portfolio pf at dates 1..n-1 (alive.cu).
+cva_status alive_regress(Sim &s, int pf, float *pred_dev, double *coef_host, int *dropped_host, cudaStream_t st);
 
 // CVA_0 reduction (reduce.cu).
 cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);
