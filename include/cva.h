@@ -261,13 +261,14 @@ CVA_API cva_status cva_regress_portfolios(cva_sim *sim, int basis, float *pred_d
  * by a Jacobi-scaled Cholesky factorisation in FP64; a column whose pivot vanishes
  * (no default of c by t_i in the whole sample) is dropped, with coefficient 0.
  * Needs a simulation created with CVA_KEEP_DEFAULTS after cva_simulate; C must be 2
- * or 8, 1 + F + C <= 40 and N * C <= 32768 (else CVA_ENOTSUP).
+ * or 8, 1 + F + C <= 40 and N (5C + 6) bytes of draw tables must fit 160 KB of shared
+ * memory (N <= 3400 at C = 8; else CVA_ENOTSUP).
  * pred_dev: float [n][M] (nullable; date 0 untouched) receives the fit at X_i = 0
  * (every counterparty alive). coef_host: double [n][1+F+C] (nullable; date 0
  * untouched) receives w_i in the raw basis [1, Y_i, X_i]. dropped_host: int [n]
  * (nullable) receives the number of dropped columns per date (0 at date 0). The
- * scratch (n (2C + C(C-1)/2) M floats and the Gram partials) belongs to the
- * simulation: the first call allocates it, so make one call before capturing this
+ * scratch (n C M floats of per-path default counts, the pair and loss sums of each
+ * block of 8 paths, and the Gram partials) belongs to the simulation: the first call allocates it, so make one call before capturing this
  * one in a CUDA graph. Synchronises `stream` only when coef_host or dropped_host is
  * given. */
 CVA_API cva_status cva_regress_alive(cva_sim *sim, int pf, float *pred_dev, double *coef_host, int *dropped_host,
