@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--lsq", action="store_true", help="least-squares regression instead of the workload's MLP")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     p.add_argument("--no-batched", action="store_true", help="skip the 6-portfolio CUDA-graph measurement")
+    p.add_argument("--no-alive", action="store_true",
+                   help="skip the least squares on (default indicators, state) over the M N sample")
     p.add_argument("--no-precision", action="store_true",
                    help="skip the 2^20-path width-128 network measurement")
     p.add_argument("--paths", type=int, default=None,
@@ -501,6 +503,41 @@ def main():
         bsim.close()
         del bpred, graph
 
+    # ---- least squares on (default indicators X, state Y) over the M N hierarchical sample (rank 0) ----
+    alive = None
+    if rank == 0 and not args.no_alive and args.workload in ("paper", "small"):
+        xwl = workload.make(args.workload, M=args.paths)
+        xsim = api.Simulation(xwl.model, xwl.portfolios, xwl.grid, xwl.M, xwl.N, keep_defaults=True)
+        xsim.run(xwl.seed)
+        xpred = torch.zeros((xsim.n, xsim.M), dtype=torch.float32, device="cuda")
+        _, xcoef, xdrop = xsim.regress_alive(0, pred=xpred)          # allocates the scratch
+        torch.cuda.synchronize()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        x0.record(stream)
+        for _ in range(reps):
+            xsim.regress_alive(0, pred=xpred, want_coef=False)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        xms = x0.elapsed_time(x1) / reps
+        xn, xM, xN, xC, xF = xwl.grid.n_steps, xwl.M, xwl.N, xwl.model.C, xwl.model.F
+        # bytes a single pass must move: default steps, exposures, discount integrals,
+        # features and targets of the regressed dates, predictions written
+        xbytes = xM * xN * xC + 4 * xM * ((xn + 1) * (xC + 1) + (xn - 1) * (xF + 2))
+        xgbs = xbytes / (xms / 1e3) / 1e9
+        alive = {"workload": describe(xwl),
+                 "regression": f"least squares on [1, Y ({xF}), X ({xC})] over M N = {xM * xN} rows per date, "
+                               f"{xn - 1} dates, per-path exact draw statistics (no M N design)",
+                 "ms": xms, "rows_per_s": xM * xN * (xn - 1) / (xms / 1e3),
+                 "dropped_columns": int(np.sum(xdrop)),
+                 "roofline": {"bound": "hbm", "kernel": "cva_regress_alive (4 kernels)", "achieved": xgbs,
+                              "peak": hbm, "unit": "GB/s", "frac": xgbs / hbm, "traffic": None,
+                              "algorithmic_bytes": int(xbytes),
+                              "note": "latency-bound per-path event walk, not HBM-bound"}}
+        xsim.close()
+        del xpred
+
     # ---- the 2^20-path workload with the width-128 network (rank 0) ----
     precision = None
     if rank == 0 and not args.no_precision and args.workload != "precision":
@@ -560,7 +597,7 @@ def main():
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
                "mlp_roofline": mlp_roof, "twin_validation": twin, "oversimulation": oversim,
                "nested_validation": nested,
-               "adjoint_forward": adj, "batched": batched,
+               "adjoint_forward": adj, "batched": batched, "alive_regression": alive,
                "precision": precision,
                "cpu_baseline": cpu,
                "clocks": clk,
