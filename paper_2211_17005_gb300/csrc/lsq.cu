@@ -4,7 +4,8 @@
 // 0's state is accumulated from FP32 products in FP32 runs of 512 rows per thread,
 // then in FP64 (per thread, per block, then across blocks in a fixed order), and
 // solved by a Jacobi-scaled Cholesky factorisation in FP64. The pass over the
-// features and targets is the only HBM traffic: every byte is read once.
+// features and targets is the only HBM traffic: every byte is read once. For the
+// linear basis the tiles are copied by cp.async into two buffers (lsq_gram_async).
 #include <math.h>
 
 #include <mutex>
@@ -134,6 +135,139 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram(LsqArgs a)
         for (int q = 0; q < NRG; ++q) s += red[(size_t)q * NUT * 16 + e];
         out[e] = s;
     }
+}
+
+__device__ __forceinline__ void cp_async4_zfill(uint32_t saddr, const void *g, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr), "l"(g), "r"(valid ? 4 : 0) : "memory");
+}
+
+// lsq_gram for the linear basis [1, Y - Y^0] with the same arithmetic (the same rows
+// per thread in the same order, the same flushes), its tiles copied by cp.async into
+// two buffers so that the copies of the next tile run during the products of this
+// one; the state columns are centred on path 0 in place once a tile has landed.
+template <int MP, int TR>
+__global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
+{
+    constexpr int NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2, RS = MP + 4, TS = TR * RS;
+    constexpr int NRG = kGramThreads / NUT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *tiles = reinterpret_cast<float *>(smem);          // [2][TR][RS]
+    const int g = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    const float *feat = a.feat0 + (size_t)g * a.feat_stride;
+    const float *targ = a.targ0 + (size_t)g * a.targ_stride;
+    const uint32_t r_begin = (uint32_t)chunk * a.rows_per_chunk;
+    const uint32_t r_end = min(a.M, r_begin + a.rows_per_chunk);
+    const int mA = a.m + a.nt, F = a.F, nload = a.F + a.nt;   // copied columns 1..F+nt: state, targets
+    const int b = tid % NUT, rg = tid / NUT;
+    int bi = 0, bj = 0;
+    {
+        int t = b;
+        for (int i = 0; i < NBLK; ++i) {
+            if (t < NBLK - i) {
+                bi = i;
+                bj = i + t;
+                break;
+            }
+            t -= NBLK - i;
+        }
+    }
+    __shared__ float c0[40];
+    for (int f = tid; f < F; f += kGramThreads) c0[f] = __ldg(feat + (size_t)f * a.M);
+    for (int e = tid; e < 2 * TR; e += kGramThreads)       // padding columns stay zero
+        for (int c = mA; c < MP; ++c) tiles[e * RS + c] = 0.f;
+    __syncthreads();
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tiles);
+    auto issue = [&](uint32_t r0, int buf) {
+        for (int e = tid; e < nload * TR; e += kGramThreads) {
+            const int lc = e / TR, r = e % TR;
+            const uint32_t k = r0 + r;
+            const bool ok = k < r_end;
+            const float *src = lc < F ? feat + (size_t)lc * a.M : targ + (size_t)(lc - F) * a.targ_tstride;
+            cp_async4_zfill(sbase + (uint32_t)(buf * TS + r * RS + 1 + lc) * 4u, src + (ok ? k : 0u), ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    double dacc[16];
+    float acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        dacc[i] = 0.0;
+        acc[i] = 0.f;
+    }
+    int since_flush = 0;
+    if (r_begin < r_end) issue(r_begin, 0);
+    int buf = 0;
+    for (uint32_t r0 = r_begin; r0 < r_end; r0 += TR, buf ^= 1) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();                          // tile r0 is in buffer buf; buf ^ 1 is free
+        float *tile = tiles + buf * TS;
+        for (int e = tid; e < (F + 1) * TR; e += kGramThreads) {
+            const int col = e / TR, r = e % TR;
+            const bool ok = r0 + r < r_end;
+            float *v = tile + r * RS + col;
+            if (col == 0) *v = ok ? 1.f : 0.f;
+            else if (ok) *v -= c0[col - 1];
+        }
+        __syncthreads();
+        if (r0 + TR < r_end) issue(r0 + TR, buf ^ 1);
+        if (rg < NRG) {
+            for (int r = rg; r < TR; r += NRG) {
+                const float4 x = *reinterpret_cast<const float4 *>(tile + r * RS + 4 * bi);
+                const float4 y = *reinterpret_cast<const float4 *>(tile + r * RS + 4 * bj);
+                const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(xv[u], yv[v], acc[u * 4 + v]);
+                if (++since_flush == 512) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        dacc[i] += (double)acc[i];
+                        acc[i] = 0.f;
+                    }
+                    since_flush = 0;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) dacc[i] += (double)acc[i];
+    __syncthreads();
+    double *red = reinterpret_cast<double *>(smem);        // [NRG][NUT*16]
+    if (rg < NRG)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) red[(size_t)rg * NUT * 16 + b * 16 + i] = dacc[i];
+    __syncthreads();
+    double *out = a.part + ((size_t)g * a.chunks + chunk) * NUT * 16;
+    for (int e = tid; e < NUT * 16; e += kGramThreads) {
+        double s = 0.0;
+        for (int q = 0; q < NRG; ++q) s += red[(size_t)q * NUT * 16 + e];
+        out[e] = s;
+    }
+}
+
+// Launch the Gram kernel of width MP and tile TR: the cp.async form for the linear
+// basis, the plain form (per-element basis values) for [1, r, r^2]. The dynamic shared
+// memory limit is raised outside stream capture (a call before capture sets it).
+template <int MP, int TR>
+cva_status launch_gram(const LsqArgs &a, dim3 grid, cudaStream_t st)
+{
+    constexpr int NUT = (MP / 4) * (MP / 4 + 1) / 2, NRG = kGramThreads / NUT;
+    if (a.basis == CVA_BASIS_LINEAR) {
+        const size_t tiles = 2 * (size_t)TR * (MP + 4) * sizeof(float), red = (size_t)NRG * NUT * 16 * sizeof(double);
+        const size_t smem = tiles > red ? tiles : red;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CVA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+        if (cap == cudaStreamCaptureStatusNone)
+            CVA_CUDA_TRY(cudaFuncSetAttribute(lsq_gram_async<MP, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        lsq_gram_async<MP, TR><<<grid, kGramThreads, smem, st>>>(a);
+    } else {
+        lsq_gram<MP, TR><<<grid, kGramThreads, (size_t)TR * (MP + 4) * sizeof(float), st>>>(a);
+    }
+    CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
 }
 
 template <int MP>
@@ -327,13 +461,14 @@ cva_status lsq_launch(const LsqJob &j, double *scratch, size_t scratch_cap, doub
     a.coef_raw = a.coef + (size_t)j.groups * j.nt * m;
     a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)j.groups * j.nt * m);
     const dim3 ggrid((unsigned)chunks, (unsigned)j.groups);
+    cva_status gr;
     switch (MP) {
-    case 4: lsq_gram<4, 1024><<<ggrid, kGramThreads, (size_t)1024 * 8 * sizeof(float), st>>>(a); break;
-    case 12: lsq_gram<12, 512><<<ggrid, kGramThreads, (size_t)512 * 16 * sizeof(float), st>>>(a); break;
-    case 32: lsq_gram<32, 256><<<ggrid, kGramThreads, (size_t)256 * 36 * sizeof(float), st>>>(a); break;
-    default: lsq_gram<40, 256><<<ggrid, kGramThreads, (size_t)256 * 44 * sizeof(float), st>>>(a); break;
+    case 4: gr = launch_gram<4, 1024>(a, ggrid, st); break;
+    case 12: gr = launch_gram<12, 512>(a, ggrid, st); break;
+    case 32: gr = launch_gram<32, 256>(a, ggrid, st); break;
+    default: gr = launch_gram<40, 256>(a, ggrid, st); break;
     }
-    CVA_CUDA_TRY(cudaGetLastError());
+    if (gr != CVA_OK) return gr;
     switch (MP) {
     case 4: lsq_solve<4><<<j.groups, 256, 0, st>>>(a); break;
     case 12: lsq_solve<12><<<j.groups, 256, 0, st>>>(a); break;
@@ -509,14 +644,12 @@ cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups
 
     const dim3 ggrid((unsigned)chunks, (unsigned)groups);
     if (MP == 4) {
-        constexpr int TR = 1024;
-        lsq_gram<4, TR><<<ggrid, kGramThreads, (size_t)TR * 8 * sizeof(float), st>>>(a);
-        CVA_CUDA_TRY(cudaGetLastError());
+        cva_status gr = launch_gram<4, 1024>(a, ggrid, st);
+        if (gr != CVA_OK) return gr;
         lsq_solve<4><<<groups, 256, 0, st>>>(a);
     } else {
-        constexpr int TR = 256;
-        lsq_gram<32, TR><<<ggrid, kGramThreads, (size_t)TR * 36 * sizeof(float), st>>>(a);
-        CVA_CUDA_TRY(cudaGetLastError());
+        cva_status gr = launch_gram<32, 256>(a, ggrid, st);
+        if (gr != CVA_OK) return gr;
         lsq_solve<32><<<groups, 256, 0, st>>>(a);
     }
     CVA_CUDA_TRY(cudaGetLastError());
