@@ -276,6 +276,8 @@ __global__ void __launch_bounds__(256) lsq_solve(LsqArgs a)
     constexpr int NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2;
     __shared__ double blocks[NUT * 16];
     __shared__ double A[MP * MP];
+    __shared__ double sc[MP];
+    __shared__ int drop[MP];
     const int g = blockIdx.x, tid = threadIdx.x, m = a.m, mA = m + a.nt;
     for (int e = tid; e < NUT * 16; e += blockDim.x) {
         double s = 0.0;
@@ -284,79 +286,92 @@ __global__ void __launch_bounds__(256) lsq_solve(LsqArgs a)
         blocks[e] = s;
     }
     __syncthreads();
-    if (tid != 0) return;
-    // unpack upper-triangular 4x4 blocks into the dense augmented matrix
-    int b = 0;
-    for (int bi = 0; bi < NBLK; ++bi)
-        for (int bj = bi; bj < NBLK; ++bj, ++b)
-            for (int u = 0; u < 4; ++u)
-                for (int v = 0; v < 4; ++v) {
-                    const int i = 4 * bi + u, j = 4 * bj + v;
-                    if (i < mA && j < mA) {
-                        A[i * MP + j] = blocks[b * 16 + u * 4 + v];
-                        A[j * MP + i] = blocks[b * 16 + u * 4 + v];
-                    }
-                }
-    // Jacobi scaling, Cholesky of the scaled normal matrix, rank-deficient columns dropped
-    double sc[MP], L[MP * MP], y[MP];
-    bool drop[MP];
-    for (int i = 0; i < m; ++i) {
-        const double d = A[i * MP + i];
-        drop[i] = !(d > 0.0);
-        sc[i] = drop[i] ? 0.0 : 1.0 / sqrt(d);
+    // unpack the upper-triangular 4x4 blocks into the dense augmented matrix
+    for (int e = tid; e < NUT * 16; e += blockDim.x) {
+        int t = e / 16, bi = 0;
+        while (t >= NBLK - bi) {
+            t -= NBLK - bi;
+            ++bi;
+        }
+        const int bj = bi + t, i = 4 * bi + (e % 16) / 4, j = 4 * bj + e % 4;
+        if (i < mA && j < mA) {
+            A[i * MP + j] = blocks[e];
+            A[j * MP + i] = blocks[e];
+        }
     }
-    int dropped = 0;
-    for (int i = 0; i < m; ++i) {
-        for (int j = 0; j <= i; ++j) {
-            double s = (drop[i] || drop[j]) ? 0.0 : A[i * MP + j] * sc[i] * sc[j];
-            for (int p = 0; p < j; ++p) s -= L[i * MP + p] * L[j * MP + p];
-            if (i == j) {
-                if (drop[i] || !(s > 1e-12)) {
-                    drop[i] = true;
-                    L[i * MP + i] = 1.0;
-                    for (int p = 0; p < i; ++p) L[i * MP + p] = 0.0;
-                    ++dropped;
-                } else {
-                    L[i * MP + i] = sqrt(s);
-                }
+    __syncthreads();
+    // Jacobi scaling, then a right-looking Cholesky factorisation of the scaled normal
+    // matrix by the whole block (L overwrites the lower triangle); a column whose pivot
+    // vanishes is dropped: its part of L is zero and its coefficient 0
+    for (int r = tid; r < m; r += blockDim.x) {
+        const double d = A[r * MP + r];
+        drop[r] = !(d > 0.0);
+        sc[r] = drop[r] ? 0.0 : 1.0 / sqrt(d);
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += blockDim.x) {
+        const int r = e / m, c = e % m;
+        if (c <= r) A[r * MP + c] *= sc[r] * sc[c];
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        if (tid == 0) {
+            const double s = A[j * MP + j];
+            if (drop[j] || !(s > 1e-12)) {
+                drop[j] = 1;
+                A[j * MP + j] = 1.0;
             } else {
-                L[i * MP + j] = drop[i] ? 0.0 : s / L[j * MP + j];
+                A[j * MP + j] = sqrt(s);
             }
         }
+        __syncthreads();
+        const double inv = drop[j] ? 0.0 : 1.0 / A[j * MP + j];
+        for (int r = j + 1 + tid; r < m; r += blockDim.x) A[r * MP + j] *= inv;
+        __syncthreads();
+        const int t = m - j - 1;
+        for (int e = tid; e < t * t; e += blockDim.x) {
+            const int r = j + 1 + e / t, c = j + 1 + e % t;
+            if (c <= r) A[r * MP + c] -= A[r * MP + j] * A[c * MP + j];
+        }
+        __syncthreads();
     }
+    if (tid == 0) {
+        int dropped = 0;
+        for (int r = 0; r < m; ++r) dropped += drop[r];
+        a.status[g] = dropped;
+    }
+    // one thread per target column: the two triangular solves and the coefficients
+    if (tid >= a.nt) return;
+    const int t = tid, rhs = m + t;
     const float *feat = a.feat0 + (size_t)g * a.feat_stride;
-    for (int t = 0; t < a.nt; ++t) {
-        const int rhs = m + t;
-        for (int i = 0; i < m; ++i) {           // L y = D^{-1/2} b
-            double s = drop[i] ? 0.0 : A[i * MP + rhs] * sc[i];
-            for (int p = 0; p < i; ++p) s -= L[i * MP + p] * y[p];
-            y[i] = drop[i] ? 0.0 : s / L[i * MP + i];
-        }
-        double w[MP];
-        for (int i = m - 1; i >= 0; --i) {     // L^T z = y, w = D^{-1/2} z
-            double s = y[i];
-            for (int p = i + 1; p < m; ++p) s -= L[p * MP + i] * w[p];
-            w[i] = drop[i] ? 0.0 : s / L[i * MP + i];
-        }
-        for (int i = 0; i < m; ++i) w[i] *= sc[i];
-        double *co = a.coef + ((size_t)g * a.nt + t) * m, *cr = a.coef_raw + ((size_t)g * a.nt + t) * m;
-        for (int i = 0; i < m; ++i) co[i] = w[i];
-        if (a.basis == CVA_BASIS_POLY2) {
-            const double c = (double)feat[0];
-            cr[0] = w[0] - w[1] * c + w[2] * c * c;
-            cr[1] = w[1] - 2.0 * w[2] * c;
-            cr[2] = w[2];
-        } else {
-            double w0 = w[0];
-            for (int f = 0; f < a.F; ++f) {
-                const double c = (double)feat[(size_t)f * a.M];
-                w0 -= w[1 + f] * c;
-                cr[1 + f] = w[1 + f];
-            }
-            cr[0] = w0;
-        }
+    double y[MP], w[MP];
+    for (int i = 0; i < m; ++i) {               // L y = D^{-1/2} b
+        double s = A[i * MP + rhs] * sc[i];
+        for (int p = 0; p < i; ++p) s -= A[i * MP + p] * y[p];
+        y[i] = drop[i] ? 0.0 : s / A[i * MP + i];
     }
-    a.status[g] = dropped;
+    for (int i = m - 1; i >= 0; --i) {         // L^T z = y, w = D^{-1/2} z
+        double s = y[i];
+        for (int p = i + 1; p < m; ++p) s -= A[p * MP + i] * w[p];
+        w[i] = drop[i] ? 0.0 : s / A[i * MP + i];
+    }
+    for (int i = 0; i < m; ++i) w[i] *= sc[i];
+    double *co = a.coef + ((size_t)g * a.nt + t) * m, *cr = a.coef_raw + ((size_t)g * a.nt + t) * m;
+    for (int i = 0; i < m; ++i) co[i] = w[i];
+    if (a.basis == CVA_BASIS_POLY2) {
+        const double c = (double)feat[0];
+        cr[0] = w[0] - w[1] * c + w[2] * c * c;
+        cr[1] = w[1] - 2.0 * w[2] * c;
+        cr[2] = w[2];
+    } else {
+        double w0 = w[0];
+        for (int f = 0; f < a.F; ++f) {
+            const double c = (double)feat[(size_t)f * a.M];
+            w0 -= w[1 + f] * c;
+            cr[1 + f] = w[1 + f];
+        }
+        cr[0] = w0;
+    }
 }
 
 // Predictions of every target column of group g (blockIdx.y) at one path per
