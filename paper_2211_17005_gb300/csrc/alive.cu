@@ -524,11 +524,15 @@ int stats_warps(uint32_t N, int C)
     return 0;
 }
 
+// The dynamic shared memory limits are raised outside stream capture: the first call,
+// which also allocates the scratch, sets them before any capture.
 template <int C>
-cva_status launch_stats(const AliveArgs &a, int W, cudaStream_t st)
+cva_status launch_stats(const AliveArgs &a, int W, bool capturing, cudaStream_t st)
 {
     const size_t smem = stats_smem(W, a.N, C);
-    CVA_CUDA_TRY(cudaFuncSetAttribute(alive_stats_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (!capturing)
+        CVA_CUDA_TRY(cudaFuncSetAttribute(alive_stats_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
     alive_stats_kernel<C><<<a.nblk, 32 * W, smem, st>>>(a);
     CVA_CUDA_TRY(cudaGetLastError());
     return CVA_OK;
@@ -613,12 +617,14 @@ cva_status alive_regress(Sim &s, int pf, float *pred_dev, double *coef_host, int
     a.coef_raw = a.coef + (size_t)groups * m;
     a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)groups * m);
     a.pred = pred_dev;
-    cva_status r = (C == 2) ? launch_stats<2>(a, W, st) : launch_stats<8>(a, W, st);
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    cva_status r = (C == 2) ? launch_stats<2>(a, W, capturing, st) : launch_stats<8>(a, W, capturing, st);
     if (r != CVA_OK) return r;
     const size_t tile_bytes = 2 * (size_t)kTileRows * RS * sizeof(float);
     const size_t red_bytes = (size_t)(kGramThreads / NBLK) * NBLK * 16 * sizeof(double);
     const size_t gsmem = tile_bytes > red_bytes ? tile_bytes : red_bytes;
-    CVA_CUDA_TRY(cudaFuncSetAttribute(alive_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+    if (!capturing)
+        CVA_CUDA_TRY(cudaFuncSetAttribute(alive_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
     alive_gram_kernel<<<dim3((unsigned)chunks, (unsigned)groups), kGramThreads, gsmem, st>>>(a);
     CVA_CUDA_TRY(cudaGetLastError());
     alive_solve_kernel<<<groups, kSolveThreads, 0, st>>>(a);

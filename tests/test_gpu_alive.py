@@ -146,3 +146,44 @@ def test_normal_equations_hold_at_the_paper_shape(api):
         np.testing.assert_allclose(pred[i].double().cpu().numpy(), fit_y.cpu().numpy(), rtol=0,
                                    atol=1e-5 * float(fit_y.abs().max()))
     sim.close()
+
+
+def test_alive_regression_of_one_portfolio_among_several(api):
+    """The 6-portfolio workload: the learner for portfolio 3 reads that portfolio's
+    exposures and targets, and equals the oracle run on that portfolio alone."""
+    wl = W.make("batched", n_steps=20)
+    M, N, pf = 1003, 24, 3
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, M, N, keep_defaults=True)
+    sim.run(wl.seed)
+    pred, coef, dropped = sim.regress_alive(pf)
+    torch.cuda.synchronize()
+    feats = sim.features().cpu().numpy()
+    pred = pred.cpu().numpy()
+    sim.close()
+    one = copy.copy(wl)
+    one.portfolios = [wl.portfolios[pf]]
+    _check_against_oracle(one, M, N, (1, 10, 19), pred, coef, dropped, feats)
+
+
+def test_alive_regression_in_a_cuda_graph(api):
+    """After one call (which allocates the scratch), simulate + the learner captured in
+    a CUDA graph replays to the same bits as the eager calls."""
+    wl = W.make("paper", n_steps=20)
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, 4096, 32, keep_defaults=True)
+    pred = torch.zeros((sim.n, sim.M), dtype=torch.float32, device="cuda")
+    sim.run(wl.seed)
+    sim.regress_alive(0, pred=pred, want_coef=False)
+    torch.cuda.synchronize()
+    ref = pred.clone()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            sim.run(wl.seed, stream=s)
+            sim.regress_alive(0, pred=pred, stream=s, want_coef=False)
+    torch.cuda.synchronize()
+    pred.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(pred, ref)
+    sim.close()
