@@ -413,6 +413,65 @@ __global__ void __launch_bounds__(256) lsq_predict(LsqArgs a)
     }
 }
 
+// The linear-basis predictions of lsq_predict for 4 consecutive paths per thread:
+// 16-byte feature loads and prediction stores, the same FMA order per path (so the
+// same bits). Needs M, the strides and the base addresses to be multiples of 4
+// floats (checked by lsq_predict_launch).
+__global__ void __launch_bounds__(256) lsq_predict4(LsqArgs a)
+{
+    __shared__ float cs[40 * 40];   // [nt][m], m + nt <= 40
+    __shared__ float f0[40];
+    const int g = blockIdx.y, nt = a.nt, m = a.m;
+    const double *co = a.coef + (size_t)g * nt * m;
+    const float *feat = a.feat0 + (size_t)g * a.feat_stride;
+    for (int i = threadIdx.x; i < nt * m; i += blockDim.x) cs[i] = (float)co[i];
+    for (int f = threadIdx.x; f < a.F; f += blockDim.x) f0[f] = __ldg(feat + (size_t)f * a.M);
+    __syncthreads();
+    const uint32_t k = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (k >= a.M) return;
+    float *out = a.pred0 + (size_t)g * a.pred_stride + k;
+    for (int t0 = 0; t0 < nt; t0 += 8) {
+        const int tn = nt - t0 < 8 ? nt - t0 : 8;
+        float4 acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float c = u < tn ? cs[(t0 + u) * m] : 0.f;
+            acc[u] = make_float4(c, c, c, c);
+        }
+#pragma unroll 4
+        for (int f = 0; f < a.F; ++f) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(feat + (size_t)f * a.M + k));
+            const float c0 = f0[f];
+            const float x0 = v.x - c0, x1 = v.y - c0, x2 = v.z - c0, x3 = v.w - c0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < tn) {
+                    const float c = cs[(t0 + u) * m + 1 + f];
+                    acc[u].x = fmaf(c, x0, acc[u].x);
+                    acc[u].y = fmaf(c, x1, acc[u].y);
+                    acc[u].z = fmaf(c, x2, acc[u].z);
+                    acc[u].w = fmaf(c, x3, acc[u].w);
+                }
+        }
+        for (int u = 0; u < tn; ++u) *reinterpret_cast<float4 *>(out + (size_t)(t0 + u) * a.pred_tstride) = acc[u];
+    }
+}
+
+// Predictions of every group: 4 paths per thread where the shapes allow 16-byte
+// accesses, else one path per thread.
+cva_status lsq_predict_launch(const LsqArgs &a, int groups, cudaStream_t st)
+{
+    const bool wide = a.basis == CVA_BASIS_LINEAR && a.M % 4 == 0 && a.feat_stride % 4 == 0 && a.pred_stride % 4 == 0 &&
+                      a.pred_tstride % 4 == 0 && (reinterpret_cast<uintptr_t>(a.feat0) & 15u) == 0 &&
+                      (reinterpret_cast<uintptr_t>(a.pred0) & 15u) == 0;
+    if (wide)
+        lsq_predict4<<<dim3((unsigned)((a.M / 4 + 255) / 256), (unsigned)groups), 256, 0, st>>>(a);
+    else
+        lsq_predict<<<dim3((unsigned)((a.M + 255) / 256), (unsigned)groups), 256, 0, st>>>(a);
+    CVA_CUDA_TRY(cudaGetLastError());
+    return CVA_OK;
+}
+
 // Library-owned scratch for the Gram partials and coefficients, per device.
 // Reuse is ordered by an event: a call waits for the previous call's kernels.
 struct LsqScratch {
@@ -492,8 +551,8 @@ cva_status lsq_launch(const LsqJob &j, double *scratch, size_t scratch_cap, doub
     }
     CVA_CUDA_TRY(cudaGetLastError());
     if (j.pred0) {
-        lsq_predict<<<dim3((unsigned)((j.M + 255) / 256), (unsigned)j.groups), 256, 0, st>>>(a);
-        CVA_CUDA_TRY(cudaGetLastError());
+        cva_status pr = lsq_predict_launch(a, j.groups, st);
+        if (pr != CVA_OK) return pr;
     }
     if (coef_host) {
         std::vector<int> status(j.groups);
@@ -669,8 +728,8 @@ cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups
     }
     CVA_CUDA_TRY(cudaGetLastError());
     if (pred0) {
-        lsq_predict<<<dim3((unsigned)((M + 255) / 256), (unsigned)groups), 256, 0, st>>>(a);
-        CVA_CUDA_TRY(cudaGetLastError());
+        cva_status pr = lsq_predict_launch(a, groups, st);
+        if (pr != CVA_OK) return pr;
     }
     if (coef_host) {
         int status[1024];
