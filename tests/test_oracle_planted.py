@@ -86,3 +86,43 @@ def test_planted_mistake_is_caught(name, old, new, pin, tmp_path, oracle_lib):
                 pin(oracle_lib, tmp_path)
             else:
                 pin(oracle_lib)
+
+
+# ---- Algorithms 1 and 2 in the Python MLP oracle --------------------------------
+from tests import test_oracle_mlp as mlp_pins  # noqa: E402
+
+MLP_SRC = os.path.join(os.path.dirname(oracle.__file__), "mlp.py")
+
+MLP_PLANTS = [
+    ("dates iterated in increasing order",
+     "for i in sorted(dates, reverse=True):",
+     "for i in sorted(dates):",
+     mlp_pins.pin_backward_learning_runs_dates_downwards),
+    ("every date restarted from the initial parameters",
+     "p, best = base_alg(p, Z, y, **kw)",
+     "p, best = base_alg(p_init, Z, y, **kw)",
+     mlp_pins.pin_backward_learning_warm_starts),
+    ("output layer refitted at the last epoch",
+     "if epoch == epochs // 2:",
+     "if epoch == epochs:",
+     mlp_pins.pin_refit_at_half_the_epochs),
+    ("output ReLU never switched on",
+     "            pos = 1\n",
+     "            pos = 0\n",
+     mlp_pins.pin_output_relu_after_the_refit),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", MLP_PLANTS, ids=[p[0] for p in MLP_PLANTS])
+def test_planted_mlp_mistake_is_caught(name, old, new, pin, tmp_path):
+    import importlib.util
+    src = open(MLP_SRC).read()
+    assert src.count(old) == 1, f"plant site for {name!r} not found exactly once"
+    path = tmp_path / "mlp_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("mlp_mutant", str(path))
+    mutant = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mutant)
+    pin(mlp_pins.mlp)   # the unmodified oracle passes
+    with pytest.raises(AssertionError):
+        pin(mutant)
