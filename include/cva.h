@@ -165,6 +165,26 @@ CVA_API cva_status cva_relative_rmse(const float *phi_dev, const float *ref_dev,
 CVA_API cva_status cva_oversim_stats(const cva_sim *sim, int pf, const float *pred_dev, uint64_t seed,
                                      double *qr_host, void *stream);
 
+/* Choice of the oversimulation factor from the statistics of cva_oversim_stats
+ * (Prop. 1 and Heuristic 1, Sec. ss:choice1). qr_host: host double [n][2], the
+ * (Q_i, R_i) of n dates. Ni_host (host double [n]) receives, per date, the N that
+ * minimises the variance (R_i + Q_i / N)(N + kappa) / budget of the empirical loss at
+ * a fixed budget of M (N + kappa) inner-draw units, N_i = sqrt(Q_i kappa / R_i)
+ * (eq. (e:optom)), or NaN where R_i <= 0 or Q_i < 0 (no interior optimum); N_out
+ * receives Heuristic 1's N, the mean of the defined N_i; M_out (nullable) receives
+ * budget / (N + kappa), the outer paths the budget then pays for (NaN when budget
+ * <= 0). kappa is the cost of an outer path in inner draws (cva_inner_cost_ratio).
+ * CVA_ENUMERIC if no date defines N_i. Host-only, no device work. */
+CVA_API cva_status cva_oversim_choice(const double *qr_host, int n, double kappa, double budget,
+                                      double *Ni_host, double *N_out, double *M_out);
+
+/* The cost kappa of one outer path in units of one inner draw, eq. (l:ratio): from
+ * the times t1, t2 (any unit, > 0) of two simulations of the same M outer paths with
+ * N1 != N2 inner draws, assuming time = c M (kappa + N). kappa_out (host) receives
+ * (t1 N2 - t2 N1) / (t2 - t1). CVA_EINVAL for N1 == N2, equal or non-positive
+ * times. Host-only, no device work. */
+CVA_API cva_status cva_inner_cost_ratio(double t1, uint32_t N1, double t2, uint32_t N2, double *kappa_out);
+
 /* The twin estimator of eq. (e:val1): the mean over M paths of
  * phi^2 - (xi1 + xi2) phi + xi1 xi2, an unbiased estimate of the L2 error
  * E[(phi - E[xi | state at the branch date])^2] of any estimate phi computed from
@@ -347,6 +367,16 @@ CVA_API cva_status cva_mlp_fit(const float *targets_dev, const float *features_d
 /* Number of parameters of the network of cva_mlp_fit. */
 CVA_API int cva_mlp_num_params(int hidden);
 
+/* Launch shape cva_mlp_fit uses for M paths in n_batches batches at width hidden
+ * (Algorithm 1's batch of M / n_batches paths = tiles of 128 paths): out4_host
+ * (host int32 [4]) receives the number of CTAs of the trainer, its thread-block
+ * cluster size (0: a cooperative grid, width 128), the tiles per batch and the
+ * rounds of tiles a CTA runs per Adam step. Width 64 trains on one cluster of
+ * 4, 8 or 16 CTAs with two tile slots each; width 128 on a cooperative grid with
+ * one CTA per SM at most. Queries the current device; no GPU work. CVA_EINVAL
+ * (CVA_ENOTSUP for another width) on the arguments cva_mlp_fit would reject. */
+CVA_API cva_status cva_mlp_plan(uint64_t M, int hidden, int n_batches, int32_t *out4_host);
+
 /* Validation hook of cva_mlp_fit: one Adam step on the first batch; grad_dev
  * (float [cva_mlp_num_params]) receives that batch's gradient, params_dev the
  * updated parameters. */
@@ -377,14 +407,23 @@ CVA_API cva_status cva_mlp_regress_all(const cva_sim *sim, int pf, int hidden, i
  * It allocates nothing: its scratch (Gram partials, coefficients, status) is a
  * static 1 MiB device array inside the library, present on every device that
  * loads the library until the process exits. That array bounds the batch: a
- * call with more groups than fit (about 200 for the linear basis with F = 27,
- * 1024 at most) returns CVA_EINVAL with the limit in cva_last_error(). The
- * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; later calls reuse it. Every call shares
- * the array and leaves its contents behind; each call writes what it reads, so
- * nothing needs clearing, but calls whose kernels overlap on the GPU (e.g. on two
- * streams) race on the array and must be ordered by the caller. Synchronises
- * `stream` when coef_host is not NULL. */
+ * call with more groups than fit (207 for the linear basis with F = 27; 1024
+ * at most, e.g. for F <= 10 or the poly2 basis) returns CVA_EINVAL with the
+ * limit in cva_last_error().
+ *
+ * Set-up: the first call on a device (and again after the device's context was
+ * destroyed and re-created, e.g. by cudaDeviceReset) looks up the array's device
+ * address with cudaGetSymbolAddress and sets the shared-memory limit of the
+ * kernels it launches; later calls reuse both. Make that first call before any
+ * stream capture. coef_host needs a synchronisation of `stream`: while `stream`
+ * is being captured the call returns CVA_EINVAL unless coef_host is NULL.
+ *
+ * Every call shares the array and leaves its contents behind; each call writes
+ * what it reads, so nothing needs clearing, but calls whose kernels overlap on
+ * the GPU (e.g. on two streams) race on the array and must be ordered by the
+ * caller. Synchronises `stream` when coef_host is not NULL. Singular normal
+ * equations are reported (CVA_ENUMERIC) only when coef_host is given; without
+ * it the predictions of such a group are not checked. */
 CVA_API cva_status cva_regress_batched_static(const float *targets_dev, const float *features_dev,
                                               int groups, int F, uint64_t M, int basis,
                                               float *pred_dev, double *coef_host, void *stream);

@@ -56,6 +56,9 @@ SIGNATURES = {
     "cva_relative_rmse": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, _dp, ctypes.c_void_p]),
     "cva_oversim_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, _dp,
                                          ctypes.c_void_p]),
+    "cva_oversim_choice": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]),
+    "cva_inner_cost_ratio": (ctypes.c_int, [ctypes.c_double, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32,
+                                            _dp]),
     "cva_sim_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                     ctypes.POINTER(ctypes.c_size_t)]),
     "cva_sim_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
@@ -82,6 +85,7 @@ SIGNATURES = {
                                    ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p]),
     "cva_mlp_num_params": (ctypes.c_int, [ctypes.c_int]),
+    "cva_mlp_plan": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
     "cva_mlp_first_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
                                               ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p]),

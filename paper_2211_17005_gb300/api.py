@@ -252,22 +252,25 @@ def relative_rmse(phi: torch.Tensor, ref: torch.Tensor, stream=None) -> Tuple[fl
 
 
 def inner_cost_ratio(t1: float, N1: int, t2: float, N2: int) -> float:
-    """The cost kappa of an outer path in units of inner draws, from the times t1, t2
-    of two runs with the same M and N1 != N2 inner draws (time proportional to
-    M (kappa + N), eq. (l:ratio))."""
-    return (t1 * N2 - t2 * N1) / (t2 - t1)
+    """The cost kappa of an outer path in units of inner draws from two timings at the
+    same M (see cva_inner_cost_ratio)."""
+    k = ctypes.c_double()
+    nat.check(N_lib().cva_inner_cost_ratio(float(t1), int(N1), float(t2), int(N2), ctypes.byref(k)),
+              "cva_inner_cost_ratio")
+    return float(k.value)
 
 
 def oversimulation_choice(Q, R, kappa: float, budget: Optional[float] = None):
-    """Prop. 1 and Heuristic 1: per date N_i = sqrt(Q_i kappa / R_i) (dates with
-    R_i <= 0 or Q_i < 0 skipped), N = their mean, and M = budget / (N + kappa) when a
-    budget (in inner-draw units) is given. Returns (N_i array, N, M or None)."""
-    Q, R = np.asarray(Q, dtype=np.float64), np.asarray(R, dtype=np.float64)
-    ok = (R > 0) & (Q >= 0)
-    Ni = np.full(Q.shape, np.nan)
-    Ni[ok] = np.sqrt(Q[ok] * kappa / R[ok])
-    N = float(np.nanmean(Ni)) if ok.any() else float("nan")
-    return Ni, N, (budget / (N + kappa) if budget is not None else None)
+    """Prop. 1 and Heuristic 1 (see cva_oversim_choice): (N_i per date, N, M or None)."""
+    qr = np.ascontiguousarray(np.stack([np.asarray(Q, dtype=np.float64), np.asarray(R, dtype=np.float64)], axis=1))
+    n = qr.shape[0]
+    Ni = np.zeros(n)
+    N, M = ctypes.c_double(), ctypes.c_double()
+    _dp = ctypes.POINTER(ctypes.c_double)
+    nat.check(N_lib().cva_oversim_choice(qr.ctypes.data_as(_dp), n, float(kappa),
+                                         float(budget) if budget is not None else 0.0, Ni.ctypes.data_as(_dp),
+                                         ctypes.byref(N), ctypes.byref(M)), "cva_oversim_choice")
+    return Ni, float(N.value), (float(M.value) if budget is not None else None)
 
 
 def twin_l2(phi: torch.Tensor, xi1: torch.Tensor, xi2: torch.Tensor, stream=None) -> Tuple[float, float]:
@@ -320,6 +323,13 @@ MLP_IN = 32
 
 def mlp_num_params(hidden: int) -> int:
     return int(N_lib().cva_mlp_num_params(hidden))
+
+
+def mlp_plan(M: int, hidden: int = 64, n_batches: int = 32) -> dict:
+    """Launch shape of the trainer for M paths in n_batches batches (see cva_mlp_plan)."""
+    out = (ctypes.c_int32 * 4)()
+    nat.check(N_lib().cva_mlp_plan(int(M), int(hidden), int(n_batches), out), "cva_mlp_plan")
+    return {"ctas": int(out[0]), "cluster": int(out[1]), "tiles_per_batch": int(out[2]), "rounds": int(out[3])}
 
 
 def mlp_pack(p, hidden: int) -> torch.Tensor:

@@ -408,6 +408,44 @@ cva_status cva_relative_rmse(const float *phi_dev, const float *ref_dev, uint64_
     return relative_rmse_fp64(phi_dev, ref_dev, M, out2, reinterpret_cast<cudaStream_t>(stream));
 }
 
+cva_status cva_inner_cost_ratio(double t1, uint32_t N1, double t2, uint32_t N2, double *kappa_out)
+{
+    if (!kappa_out) return fail(CVA_EINVAL, "cost_ratio: NULL output");
+    if (!is_fin(t1) || !is_fin(t2) || !(t1 > 0.0) || !(t2 > 0.0) || N1 == N2)
+        return fail(CVA_EINVAL, "cost_ratio: need two positive timings at different N");
+    // t = c M (kappa + N) at both N: two equations in c M and kappa (eq. (l:ratio))
+    const double kappa = (t1 * (double)N2 - t2 * (double)N1) / (t2 - t1);
+    if (!is_fin(kappa)) return fail(CVA_EINVAL, "cost_ratio: equal timings");
+    *kappa_out = kappa;
+    return CVA_OK;
+}
+
+cva_status cva_oversim_choice(const double *qr_host, int n, double kappa, double budget, double *Ni_host,
+                              double *N_out, double *M_out)
+{
+    if (!qr_host || !Ni_host || !N_out || n < 1) return fail(CVA_EINVAL, "oversim_choice: bad arguments");
+    if (!is_fin(kappa) || !(kappa >= 0.0)) return fail(CVA_EINVAL, "oversim_choice: kappa must be >= 0");
+    // Prop. 1: at a fixed budget M (N + kappa) the variance of the empirical loss,
+    // (R + Q / N) (N + kappa) / budget, is smallest at N_i = sqrt(Q_i kappa / R_i)
+    // (eq. (e:optom)); Heuristic 1 takes the mean of the N_i over the dates and
+    // spends the budget on M = budget / (N + kappa) outer paths.
+    double sum = 0.0;
+    int used = 0;
+    for (int i = 0; i < n; ++i) {
+        const double Q = qr_host[2 * i], R = qr_host[2 * i + 1];
+        if (is_fin(Q) && is_fin(R) && R > 0.0 && Q >= 0.0) {
+            Ni_host[i] = std::sqrt(Q * kappa / R);
+            sum += Ni_host[i];
+            ++used;
+        } else {
+            Ni_host[i] = std::nan("");   // no optimum: R <= 0 or Q < 0 (estimates at a degenerate date)
+        }
+    }
+    *N_out = used > 0 ? sum / used : std::nan("");
+    if (M_out) *M_out = (used > 0 && budget > 0.0) ? budget / (*N_out + kappa) : std::nan("");
+    return used > 0 ? CVA_OK : fail(CVA_ENUMERIC, "oversim_choice: no date with R > 0 and Q >= 0");
+}
+
 cva_status cva_oversim_stats(const cva_sim *sim, int pf, const float *pred_dev, uint64_t seed, double *qr_host,
                              void *stream)
 {
@@ -706,6 +744,12 @@ cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner
 }
 
 int cva_mlp_num_params(int hidden) { return mlp_num_params(hidden); }
+
+cva_status cva_mlp_plan(uint64_t M, int hidden, int n_batches, int32_t *out4_host)
+{
+    if (!out4_host) return fail(CVA_EINVAL, "mlp_plan: NULL output");
+    return mlp_plan(M, hidden, n_batches, out4_host);
+}
 
 cva_status cva_mlp_fit(const float *targets_dev, const float *features_dev, int F, uint64_t M, int hidden,
                        int n_batches, int epochs, float lr, float *params_dev, float *pred_dev, float *loss_dev,

@@ -170,6 +170,9 @@ cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups
 // mlp_begin clears the device status before it and mlp_finish synchronises `st`
 // and reports a bounded wait that gave up.
 int mlp_num_params(int U);
+// Launch shape of the trainer (cva_mlp_plan); mlp_wide_plan is the width-128 one.
+cva_status mlp_plan(uint64_t M, int U, int n_batches, int32_t out[4]);
+cva_status mlp_wide_plan(int tiles_per_batch, int32_t out[4]);
 cva_status mlp_begin(cudaStream_t st);
 cva_status mlp_finish(cudaStream_t st);
 cva_status mlp_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride, int n_dates,

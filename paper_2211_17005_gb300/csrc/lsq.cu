@@ -6,6 +6,8 @@
 // solved by a Jacobi-scaled Cholesky factorisation in FP64. The pass over the
 // features and targets is the only HBM traffic: every byte is read once. For the
 // linear basis the tiles are copied by cp.async into two buffers (lsq_gram_async).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 
 #include <mutex>
@@ -645,25 +647,64 @@ static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
 namespace {
 std::mutex g_static_mu;
-double *g_static_ptr[64] = {};
+struct StaticSetup {
+    unsigned long long ctx_id = 0;   // CUDA context the address below belongs to (0: none yet)
+    double *ptr = nullptr;
+};
+StaticSetup g_static[64];
+PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+
+// dynamic shared memory of the linear-basis Gram kernel at width MP (launch_gram's size)
+template <int MP, int TR>
+cva_status static_gram_attr()
+{
+    constexpr int NUT = (MP / 4) * (MP / 4 + 1) / 2, NRG = kGramThreads / NUT;
+    const size_t tiles = 2 * (size_t)TR * (MP + 4) * sizeof(float), red = (size_t)NRG * NUT * 16 * sizeof(double);
+    CVA_CUDA_TRY(cudaFuncSetAttribute(lsq_gram_async<MP, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(tiles > red ? tiles : red)));
+    return CVA_OK;
+}
 }  // namespace
 
-// Device address of the static scratch on the current device. The first call on
-// a device resolves it with cudaGetSymbolAddress (the host-side name is only a
-// stand-in for the device array), later calls reuse the cached address.
+// Set-up of the allocation-free path on the current device, once per device and
+// CUDA context (a context created after cudaDeviceReset gets its own): the device
+// address of the static scratch (cudaGetSymbolAddress; the host-side name is only
+// a stand-in for the device array) and the shared-memory limits of the Gram
+// kernels it launches. Later calls in the same context reuse both.
 static cva_status static_scratch(double **out)
 {
     int dev = 0;
     CVA_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        CVA_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1));
+        CVA_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        if (!f1 || !f2 || q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess)
+            return fail(CVA_ECUDA, "regress_static: cuCtxGetCurrent / cuCtxGetId not available");
+        g_ctx_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+        g_ctx_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+    }
+    CVA_CUDA_TRY(cudaSetDevice(dev));   // initialises the device's primary context and makes it current
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_id(ctx, &id) != CUDA_SUCCESS)
+        return fail(CVA_ECUDA, "regress_static: no current CUDA context");
+    StaticSetup &su = g_static[dev];
+    if (su.ctx_id != id || !su.ptr) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
-        g_static_ptr[dev] = static_cast<double *>(p);
+        cva_status r = static_gram_attr<12, 512>();
+        if (r == CVA_OK) r = static_gram_attr<32, 256>();
+        if (r != CVA_OK) return r;
+        su.ptr = static_cast<double *>(p);
+        su.ctx_id = id;
     }
-    *out = g_static_ptr[dev];
+    *out = su.ptr;
     return CVA_OK;
 }
 
@@ -678,7 +719,7 @@ cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups
     if (basis == CVA_BASIS_LINEAR && (F < 1 || m + 1 > 32))
         return fail(CVA_ENOTSUP, "regress_static: linear basis supports 1 <= F <= 30");
     if (basis == CVA_BASIS_POLY2 && F < 1) return fail(CVA_EINVAL, "regress_static: need one factor");
-    const int MP = (m + 1 <= 4) ? 4 : 32;
+    const int MP = lsq_width(m, 1);
     const size_t NUT = (size_t)(MP / 4) * (MP / 4 + 1) / 2;
     const size_t per_group_fixed = 2 * (size_t)m + 1;          // coefficients (two bases) + status
     const size_t per_chunk = NUT * 16;
@@ -687,6 +728,13 @@ cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups
         return fail(CVA_EINVAL, "regress_static: " + std::to_string(groups) + " groups exceed the static scratch (at most " +
                                     std::to_string(max_groups < 1024 ? max_groups : 1024) +
                                     " groups of this basis per call)");
+    if (coef_host) {   // the coefficients come back through a synchronisation of st
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CVA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(CVA_EINVAL, "regress_static: coef_host needs a synchronisation of the stream, which is "
+                                    "being captured; pass coef_host = NULL there");
+    }
     double *scratch = nullptr;
     cva_status r = static_scratch(&scratch);
     if (r != CVA_OK) return r;
@@ -717,14 +765,17 @@ cva_status lsq_batched_static(const float *targ0, const float *feat0, int groups
     a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)groups * m);
 
     const dim3 ggrid((unsigned)chunks, (unsigned)groups);
-    if (MP == 4) {
-        cva_status gr = launch_gram<4, 1024>(a, ggrid, st);
-        if (gr != CVA_OK) return gr;
-        lsq_solve<4><<<groups, 256, 0, st>>>(a);
-    } else {
-        cva_status gr = launch_gram<32, 256>(a, ggrid, st);
-        if (gr != CVA_OK) return gr;
-        lsq_solve<32><<<groups, 256, 0, st>>>(a);
+    cva_status gr = CVA_OK;
+    switch (MP) {
+    case 4: gr = launch_gram<4, 1024>(a, ggrid, st); break;
+    case 12: gr = launch_gram<12, 512>(a, ggrid, st); break;
+    default: gr = launch_gram<32, 256>(a, ggrid, st); break;
+    }
+    if (gr != CVA_OK) return gr;
+    switch (MP) {
+    case 4: lsq_solve<4><<<groups, 256, 0, st>>>(a); break;
+    case 12: lsq_solve<12><<<groups, 256, 0, st>>>(a); break;
+    default: lsq_solve<32><<<groups, 256, 0, st>>>(a); break;
     }
     CVA_CUDA_TRY(cudaGetLastError());
     if (pred0) {

@@ -792,11 +792,11 @@ struct MlpPlan {
     int sweep_grid, cluster;
 };
 
-cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, int n_dates, int epochs, cudaStream_t st,
-                       MlpWork *&wout, MlpPlan &pl)
+// kernel attributes, the largest cluster the train kernel can run on, the internal
+// streams and events of a device (once per device; the caller holds g_mlp_mu)
+cva_status mlp_attrs(MlpWork &w)
 {
     using L = Layout<64>;
-    MlpWork &w = g_mlp[dev];
     if (!w.attrs) {
         CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           L::bytes_train));
@@ -830,12 +830,30 @@ cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, int n_
             CVA_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         w.attrs = true;
     }
+    return CVA_OK;
+}
+
+// cluster of the train kernel for a batch of tiles_per_batch tiles: the smallest
+// power of two >= 4 whose two tile slots per CTA cover the batch in one round, at
+// most the largest cluster that fits
+int mlp_cluster(const MlpWork &w, int tiles_per_batch)
+{
+    int cl = 4;
+    while (cl < w.max_cluster && 2 * cl < tiles_per_batch) cl *= 2;
+    return cl;
+}
+
+cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, int n_dates, int epochs, cudaStream_t st,
+                       MlpWork *&wout, MlpPlan &pl)
+{
+    using L = Layout<64>;
+    MlpWork &w = g_mlp[dev];
+    cva_status ar = mlp_attrs(w);
+    if (ar != CVA_OK) return ar;
     const uint64_t tiles = M / kRows;
     const int rounds = (int)((tiles + 2 * (uint64_t)sms - 1) / (2 * (uint64_t)sms));
     pl.sweep_grid = (int)((tiles + 2 * (uint64_t)rounds - 1) / (2 * (uint64_t)rounds));
-    int cl = 4;
-    while (cl < w.max_cluster && 2 * cl < tiles_per_batch) cl *= 2;
-    pl.cluster = cl;
+    pl.cluster = mlp_cluster(w, tiles_per_batch);
     constexpr int Z = L::Z;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_adam = al(2 * (size_t)L::NPpad * 4), b_best = al((size_t)L::NPpad * 4),
@@ -891,6 +909,27 @@ cva_status mlp_check_args(int F, uint64_t M, int U, int n_batches, int epochs)
 }  // namespace
 
 int mlp_num_params(int U) { return 35 * U + U * U + 2; }
+
+cva_status mlp_plan(uint64_t M, int U, int n_batches, int32_t out[4])
+{
+    cva_status r = mlp_check_args(1, M, U, n_batches, 1);
+    if (r != CVA_OK) return r;
+    const int tiles_per_batch = (int)(M / n_batches / kRows);
+    if (U == 128) return mlp_wide_plan(tiles_per_batch, out);
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    MlpWork &w = g_mlp[dev];
+    r = mlp_attrs(w);
+    if (r != CVA_OK) return r;
+    const int cl = mlp_cluster(w, tiles_per_batch);
+    out[0] = cl;
+    out[1] = cl;
+    out[2] = tiles_per_batch;
+    out[3] = (tiles_per_batch + 2 * cl - 1) / (2 * cl);
+    return CVA_OK;
+}
 
 cva_status mlp_begin(cudaStream_t st)
 {

@@ -862,7 +862,27 @@ struct WideWork {
 std::mutex g_wide_mu;
 WideWork g_wide[64];
 
+
+// grid of the trainer: at most one CTA per SM, about two tiles per CTA and round
+int wide_grid(int tiles_per_batch, int sms)
+{
+    int G = tiles_per_batch >= 2 ? (tiles_per_batch + 1) / 2 : 1;
+    return G > sms ? sms : G;
+}
 }  // namespace
+
+cva_status mlp_wide_plan(int tiles_per_batch, int32_t out[4])
+{
+    int dev = 0, sms = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    CVA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int G = wide_grid(tiles_per_batch, sms);
+    out[0] = G;
+    out[1] = 0;
+    out[2] = tiles_per_batch;
+    out[3] = (tiles_per_batch + G - 1) / G;
+    return CVA_OK;
+}
 
 cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride,
                               int n_dates, int F, uint64_t M, int n_batches, int epochs, float lr, int max_steps,
@@ -887,9 +907,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     int per_sm = 0;
     CVA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide_train_kernel, kWThreads, WL::bytes));
     if (per_sm < 1) return fail(CVA_ENOTSUP, "mlp: the width-128 trainer does not fit on an SM");
-    // grid of the trainer: at most one CTA per SM, about two tiles per CTA and round
-    int G = tiles_per_batch >= 2 ? (tiles_per_batch + 1) / 2 : 1;
-    if (G > sms) G = sms;
+    const int G = wide_grid(tiles_per_batch, sms);
     const uint64_t tiles = M / kRows;
     const int sweep_grid = (int)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
 

@@ -85,3 +85,21 @@ def test_python_binding_marshals_and_reports_errors(libcva):
     assert ei.value.status == CVA_EINVAL
     with pytest.raises(CvaError):
         api.Simulation(wl.model, wl.portfolios, wl.grid, 64, 0)
+
+
+def test_oversimulation_choice_edges(libcva):
+    """Prop. 1 / Heuristic 1 in the library (host only): dates without an interior
+    optimum get NaN and are left out of the mean; no usable date is an error; the
+    cost ratio needs two different draw counts."""
+    import numpy as np
+    from paper_2211_17005_gb300 import api
+    from paper_2211_17005_gb300._native import CvaError, CVA_EINVAL, CVA_ENUMERIC
+    Ni, N, M = api.oversimulation_choice([4.0, 1.0, -1.0], [1.0, 0.0, 1.0], 100.0, budget=1e6)
+    assert Ni[0] == np.sqrt(4.0 * 100.0 / 1.0) and np.isnan(Ni[1]) and np.isnan(Ni[2])
+    assert N == Ni[0] and M == 1e6 / (N + 100.0)
+    with pytest.raises(CvaError) as ei:
+        api.oversimulation_choice([1.0], [0.0], 10.0)
+    assert ei.value.status == CVA_ENUMERIC
+    with pytest.raises(CvaError) as ei:
+        api.inner_cost_ratio(1.0, 8, 2.0, 8)
+    assert ei.value.status == CVA_EINVAL

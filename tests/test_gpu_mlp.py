@@ -30,11 +30,22 @@ def _problem(M, d=27, seed=0):
     return Y, xi
 
 
-@pytest.mark.parametrize("u,M", [(64, 4096 * 4), (128, 4096 * 4), (128, 1 << 20)])
+# (width, paths) -> the trainer's launch shape at 32 batches: width 64 runs one cluster
+# whose two tile slots per CTA cover a batch in one round (4 tiles: 4 CTAs; 16 tiles:
+# 8 CTAs; 32 tiles, the 2^17-path workload's batch: 16 CTAs summing 16 partials over
+# distributed shared memory); width 128 a cooperative grid of about half a batch's tiles.
+PLANS = {(64, 4096 * 4): (4, 4, 4, 1), (64, 1 << 16): (8, 8, 16, 1), (64, 1 << 17): (16, 16, 32, 1),
+         (128, 4096 * 4): (2, 0, 4, 2), (128, 1 << 20): (128, 0, 256, 2)}
+
+
+@pytest.mark.parametrize("u,M", list(PLANS))
 def test_first_step_gradient_matches_oracle(api, u, M):
-    """One Adam step; at (128, 2^20) the batch is the 2^20-path workload's (256 tiles over
-    a grid of 128 CTAs exchanging their partials)."""
+    """One Adam step at each launch shape of the trainer, among them the two that the
+    benchmark runs: (64, 2^17) on a 16-CTA cluster and (128, 2^20), 256 tiles over a
+    grid of 128 CTAs exchanging their partials."""
     nb = 32
+    plan = api.mlp_plan(M, hidden=u, n_batches=nb)
+    assert (plan["ctas"], plan["cluster"], plan["tiles_per_batch"], plan["rounds"]) == PLANS[(u, M)], plan
     Y, xi = _problem(M)
     p0 = W.mlp_init(27, u, seed=11)
     flat = api.mlp_pack(p0, u)
@@ -57,9 +68,11 @@ def test_first_step_gradient_matches_oracle(api, u, M):
     assert np.all(g[:u * 32].reshape(u, 32)[:, 27:] == 0)
 
 
-@pytest.mark.parametrize("u", [64, 128])
-def test_base_alg_trains_like_the_oracle(api, u):
-    M, nb, E = 4096 * 4, 32, 8
+@pytest.mark.parametrize("u,M", [(64, 4096 * 4), (128, 4096 * 4), (64, 1 << 17)])
+def test_base_alg_trains_like_the_oracle(api, u, M):
+    """Algorithm 1 at one date; (64, 2^17) is the benchmark's trainer shape (a 16-CTA
+    cluster, 256 Adam steps)."""
+    nb, E = 32, 8
     Y, xi = _problem(M, seed=1)
     p0 = W.mlp_init(27, u, seed=12)
     flat = api.mlp_pack(p0, u)

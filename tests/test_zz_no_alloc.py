@@ -4,7 +4,11 @@ the same fits as the allocating one (cva_regress), call after call.
 It serves callers that cannot allocate device memory when they need a fit (a
 framework owning the whole device through its pool, a fixed memory budget, or a
 loop that cannot afford cudaMalloc's device-wide synchronisation); its scratch is
-a static array inside the library. This file is collected last on purpose.
+a static array inside the library.
+
+The file's name makes pytest collect it after every other test file: should it
+fail, a run that stops at the first failure has already run all the other tests.
+It depends on no other test and passes alone in a fresh process as well.
 """
 import ctypes
 
@@ -44,7 +48,12 @@ def _static_call(nat, xi, Y, basis, m):
     return pred.cpu().numpy(), coef
 
 
-@pytest.mark.parametrize("basis_name,G,F,M", [("linear", 6, 27, 70_001), ("poly2", 3, 1, 16_384)])
+# widths of the normal matrix: F = 27 -> 32 columns, F = 5 -> 12, poly2 -> 4; M = 70 001
+# and 9 999 take the scalar prediction path (M not a multiple of 4); 207 groups of the
+# 28-column basis is the most the static array holds (one Gram chunk per group)
+@pytest.mark.parametrize("basis_name,G,F,M", [("linear", 6, 27, 70_001), ("linear", 4, 5, 9_999),
+                                              ("linear", 5, 5, 32_768), ("poly2", 3, 1, 16_384),
+                                              ("poly2", 2, 1, 16_385), ("linear", 207, 27, 4_096)])
 def test_static_scratch_matches_allocating_entry_point(lib, basis_name, G, F, M):
     from paper_2211_17005_gb300 import api
     nat = lib
@@ -68,11 +77,15 @@ def test_static_scratch_matches_allocating_entry_point(lib, basis_name, G, F, M)
         np.testing.assert_allclose(coef, ref_coef, rtol=1e-4, atol=1e-6 * np.abs(ref_coef).max())
 
 
-def test_static_scratch_rejects_oversized_batches(lib):
+@pytest.mark.parametrize("groups,F,limit", [(5000, 27, 207), (208, 27, 207), (1025, 5, 1024)])
+def test_static_scratch_rejects_oversized_batches(lib, groups, F, limit):
+    """A batch beyond the static array is refused on the host, before any launch, with
+    the limit in the message."""
     nat = lib
-    Y, xi = _inputs(1, 27, 1024, seed=1)
+    Y, xi = _inputs(1, F, 1024, seed=1)
     st = nat.lib().cva_regress_batched_static(
-        ctypes.c_void_p(xi.data_ptr()), ctypes.c_void_p(Y.data_ptr()), 5000, 27, 1024, nat.BASIS_LINEAR,
+        ctypes.c_void_p(xi.data_ptr()), ctypes.c_void_p(Y.data_ptr()), groups, F, 1024, nat.BASIS_LINEAR,
         None, None, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == nat.CVA_EINVAL
-    assert b"static scratch" in nat.lib().cva_last_error()
+    msg = nat.lib().cva_last_error()
+    assert b"static scratch" in msg and f"at most {limit} groups".encode() in msg, msg
