@@ -46,6 +46,8 @@ def parse():
                    help="skip the least squares on (default indicators, state) over the M N sample")
     p.add_argument("--no-precision", action="store_true",
                    help="skip the 2^20-path width-128 network measurement")
+    p.add_argument("--no-validation", action="store_true",
+                   help="skip the twin, oversimulation and nested Monte Carlo measurements (profiling runs)")
     p.add_argument("--paths", type=int, default=None,
                    help="override the number of outer paths (small cases for profiling captures)")
     return p.parse_args()
@@ -60,9 +62,9 @@ def peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
-def alu_peak_lane_instr_per_s(sm_mhz):
-    """Issue peak of the SM sub-partitions: 152 SMs x 4 schedulers x 32 lanes per clock."""
-    return 152 * 4 * 32 * sm_mhz * 1e6
+def alu_peak_lane_instr_per_s(sm_mhz, sms):
+    """Issue peak of the SM sub-partitions: SMs x 4 schedulers x 32 lanes per clock."""
+    return sms * 4 * 32 * sm_mhz * 1e6
 
 
 def _shape(wl):
@@ -176,10 +178,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(wl, M_sample, use_mlp=None):
+def cpu_oracle_sample(wl, M_sample, use_mlp=None, n_threads=0):
     """Time the FP64 oracle on the first M_sample outer paths of the workload: simulation,
     targets and the per-date regression (Algorithm 2 with the NN+ network for the MLP
-    workloads, least squares otherwise). Returns (seconds, threads)."""
+    workloads, least squares otherwise). Returns (seconds, threads, oracle outputs,
+    per-date regression results)."""
     import oracle
     from oracle import mlp as omlp
     from paper_2211_17005_gb300 import workload
@@ -188,18 +191,79 @@ def cpu_oracle_sample(wl, M_sample, use_mlp=None):
         use_mlp = wl.regression == "mlp"
     t0 = time.perf_counter()
     o = oracle.simulate(wl.model, wl.portfolios[0], wl.grid, 0, M_sample, wl.N, wl.seed,
-                        want=("features", "xi_bar"))
+                        want=("features", "I0", "Lambda", "mtm", "idx", "xi_bar"), n_threads=n_threads)
     dates = range(1, wl.grid.n_steps)
     if use_mlp:
         p0 = workload.mlp_init(wl.model.F, wl.hidden or 64)
-        omlp.backward_alg(p0, o["features"], o["xi_bar"], dates, n_batches=32, epochs=8, lr=1e-3)
+        reg = omlp.backward_alg(p0, o["features"], o["xi_bar"], dates, n_batches=32, epochs=8, lr=1e-3)
     else:
+        reg = {}
         for i in dates:
             phi = oracle.linear_features(o["features"][i]) if wl.name != "small" else \
                 oracle.poly2_features(o["features"][i, 0])
-            oracle.lsq(phi, o["xi_bar"][i])
+            reg[i] = oracle.lsq(phi, o["xi_bar"][i])
     dt = time.perf_counter() - t0
-    return dt, os.cpu_count()
+    return dt, (n_threads or os.cpu_count()), o, reg
+
+
+def sim_errors(api, o, wl, M, pf=0, keep_sim=False):
+    """Errors of the GPU simulation (first M paths, the workload's seed, portfolio pf)
+    against the oracle's outputs o on the same paths: CVA_0, every per-path target
+    (against the oracle's targets rebuilt at the GPU's default step on tie-moved draws)
+    and the default steps."""
+    import oracle
+    import torch
+    from oracle import compare
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, M, wl.N, keep_defaults=True)
+    sim.run(wl.seed)
+    torch.cuda.synchronize()
+    idx = sim.defaults().cpu().numpy()
+    xi = sim.targets()[pf].cpu().numpy()
+    c0 = sim.cva0(pf)[0]
+    eps = oracle.exp_clocks(wl.seed, 0, M, wl.N, wl.model.C)
+    d = compare.default_mismatches(idx, o["idx"], o["Lambda"], eps, wl.grid.n_steps)
+    ref = compare.tie_corrected_targets(o, wl.model.recovery, idx, d["mism"])
+    c_or, c_corr = float(o["xi_bar"][0].mean()), float(ref[0].mean())
+    out = {"paths": M, "draws": d["draws"], "default_step_mismatches": d["n_mism"], "ties": d["n_tie"],
+           "tie_share": d["n_tie"] / d["draws"], "mismatches_outside_tie_band": len(d["outside"]),
+           "cva0_gpu": c0, "cva0_oracle": c_or, "cva0_rel_err": abs(c0 - c_or) / c_or,
+           "cva0_rel_err_tie_corrected": abs(c0 - c_corr) / c_corr,
+           "targets": compare.target_errors(xi, ref, c_corr),
+           "tolerances": {"cva0_rel": compare.CVA0_RTOL, "target_rel": compare.XI_RTOL,
+                          "target_floor_cva0": compare.XI_FLOOR_CVA0, "tie_share_max": compare.TIE_MAX_SHARE}}
+    if keep_sim:
+        return out, sim, c_corr
+    sim.close()
+    return out
+
+
+def lsq_gap(pred_gpu, feats_or, xi_or, dates, cva0, poly2=False):
+    """Largest and median RMS gap, in units of CVA_0, between the GPU's per-date least
+    squares predictions and the oracle's QR fit on its own data."""
+    import oracle
+    gaps = []
+    for i in dates:
+        phi = oracle.poly2_features(feats_or[i, 0]) if poly2 else oracle.linear_features(feats_or[i])
+        _, po = oracle.lsq(phi, xi_or[i])
+        gaps.append(float(np.sqrt(np.mean((pred_gpu[i].astype(np.float64) - po) ** 2))) / cva0)
+    return {"l2_gap_over_cva0_max": max(gaps), "l2_gap_over_cva0_median": float(np.median(gaps)),
+            "dates": len(gaps), "bound": 1e-3}
+
+
+def mlp_gaps(pred_gpu, xi_gpu, res, xi_or, dates):
+    """Per-date gaps of the GPU's NN+ regression against the FP64 oracle's Algorithm 1/2:
+    the relative excess of the GPU's training loss over the oracle's, and the RMS gap of
+    the predictions in units of the targets' RMS."""
+    lg, pg = [], []
+    for i in dates:
+        p_or = res[i][2]
+        l_gpu = float(np.mean((pred_gpu[i].astype(np.float64) - xi_gpu[i]) ** 2))
+        l_or = float(np.mean((p_or - xi_or[i]) ** 2))
+        lg.append((l_gpu - l_or) / l_or)
+        pg.append(float(np.sqrt(np.mean((pred_gpu[i] - p_or) ** 2)) / np.sqrt(np.mean(xi_or[i] ** 2))))
+    return {"loss_excess_max": max(lg), "loss_excess_median": float(np.median(lg)),
+            "pred_gap_over_target_rms_max": max(pg), "pred_gap_over_target_rms_median": float(np.median(pg)),
+            "dates": len(lg)}
 
 
 def reference_arm(args):
@@ -213,13 +277,14 @@ def reference_arm(args):
         cpu_oracle_sample(wl, M_sample)
     times = []
     for _ in range(args.steps):
-        dt, cores = cpu_oracle_sample(wl, M_sample)
+        dt, cores, _, _ = cpu_oracle_sample(wl, M_sample)
         times.append(dt)
     t = float(np.sum(times))
     value = args.steps * M_sample * wl.N * wl.grid.n_steps / t
     cb = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
           "sample": f"first {M_sample} of {wl.M} outer paths per step, all {wl.N} inner draws, "
-                    f"{wl.grid.n_steps} dates, per-date least squares"}
+                    f"{wl.grid.n_steps} dates, per-date "
+                    + ("NN+ Algorithm 2" if wl.regression == "mlp" else "least squares")}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
                       "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
@@ -319,7 +384,7 @@ def main():
 
     # ---- twin Monte Carlo validation of the last step's regression at the middle date ----
     twin = None
-    if rank == 0:
+    if rank == 0 and not args.no_validation:
         i_tw = n // 2
         phi = last_pred[i_tw].clone()
         t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -340,7 +405,7 @@ def main():
 
     # ---- oversimulation factor (Prop. 1, Heuristic 1) for the step's regression ----
     oversim = None
-    if rank == 0:
+    if rank == 0 and not args.no_validation:
         sim.run(args.steps, k0=k0)   # the buffers hold twin copy 2: the step's own paths again
         torch.cuda.synchronize()
         Qs, Rs = sim.oversim_stats(last_pred, args.steps)
@@ -369,7 +434,7 @@ def main():
 
     # ---- nested Monte Carlo reference at the middle date (first 16384 paths, 1024 copies) ----
     nested = None
-    if rank == 0:
+    if rank == 0 and not args.no_validation:
         Mv, K = min(16384, wl.M), 1024
         i_n = n // 2
         sim_v = api.Simulation(wl.model, wl.portfolios, wl.grid, Mv, wl.N)
@@ -417,7 +482,9 @@ def main():
     s_avg, p_avg, i_avg = float(np.mean(sim_ms)), float(np.mean(price_ms)), float(np.mean(inner_ms))
     clk = clocks.summary()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    peak_alu = alu_peak_lane_instr_per_s(sm_mhz)
+    n_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak_alu = alu_peak_lane_instr_per_s(sm_mhz, n_sms)
+    pipes = api.pipe_peaks() if rank == 0 else None
     kern = {"sim_kernel": (sim_instr_per_path_step(wl), s_avg, "path-step"),
             "price_kernel": (price_instr_per_path_date(wl), p_avg, "path-date")}
     alu = {}
@@ -428,7 +495,7 @@ def main():
                      "algorithmic_instr_per_unit": per_unit, "unit_of_work": unit, "ms": ms}
     dom = max(alu, key=lambda k: alu[k]["ms"])
     roof = dict(alu[dom])
-    roof["peak_source"] = f"152 SMs x 128 lanes x {sm_mhz:g} MHz ({src} max SM clock)"
+    roof["peak_source"] = f"{n_sms} SMs x 128 lanes x {sm_mhz:g} MHz ({src} max SM clock)"
     hbm = pk.get("hbm_gbs", 6800.0)
     inner_gbs = inner_bytes_per_path(wl) * wl.M / (i_avg / 1e3) / 1e9
     reg_bytes = 4 * (n - 1) * wl.M * (wl.model.F + 1 + 1)
@@ -570,13 +637,104 @@ def main():
                                   "peak_source": "measured bf16 cuBLAS, sustained"}}
         psim.close()
 
-    cpu = None
+    # ---- the FP64 oracle: CPU baseline on a path prefix, and the error of every
+    # benchmarked result against it (rank 0; after every timed region) ----
+    cpu, errors = None, None
     if rank == 0 and not args.no_cpu_baseline:
-        M_sample = 2048 if wl.name != "small" else wl.M
-        dt, cores = cpu_oracle_sample(wl, M_sample, use_mlp)
-        cpu = {"value": M_sample * wl.N * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {M_sample} of {wl.M} outer paths, all {wl.N} inner draws, {n} dates, "
+        from oracle import compare as ocmp
+        from oracle import mlp as omlp
+        import oracle
+        M_s = 4096 if wl.name != "small" else wl.M
+        dt, cores, o, reg_or = cpu_oracle_sample(wl, M_s, use_mlp)
+        cpu = {"value": M_s * wl.N * n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {M_s} of {wl.M} outer paths, all {wl.N} inner draws, {n} dates, "
                          f"per-date {'NN+ Algorithm 2' if use_mlp else 'least squares'} ({dt:.1f} s)"}
+        # one host core: the oracle's simulation and regression of the first 512 paths
+        M_1 = 512 if wl.name != "small" else 2048
+        dt1, _, _, _ = cpu_oracle_sample(wl, M_1, use_mlp and M_1 % 32 == 0, n_threads=1)
+        cpu["one_core"] = {"value": M_1 * wl.N * n / dt1, "unit": UNIT, "cores": 1,
+                           "sample": f"first {M_1} paths, simulation on 1 thread, numpy regression ({dt1:.1f} s)"}
+        errors = {"note": "GPU result on the first paths of the workload (its seed) against the FP64 oracle on "
+                          "the same paths; targets and CVA_0 also against the oracle rebuilt at the GPU's default "
+                          "step on tie-moved draws"}
+        e_sim, gsim, c_corr = sim_errors(api, o, wl, M_s, keep_sim=True)
+        errors["timed_workload"] = e_sim
+        g_lsq, _ = gsim.regress_all(0, basis=basis, want_coef=False)
+        errors["timed_workload"]["least_squares"] = lsq_gap(g_lsq.cpu().numpy(), o["features"], o["xi_bar"],
+                                                            range(1, n), c_corr, poly2=(basis == "poly2"))
+        if use_mlp:
+            g_pred = api.mlp_regress_all(gsim, p_init.clone(), hidden=hidden, n_batches=n_batches,
+                                         epochs=epochs, lr=lr).cpu().numpy()
+            errors["timed_workload"]["nn_algorithm2"] = mlp_gaps(g_pred, gsim.targets()[0].cpu().numpy()
+                                                                 .astype(np.float64), reg_or, o["xi_bar"],
+                                                                 range(1, n))
+        gsim.close()
+        del o, reg_or
+
+        if not args.no_precision and args.workload != "precision":
+            pwl = workload.make("precision", M=args.paths)
+            Mp = 4096
+            po = oracle.simulate(pwl.model, pwl.portfolios[0], pwl.grid, 0, Mp, pwl.N, pwl.seed,
+                                 want=("features", "I0", "Lambda", "mtm", "idx", "xi_bar"))
+            e_p, psim2, pc = sim_errors(api, po, pwl, Mp, keep_sim=True)
+            i_m = pwl.grid.n_steps // 2
+            feats_t = psim2.features()[i_m].contiguous()
+            targ_t = psim2.targets()[0, i_m].contiguous()
+            pp = api.mlp_pack(workload.mlp_init(pwl.model.F, pwl.hidden), pwl.hidden)
+            pred_g, _ = api.mlp_fit(targ_t, feats_t, pp, hidden=pwl.hidden, n_batches=n_batches, epochs=epochs, lr=lr)
+            Zo, _, _ = omlp.standardize(po["features"][i_m].T)
+            bp, _ = omlp.base_alg(workload.mlp_init(pwl.model.F, pwl.hidden), Zo, po["xi_bar"][i_m],
+                                  n_batches=n_batches, epochs=epochs, lr=lr)
+            e_p["nn_algorithm1_middle_date"] = mlp_gaps({i_m: pred_g.cpu().numpy()},
+                                                        {i_m: targ_t.cpu().numpy().astype(np.float64)},
+                                                        {i_m: (bp, None, omlp.forward(bp, Zo, 1)[0])},
+                                                        po["xi_bar"], [i_m])
+            psim2.close()
+            errors["precision"] = e_p
+            del po
+
+        if not args.no_batched:
+            bwl = workload.make("batched", M=args.paths)
+            Mb, pb = 1024, len(bwl.portfolios) - 1      # the 2000-swap portfolio
+            bo = oracle.simulate(bwl.model, bwl.portfolios[pb], bwl.grid, 0, Mb, bwl.N, bwl.seed,
+                                 want=("features", "I0", "Lambda", "mtm", "idx", "xi_bar"))
+            e_b, bsim2, bc = sim_errors(api, bo, bwl, Mb, pf=pb, keep_sim=True)
+            bpred2, _ = bsim2.regress_portfolios("linear")
+            e_b["least_squares"] = lsq_gap(bpred2[pb].cpu().numpy(), bo["features"], bo["xi_bar"],
+                                           range(1, bwl.grid.n_steps), bc)
+            e_b["portfolio"] = f"{pb} ({bwl.portfolios[pb].n_swaps} swaps) of the six, simulated together"
+            bsim2.close()
+            errors["batched"] = e_b
+            del bo
+
+        if not args.no_adjoint:
+            awl = workload.make("adjoint", M=args.paths)
+            apf = api.frozen(awl.model, awl.portfolios[0])
+            Ma = 128
+            c_g, g_g = api.grad_cva0(awl.model, apf, awl.grid, Ma, awl.seed, ckpt_every=10)
+            theta = api.grad_params(awl.model)
+
+            def smooth(th):
+                oo = oracle.simulate(api.with_params(awl.model, th), apf, awl.grid, 0, Ma, 1, awl.seed,
+                                     want=("smooth",))
+                return float(oo["smooth"][0].mean())
+            c_o = smooth(theta)
+            fd = np.zeros_like(theta)
+            for i in range(theta.size):
+                h = 1e-6 * max(abs(theta[i]), 1e-2)
+                tp, tm = theta.copy(), theta.copy()
+                tp[i] += h
+                tm[i] -= h
+                fd[i] = (smooth(tp) - smooth(tm)) / (2 * h)
+            sc = float(np.max(np.abs(fd)))
+            big = np.abs(fd) > 1e-3 * sc
+            errors["adjoint"] = {"paths": Ma, "parameters": int(theta.size),
+                                 "smooth_cva0_rel_err": abs(c_g - c_o) / c_o,
+                                 "grad_max_abs_err_over_max_grad": float(np.max(np.abs(g_g - fd))) / sc,
+                                 "grad_max_rel_err_components_above_1e-3_max": float(np.max(np.abs(g_g - fd)[big]
+                                                                                         / np.abs(fd[big]))),
+                                 "reference": "central differences of the oracle's smooth CVA_0 (FP64, common "
+                                              "random numbers, bump 1e-6 max(|theta|, 1e-2))"}
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -591,6 +749,9 @@ def main():
                "inner_kernel_ms": i_avg, "regression_ms": float(np.mean(reg_ms)),
                "sim_throughput": wl.M * wl.N * n / ((s_avg + p_avg + i_avg) / 1e3),
                "alu_kernels": alu,
+               "pipe_peaks_measured": ({k: v / 1e12 for k, v in pipes.items()} | {
+                   "unit": "T lane-op/s", "issue_peak": peak_alu / 1e12,
+                   "note": "cva_pipe_peaks: 8 independent chains per thread, 64 warps per SM"}) if pipes else None,
                "regression_samples_per_s": wl.M * (n - 1) / (np.mean(reg_ms) / 1e3),
                "inner_kernel_gbs": inner_gbs, "regression_gbs": reg_gbs, "hbm_peak_gbs": hbm,
                "cva0": c0[0], "cva0_se": c0[1],
@@ -599,7 +760,7 @@ def main():
                "nested_validation": nested,
                "adjoint_forward": adj, "batched": batched, "alive_regression": alive,
                "precision": precision,
-               "cpu_baseline": cpu,
+               "cpu_baseline": cpu, "errors_vs_oracle": errors,
                "clocks": clk,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},

@@ -437,6 +437,16 @@ CVA_API cva_status cva_regress_batched_static(const float *targets_dev, const fl
 CVA_API cva_status cva_philox4x32_10(const uint32_t *ctr_dev, uint32_t *out_dev, uint64_t n,
                                      uint64_t seed, void *stream);
 
+/* Measured throughput of the SMs' plain arithmetic pipes on the current device,
+ * the ceilings of the kernels that neither HBM nor the tensor cores bound (the
+ * path simulation and the pricing; the paper gives no such figure). Each probe
+ * runs eight independent chains of one instruction per thread on 64 warps per SM
+ * and is timed with CUDA events after a warm-up launch. out5_host (host double
+ * [5]) receives lane-operations per second of: fma.rn.f32, lop3.b32,
+ * mul.hi.u32, ex2.approx.f32, lg2.approx.f32. Allocates a 4 KB sink; synchronises
+ * `stream`; about 10 ms of GPU time. */
+CVA_API cva_status cva_pipe_peaks(double *out5_host, void *stream);
+
 /* Thread-local message describing the last error of this thread. */
 CVA_API const char *cva_last_error(void);
 

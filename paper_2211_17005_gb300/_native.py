@@ -96,6 +96,7 @@ SIGNATURES = {
                                                   ctypes.c_void_p]),
     "cva_philox4x32_10": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_void_p]),
+    "cva_pipe_peaks": (ctypes.c_int, [_dp, ctypes.c_void_p]),
     "cva_last_error": (ctypes.c_char_p, []),
     "cva_version": (ctypes.c_char_p, []),
 }

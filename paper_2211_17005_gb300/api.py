@@ -306,6 +306,15 @@ def regress(targets: torch.Tensor, features: torch.Tensor, basis: str = "linear"
     return pred, coef
 
 
+def pipe_peaks(stream=None) -> dict:
+    """Measured lane-operations per second of the SMs' FMA, ALU, integer multiply-high
+    and MUFU pipes (see cva_pipe_peaks)."""
+    out = np.zeros(5)
+    nat.check(N_lib().cva_pipe_peaks(out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_handle(stream)),
+              "cva_pipe_peaks")
+    return dict(zip(("fma_f32", "lop3_b32", "mul_hi_u32", "ex2_f32", "lg2_f32"), (float(x) for x in out)))
+
+
 def philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
     """Philox4x32-10 blocks of the counters ctr (device int32/uint32 tensor [n, 4])."""
     assert ctr.is_cuda and ctr.shape[-1] == 4 and ctr.element_size() == 4

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2211_17005_gb300 import workload as W
-from tests.gpu_helpers import compare_defaults, compare_targets
+from tests.gpu_helpers import compare_all_targets
 
 pytestmark = pytest.mark.gpu
 
@@ -32,11 +32,9 @@ def test_six_portfolios_and_grouped_regression_match_oracle(api):
     n = wl.grid.n_steps
     for p, pf in enumerate(wl.portfolios):
         o = oracle.simulate(wl.model, pf, wl.grid, 0, wl.M, wl.N, wl.seed,
-                            want=("features", "Lambda", "idx", "xi_bar"))
+                            want=("features", "Lambda", "I0", "mtm", "idx", "xi_bar"))
         eps = oracle.exp_clocks(wl.seed, 0, wl.M, wl.N, wl.model.C)
-        skip, _, _ = compare_defaults(idx, o["idx"], o["Lambda"], eps, n)
-        cva0 = float(o["xi_bar"][0].mean())
-        compare_targets(xi[p], o["xi_bar"], skip, cva0)
+        cva0, _, _ = compare_all_targets(xi[p], o, wl.model.recovery, idx, o["Lambda"], eps, n)
         for i in range(1, n):
             _, p_or = oracle.lsq(oracle.linear_features(o["features"][i]), o["xi_bar"][i])
             assert np.sqrt(np.mean((pred[p, i] - p_or) ** 2)) <= 1e-3 * cva0, (p, i)

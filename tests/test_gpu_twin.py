@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2211_17005_gb300 import workload as W
-from tests.gpu_helpers import compare_defaults, compare_targets
+from tests.gpu_helpers import compare_all_targets
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +29,7 @@ def _copy_pair(api, wl, M, date, copy):
          "xi": sim.targets()[0].cpu().numpy()}
     sim.close()
     o = oracle.simulate(wl.model, wl.portfolios[0], wl.grid, 0, M, wl.N, wl.seed,
-                        want=("features", "Lambda", "idx", "xi_bar"), copy=(date, copy))
+                        want=("features", "Lambda", "I0", "mtm", "idx", "xi_bar"), copy=(date, copy))
     o["eps"] = oracle.exp_clocks(wl.seed, 0, M, wl.N, wl.model.C, copy=copy)
     return g, o
 
@@ -39,8 +39,7 @@ def test_twin_copy_matches_oracle(api, name, M, date, copy):
     wl = W.make(name)
     g, o = _copy_pair(api, wl, M, date, copy)
     np.testing.assert_allclose(g["features"], o["features"], rtol=0, atol=2e-6)
-    skip, _, _ = compare_defaults(g["idx"], o["idx"], o["Lambda"], o["eps"], wl.grid.n_steps)
-    compare_targets(g["xi"], o["xi_bar"], skip, float(o["xi_bar"][0].mean()))
+    compare_all_targets(g["xi"], o, wl.model.recovery, g["idx"], o["Lambda"], o["eps"], wl.grid.n_steps)
 
 
 def test_twin_estimator_matches_oracle_on_the_same_inputs(api):

@@ -71,9 +71,11 @@ def test_static_scratch_matches_allocating_entry_point(lib, basis_name, G, F, M)
     for call in range(2):        # two calls in a row share the static scratch
         pred, coef = _static_call(nat, xi, Y, basis, m)
         assert np.all(np.isfinite(pred))
-        assert np.sqrt(np.mean((pred - ref_pred) ** 2)) < 1e-6 * scale, call
-        # coefficients: the tolerance of the same-input regression test (test_gpu_lsq.py);
-        # the two entry points split the Gram sums into different chunk counts
+        # the two entry points split the Gram sums into different chunk counts (one per
+        # group at the 207-group limit), so the FP32 runs round differently: predictions
+        # agree to 1e-5 of the targets' scale, the coefficients to 1e-4 relative
+        assert np.sqrt(np.mean((pred - ref_pred) ** 2)) < 1e-5 * scale, call
+        # coefficients: the tolerance of the same-input regression test (test_gpu_lsq.py)
         np.testing.assert_allclose(coef, ref_coef, rtol=1e-4, atol=1e-6 * np.abs(ref_coef).max())
 
 
