@@ -48,6 +48,9 @@ def parse():
                    help="skip the 2^20-path width-128 network measurement")
     p.add_argument("--no-validation", action="store_true",
                    help="skip the twin, oversimulation and nested Monte Carlo measurements (profiling runs)")
+    p.add_argument("--tiles", default=None,
+                   help="sim_block,price_block,inner_paths,lsq_chunks,portfolios_per_price_block for the timed "
+                        "simulation (profiling runs; default: the library's defaults)")
     p.add_argument("--paths", type=int, default=None,
                    help="override the number of outer paths (small cases for profiling captures)")
     return p.parse_args()
@@ -337,6 +340,8 @@ def main():
         return s.regress_all(0, basis=basis, want_coef=False)[0]
     k0 = rank * wl.M          # weak scaling: each rank owns its own outer paths
     sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N, profile=True)
+    if args.tiles:
+        sim.set_tiles(*(int(v) for v in args.tiles.split(",")))
     stream = torch.cuda.current_stream()
     n = wl.grid.n_steps
 

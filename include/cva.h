@@ -308,8 +308,11 @@ CVA_API cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *re
  * in an earlier process): sim_block in {64, 128}, price_block in {128, 256},
  * inner_paths_per_block in {0 (automatic), 2, 4, 8}, lsq_chunk_target in
  * [152, 2^20], portfolios_per_price_block in {1, 2, 3} dividing the simulation's
- * number of portfolios. None of them changes any result bit. Returns CVA_EINVAL
- * (nothing changed) on a value outside these sets. No GPU work. */
+ * number of portfolios (a pricing block prices that many portfolios, weights in
+ * constant memory) or 0 (every thread prices every portfolio for two paths,
+ * weights staged in shared memory; price_block is then unused). None of them
+ * changes any result bit. Returns CVA_EINVAL (nothing changed) on a value outside
+ * these sets. No GPU work. */
 CVA_API cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner_paths_per_block,
                                  int lsq_chunk_target, int portfolios_per_price_block);
 
@@ -376,6 +379,16 @@ CVA_API int cva_mlp_num_params(int hidden);
  * one CTA per SM at most. Queries the current device; no GPU work. CVA_EINVAL
  * (CVA_ENOTSUP for another width) on the arguments cva_mlp_fit would reject. */
 CVA_API cva_status cva_mlp_plan(uint64_t M, int hidden, int n_batches, int32_t *out4_host);
+
+/* Failure-detection hook of the width-128 trainer: a CTA waiting at the trainer's
+ * grid barrier gives up after grid_polls polls (about 32 ns apart; the default is
+ * 2^22, over 0.1 s), sets the device status word and leaves its remaining waits at
+ * once, so that every CTA ends its launch and the call returns CVA_ETIMEOUT (no
+ * CTA outlives its tensor-core or copy operations: their own bounded waits are not
+ * shortened). 0 makes every wait give up unless the barrier is already complete;
+ * UINT32_MAX restores the default. Applies to the launches enqueued after it, on
+ * every device; host-only, no device work. */
+CVA_API cva_status cva_mlp_set_wait_limit(uint32_t grid_polls);
 
 /* Validation hook of cva_mlp_fit: one Adam step on the first batch; grad_dev
  * (float [cva_mlp_num_params]) receives that batch's gradient, params_dev the

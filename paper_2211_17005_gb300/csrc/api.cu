@@ -676,8 +676,9 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
             s.tune_price_pf = save[4];
             return err == CVA_OK ? t : 1e30f;
         };
-        // portfolios per pricing block: the divisors of n_pf among 1, 2, 3
-        std::vector<int> ppf = {1};
+        // portfolios per pricing block: the divisors of n_pf among 1, 2, 3 (weights in
+        // constant memory), or 0 (every portfolio per thread, weights in shared memory)
+        std::vector<int> ppf = {0, 1};
         for (int v : {2, 3})
             if (s.NPF % v == 0) ppf.push_back(v);
         const std::vector<std::vector<int>> cand = {{64, 128}, {128, 256}, {2, 4, 8}, {1216, 2432, 4864, 9728}, ppf};
@@ -733,8 +734,9 @@ cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner
         return fail(CVA_EINVAL, "inner_paths_per_block must be 0, 2, 4 or 8");
     if (lsq_chunk_target < 152 || lsq_chunk_target > (1 << 20))
         return fail(CVA_EINVAL, "lsq_chunk_target must lie in [152, 2^20]");
-    if (portfolios_per_price_block < 1 || portfolios_per_price_block > 3 || s.NPF % portfolios_per_price_block != 0)
-        return fail(CVA_EINVAL, "portfolios_per_price_block must be 1, 2 or 3 and divide the number of portfolios");
+    if (portfolios_per_price_block < 0 || portfolios_per_price_block > 3 ||
+        (portfolios_per_price_block > 0 && s.NPF % portfolios_per_price_block != 0))
+        return fail(CVA_EINVAL, "portfolios_per_price_block must be 0, or 1, 2 or 3 dividing the number of portfolios");
     s.tune_sim_block = sim_block;
     s.tune_price_block = price_block;
     s.tune_inner_P = inner_paths_per_block;
@@ -744,6 +746,12 @@ cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner
 }
 
 int cva_mlp_num_params(int hidden) { return mlp_num_params(hidden); }
+
+cva_status cva_mlp_set_wait_limit(uint32_t grid_polls)
+{
+    mlp_wide_set_grid_polls(grid_polls);
+    return CVA_OK;
+}
 
 cva_status cva_mlp_plan(uint64_t M, int hidden, int n_batches, int32_t *out4_host)
 {

@@ -86,7 +86,7 @@ struct Sim {
     unsigned char *d_const_img = nullptr;
     // tile shapes, set by cva_autotune
     int tune_sim_block = 128, tune_price_block = 256, tune_inner_P = 0, tune_lsq_chunks = 2432;
-    int tune_price_pf = 1;         // portfolios per pricing block (1, 2 or 3, dividing n_pf)
+    int tune_price_pf = 1;         // portfolios per pricing block (1, 2 or 3, dividing n_pf; 0: all, from shared memory)
     // scratch of the portfolio-grouped regression, owned by the simulation
     double *d_lsq = nullptr;
     size_t lsq_cap = 0;
@@ -173,6 +173,7 @@ int mlp_num_params(int U);
 // Launch shape of the trainer (cva_mlp_plan); mlp_wide_plan is the width-128 one.
 cva_status mlp_plan(uint64_t M, int U, int n_batches, int32_t out[4]);
 cva_status mlp_wide_plan(int tiles_per_batch, int32_t out[4]);
+void mlp_wide_set_grid_polls(uint32_t polls);
 cva_status mlp_begin(cudaStream_t st);
 cva_status mlp_finish(cudaStream_t st);
 cva_status mlp_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride, int n_dates,

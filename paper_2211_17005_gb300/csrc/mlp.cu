@@ -88,10 +88,9 @@ struct Layout {
     static constexpr int sStage = sTh + NPpad * 4;              // [2][kIn + 1][128] FP32 inputs, target
     static constexpr int sVec = sStage + 2 * (kIn + 1) * kRows * 4;   // mean[32], istd[32]
     static constexpr int sGsl = sVec + 2 * kIn * 4;             // [8 warps][U + 2] output-layer gradients
-    static constexpr int sMom = sGsl + 8 * (U + 2) * 4;         // Adam moments of the owned slice
-    static constexpr int kSliceMax = NPpad / 4;                 // clusters of at least 4 CTAs
-    static constexpr int bytes_train = sMom + 2 * kSliceMax * 4;
-    static constexpr int bytes_sweep = sMom;
+    static constexpr int sRecv = sGsl + 8 * (U + 2) * 4;        // train: [CL][NPpad / CL] partial slices received
+    static constexpr int bytes_train = sRecv + NPpad * 4;
+    static constexpr int bytes_sweep = sRecv;
     static constexpr uint32_t tmem_cols = 512;   // D of slot s at [64 s, 64 s + U), DW at [128 + 128 s, +128)
 
     // The shared copy of the parameters and the gradient partials keep W1 and W2
@@ -556,6 +555,21 @@ __device__ void net_teardown(Net<U> &n)
 // One epoch (or its first n_steps batches) of Adam on one cluster of CL >= 4 CTAs.
 // Batch b covers paths [b * P, (b + 1) * P), P = tiles_per_batch * 128; in each
 // step the cluster's 2 CL slots take the batch's tiles round-robin.
+//
+// The exchange of one Adam step moves data only by bulk copies between the CTAs'
+// shared memories, each completing on the receiver's mbarrier (no cluster-wide
+// barrier inside the step loop):
+//   1. every CTA writes its gradient partial (column order q) and copies slice c
+//      of it into CTA c's receive buffer, at row = its own rank;
+//   2. CTA c waits for the CL slices of its own slice, sums them in CTA order,
+//      applies Adam (moments in global memory, requested before the wait) and
+//      writes the new values into its own copy of the parameters;
+//   3. CTA c copies that slice into every other CTA's copy of the parameters;
+//      every CTA waits for the other CL - 1 slices before its next step.
+// A CTA's next partial reaches an owner only after that CTA received the owner's
+// new slice, which the owner sent after summing the previous partials: the
+// receive buffer, the partial and the parameter slices are never overwritten
+// while still being read.
 template <int U>
 __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, const __grid_constant__ CUtensorMap tm)
 {
@@ -563,28 +577,31 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar[4];
+    __shared__ __align__(8) uint64_t s_xbar[2];   // exchange: partial slices received, parameter slices received
     Net<U> n(smem, s_mbar);
     const uint32_t rank = umma::cluster_rank(), CL = umma::cluster_size();
     float *th = reinterpret_cast<float *>(smem + L::sTh);
     float *part = reinterpret_cast<float *>(smem);   // slot 0's A rows, free between steps
     float *gsl = reinterpret_cast<float *>(smem + L::sGsl);
-    float *mom = reinterpret_cast<float *>(smem + L::sMom);
+    const float *recv = reinterpret_cast<const float *>(smem + L::sRecv);
     // owned slice [lo, hi) of the padded parameter vector: a multiple of 4 entries
     const int S = L::NPpad / (int)CL, lo = (int)rank * S, hi = lo + S;
+    const uint32_t slice_bytes = (uint32_t)S * 4u;
 
     // the previous kernel of the stream has completed and its writes are visible;
     // from here on the next train launch may become resident
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    net_setup<U>(n, &s_tmem, s_mbar, a.init, a.stats, a.F, false);
-    for (int q = lo + n.tid; q < hi; q += kThreads) {
-        mom[q - lo] = a.step0 == 0 ? 0.f : a.adam_m[q];
-        mom[L::kSliceMax + q - lo] = a.step0 == 0 ? 0.f : a.adam_v[q];
+    if (n.tid == 0) {
+        umma::mbar_init(&s_xbar[0], 1);
+        umma::mbar_init(&s_xbar[1], 1);
     }
+    net_setup<U>(n, &s_tmem, s_mbar, a.init, a.stats, a.F, false);   // fences the barrier initialisation
     if (a.step0 == 0 && rank == 0) {   // start of a date: the starting parameters are the best so far
         for (int p = n.tid; p < L::NP; p += kThreads) a.best[p] = __ldg(a.init + p);
         if (n.tid == 0) *a.best_loss = 1e300;
     }
+    umma::cluster_sync();   // every CTA's exchange barriers exist before any copy targets them
 
     const uint32_t per_batch = (uint32_t)a.tiles_per_batch * kRows;
     const float inv_batch = 1.f / (float)per_batch;
@@ -593,6 +610,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
     auto path_of = [&](int st, int rd) { return (uint32_t)st * per_batch + (uint32_t)(rd * span + my) * kRows; };
     const bool h0 = 2 * (int)rank < a.tiles_per_batch, h1 = 2 * (int)rank + 1 < a.tiles_per_batch;
     float *my_gsl = gsl + n.warp * (U + 2);
+    const uint32_t part_s = umma::smem_u32(part), th_s = umma::smem_u32(th), recv_s = umma::smem_u32(recv);
+    const uint32_t xbar_part = umma::smem_u32(&s_xbar[0]), xbar_par = umma::smem_u32(&s_xbar[1]);
+    uint32_t ph_part = 0, ph_par = 0;
 
     bool ok = true;
     if (my_rounds > 0) n.prefetch(&tm, a.targ, a.F, path_of(0, 0));
@@ -608,40 +628,73 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
         __syncthreads();
         umma::fence_after_sync();
         n.write_partial(part, gsl, h0, h1);
-        umma::cluster_sync();   // every CTA's partial is complete
+        umma::fence_proxy_async();   // the partial is read by the bulk copies (async proxy)
+        __syncthreads();
+        if (n.tid < (int)CL)   // slice c of this CTA's partial -> CTA c's receive buffer, row `rank`
+            umma::bulk_s2c(umma::map_rank(recv_s + rank * slice_bytes, (uint32_t)n.tid),
+                           part_s + (uint32_t)n.tid * slice_bytes, slice_bytes,
+                           umma::map_rank(xbar_part, (uint32_t)n.tid));
 
-        // the owned slice: 16-byte remote loads of the cluster's partials (all in
-        // flight), sums in CTA order, Adam, 16-byte remote stores of the new values
-        // into every CTA's copy of the parameters
+        // the owned slice: Adam moments requested before the wait for the partials
         const int step = a.step0 + st + 1;
+        const bool fresh = a.step0 == 0 && st == 0;   // the moments of a date start at zero
         const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
-        const uint32_t part_s = umma::smem_u32(part), th_s = umma::smem_u32(th);
-        auto adam = [&](int q, float g) -> float {
+        const int q_first = lo + 4 * n.tid;
+        float4 m4 = make_float4(0.f, 0.f, 0.f, 0.f), v4 = m4;
+        if (q_first < hi && !fresh) {
+            m4 = __ldcg(reinterpret_cast<const float4 *>(a.adam_m + q_first));
+            v4 = __ldcg(reinterpret_cast<const float4 *>(a.adam_v + q_first));
+        }
+        if (n.tid == 0) umma::mbar_arrive_expect_tx(&s_xbar[0], (uint32_t)L::NPpad * 4u);
+        if (!umma::mbar_wait(&s_xbar[0], ph_part, kMbarPolls)) {
+            ok = false;
+            atomicExch(a.err, 4);
+        }
+        ph_part ^= 1u;
+        auto adam = [&](int q, float g, float &m, float &v) -> float {
             if (step == 1 && a.grad_out && q < L::NP) a.grad_out[L::p_of(q)] = g;
             if (q >= L::NP || (q < L::ob1 && q / U >= a.F)) return 0.f;   // padding stays zero
-            float &m = mom[q - lo], &v = mom[L::kSliceMax + q - lo];
             m = a.beta1 * m + (1.f - a.beta1) * g;
             v = a.beta2 * v + (1.f - a.beta2) * g * g;
             return th[q] - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
         };
-        for (int q0 = lo + 4 * n.tid; q0 < hi; q0 += 4 * kThreads) {
-            float4 gv[kMaxCluster];
+        for (int q0 = q_first; q0 < hi; q0 += 4 * kThreads) {
+            if (q0 != q_first && !fresh) {
+                m4 = __ldcg(reinterpret_cast<const float4 *>(a.adam_m + q0));
+                v4 = __ldcg(reinterpret_cast<const float4 *>(a.adam_v + q0));
+            } else if (q0 != q_first) {
+                m4 = v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const float4 *rv = reinterpret_cast<const float4 *>(recv + (q0 - lo));
+            float4 pv[kMaxCluster];
 #pragma unroll
-            for (int c = 0; c < kMaxCluster; ++c)
-                gv[c] = (uint32_t)c < CL ? umma::ld_cluster_f32x4(umma::map_rank(part_s + 4u * (uint32_t)q0, (uint32_t)c))
-                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < kMaxCluster; ++c)   // all loads in flight
+                pv[c] = (uint32_t)c < CL ? rv[c * (S / 4)] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < kMaxCluster; ++c) {
-                g.x += gv[c].x;
-                g.y += gv[c].y;
-                g.z += gv[c].z;
-                g.w += gv[c].w;
+            for (int c = 0; c < kMaxCluster; ++c) {   // fixed CTA order
+                g.x += pv[c].x;
+                g.y += pv[c].y;
+                g.z += pv[c].z;
+                g.w += pv[c].w;
             }
-            const float4 t = make_float4(adam(q0, g.x), adam(q0 + 1, g.y), adam(q0 + 2, g.z), adam(q0 + 3, g.w));
-            for (uint32_t c = 0; c < CL; ++c) umma::st_cluster_f32x4(umma::map_rank(th_s + 4u * (uint32_t)q0, c), t);
+            const float4 t = make_float4(adam(q0, g.x, m4.x, v4.x), adam(q0 + 1, g.y, m4.y, v4.y),
+                                         adam(q0 + 2, g.z, m4.z, v4.z), adam(q0 + 3, g.w, m4.w, v4.w));
+            *reinterpret_cast<float4 *>(th + q0) = t;
+            __stcg(reinterpret_cast<float4 *>(a.adam_m + q0), m4);
+            __stcg(reinterpret_cast<float4 *>(a.adam_v + q0), v4);
         }
-        umma::cluster_sync();   // new parameters everywhere; partials read
+        umma::fence_proxy_async();   // the new slice is read by the bulk copies
+        __syncthreads();
+        if (n.tid < (int)CL && n.tid != (int)rank)   // the new slice -> every other CTA's parameters
+            umma::bulk_s2c(umma::map_rank(th_s + (uint32_t)lo * 4u, (uint32_t)n.tid), th_s + (uint32_t)lo * 4u,
+                           slice_bytes, umma::map_rank(xbar_par, (uint32_t)n.tid));
+        if (n.tid == 0) umma::mbar_arrive_expect_tx(&s_xbar[1], (CL - 1u) * slice_bytes);
+        if (!umma::mbar_wait(&s_xbar[1], ph_par, kMbarPolls)) {
+            ok = false;
+            atomicExch(a.err, 4);
+        }
+        ph_par ^= 1u;
         n.build_images();
         umma::fence_proxy_async();
         __syncthreads();
@@ -651,8 +704,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
             a.params[L::p_of(q)] = th[q];
             if (a.snap) a.snap[L::p_of(q)] = th[q];
         }
-        a.adam_m[q] = mom[q - lo];
-        a.adam_v[q] = mom[L::kSliceMax + q - lo];
     }
     umma::cluster_sync();   // no CTA leaves while another may address its shared memory
     net_teardown<U>(n);

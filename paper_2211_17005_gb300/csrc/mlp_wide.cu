@@ -39,6 +39,7 @@
 #include <math.h>
 
 #include <climits>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -51,7 +52,7 @@ namespace cva {
 namespace {
 
 constexpr int kWThreads = 256;
-constexpr uint32_t kGridPolls = 1u << 22;
+constexpr uint32_t kGridPolls = 1u << 22;   // default limit of a grid-barrier wait (polls 32 ns apart)
 
 struct WL {
     static constexpr int U = 128;
@@ -118,6 +119,7 @@ struct WTrainArgs {
     uint16_t *gimg;                // [img_elems] BF16 images of W1 | W2 (shared-memory layout)
     float *gpart;                  // [grid][NPpad] q order: gradient partials
     unsigned *flags;               // [2] grid barrier: arrivals, generation (zero at launch)
+    uint32_t grid_polls;           // polls after which a grid-barrier wait gives up
     const float *stats;            // mean[32], 1/std[32]
     float *grad_out;               // [NP] row order: gradient of the first step (nullable)
     int *err;
@@ -147,7 +149,8 @@ struct WSweepArgs {
 // the status word set) sets the status word and returns false; all threads of the
 // CTA get the same answer. Every thread's global writes before the barrier are
 // visible to every thread of the grid after it.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned &gen, int *err)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned &gen, int *err,
+                                             uint32_t max_polls)
 {
     __threadfence();
     __syncthreads();
@@ -165,7 +168,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
                 unsigned v;
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar + 1) : "memory");
                 if ((int)(v - gen) >= 0) break;
-                if (++it > kGridPolls || *(volatile int *)err) {
+                if (++it > max_polls || *(volatile int *)err) {
                     ok = 0;
                     atomicExch(err, 3);
                     break;
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
             __syncthreads();
             for (int i = n.tid; i < 8 * 66; i += kWThreads) gsl[i] = 0.f;
         }
-        if (!grid_barrier(a.flags, (unsigned)G, gen, a.err)) ok = false;
+        if (!grid_barrier(a.flags, (unsigned)G, gen, a.err, a.grid_polls)) ok = false;
 
         // the owned slice: partials summed over the grid (nsub fixed interleaved
         // ranges of CTAs per group of four parameters, added in range order), Adam,
@@ -691,7 +694,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
                 __syncthreads();
             }
         }
-        if (!grid_barrier(a.flags, (unsigned)G, gen, a.err)) ok = false;
+        if (!grid_barrier(a.flags, (unsigned)G, gen, a.err, a.grid_polls)) ok = false;
 
         // every CTA: the new images and FP32 vectors
         {
@@ -860,6 +863,7 @@ struct WideWork {
     bool attrs = false;
 };
 std::mutex g_wide_mu;
+std::atomic<uint32_t> g_grid_polls{kGridPolls};
 WideWork g_wide[64];
 
 
@@ -870,6 +874,8 @@ int wide_grid(int tiles_per_batch, int sms)
     return G > sms ? sms : G;
 }
 }  // namespace
+
+void mlp_wide_set_grid_polls(uint32_t polls) { g_grid_polls.store(polls == UINT32_MAX ? kGridPolls : polls); }
 
 cva_status mlp_wide_plan(int tiles_per_batch, int32_t out[4])
 {
@@ -963,6 +969,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     ta.gimg = gimg;
     ta.gpart = gpart;
     ta.flags = flags;
+    ta.grid_polls = g_grid_polls.load();
     ta.grad_out = grad_out_dev;
     ta.err = err;
 

@@ -55,6 +55,7 @@ struct OuterArgs {
     const int *__restrict__ date_p;    // [n+1]
     const float *__restrict__ drift;   // [n*S][E]
     float *features, *disc, *thr, *expo, *mtm;
+    const float *w_glob;               // device copy of the date-bucketed weights: wA [kMaxW], then wK [kMaxW]
 };
 
 template <int E, int C, int CS>
@@ -248,6 +249,130 @@ __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
         }
 }
 
+// Every portfolio of the simulation priced by one thread, for two outer paths of a
+// pricing date at a time, with the date-bucketed weights staged once per block in
+// shared memory: each (path, date) computes its bond prices once for all
+// portfolios, and each weight, read with one broadcast load, feeds both paths. The
+// FMA order per path is price_kernel's, so the outputs are the same bits.
+// Block: 128 threads = paths [256 b, 256 b + 256) (thread t takes t and t + 128),
+// dates [DPB y, DPB y + DPB). Shared memory: NPF C E GP float2 (wA, wK) pairs,
+// GP = G rounded up to even so that every row of pairs is 16-byte aligned.
+template <int E, int C, int CS, int G, int NPF>
+__global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_per_block)
+{
+    constexpr int F = 2 * E - 1 + CS, GP = (G + 1) / 2 * 2, NPAIR = NPF * C * E * GP;
+    extern __shared__ float4 price_smem[];
+    float2 *wsm = reinterpret_cast<float2 *>(price_smem);
+    for (int i = threadIdx.x; i < NPAIR; i += blockDim.x) {
+        const int h = i % GP, row = i / GP;   // row = (pf C + c) E + e
+        wsm[i] = h < G ? make_float2(__ldg(a.w_glob + row * G + h), __ldg(a.w_glob + kMaxW + row * G + h))
+                       : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const size_t M = a.M;
+    const int n = c_sim.n, ppp = c_sim.ppp;
+    const uint32_t k_a = blockIdx.x * 256u + threadIdx.x, k_b = k_a + 128u;
+    if (k_a >= a.M) return;
+    const bool has_b = k_b < a.M;
+    const uint32_t kk[2] = {k_a, has_b ? k_b : k_a};
+    const int j0 = (int)blockIdx.y * dates_per_block;
+    for (int j = j0; j < j0 + dates_per_block && j <= n; ++j) {
+        if (j == 0) {   // no default at t_0: exposures of date 0 are never used
+#pragma unroll
+            for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        if (t == 1 && !has_b) continue;
+                        const size_t o = ((size_t)(pf * (n + 1)) * C + c) * M + kk[t];
+                        a.expo[o] = 0.f;
+                        if (a.mtm) a.mtm[o] = 0.f;
+                    }
+            continue;
+        }
+        const int p = __ldg(a.date_p + j);          // t_j in (p delta, (p+1) delta]
+        const float2 *fx = a.fix + (size_t)p * E;
+        float beta[2], mt[2][NPF][C];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            beta[t] = expf(-__ldg(a.disc + (size_t)j * M + kk[t]));
+#pragma unroll
+            for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+                for (int c = 0; c < C; ++c) mt[t][pf][c] = 0.f;
+        }
+#pragma unroll 1
+        for (int e = 0; e < E; ++e) {
+            const float2 f2 = __ldg(fx + e);
+            const float4 *tab = a.zc + ((size_t)j * E + e) * G;
+            const float4 tp = __ldg(tab + (p < G ? p : G - 1));   // p >= G: every swap has matured
+            float Z[2][G], D[2][G], chi[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const float *fe = a.features + (size_t)j * F * M + kk[t];
+                const float *ffix = a.features + (size_t)(p * ppp) * F * M + kk[t];
+                const float re = __ldg(fe + (size_t)e * M);
+                const float fixm1 = expm1f(fmaf(f2.y, __ldg(ffix + (size_t)e * M), -f2.x));
+                const float z_first = expf(fmaf(-tp.y, re, tp.x));
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    if (g < p) {
+                        Z[t][g] = 0.f;
+                        D[t][g] = 0.f;
+                    } else if (g == p) {
+                        Z[t][g] = z_first;
+                        D[t][g] = z_first * fixm1;
+                    } else {
+                        const float4 t4 = __ldg(tab + g);
+                        const float zp = Z[t][g > 0 ? g - 1 : 0];
+                        const float em = expm1_small(fmaf(-t4.w, re, t4.z));
+                        D[t][g] = -zp * em;
+                        Z[t][g] = fmaf(zp, em, zp);
+                    }
+                }
+                chi[t] = (e == 0) ? 1.f : expf(__ldg(fe + (size_t)(E - 1 + (e > 0 ? e : 1)) * M));
+            }
+#pragma unroll
+            for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float4 *wr = reinterpret_cast<const float4 *>(wsm + ((pf * C + c) * E + e) * GP);
+                    float wa[GP], wk[GP];
+#pragma unroll
+                    for (int q = 0; q < GP / 2; ++q) {
+                        const float4 w4 = wr[q];
+                        wa[2 * q] = w4.x;
+                        wk[2 * q] = w4.y;
+                        wa[2 * q + 1] = w4.z;
+                        wk[2 * q + 1] = w4.w;
+                    }
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        float acc = 0.f;
+#pragma unroll
+                        for (int h = 0; h < G; ++h) acc = fmaf(wa[h], D[t][h], acc);
+#pragma unroll
+                        for (int g = 0; g < G; ++g) acc = fmaf(-wk[g], Z[t][g], acc);
+                        mt[t][pf][c] = fmaf(chi[t], acc, mt[t][pf][c]);
+                    }
+                }
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (t == 1 && !has_b) continue;
+#pragma unroll
+            for (int pf = 0; pf < NPF; ++pf)
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const size_t o = ((size_t)(pf * (n + 1) + j) * C + c) * M + kk[t];
+                    a.expo[o] = c_sim.lgd[c] * beta[t] * fmaxf(mt[t][pf][c], 0.f);
+                    if (a.mtm) a.mtm[o] = mt[t][pf][c];
+                }
+        }
+    }
+}
+
 }  // namespace
 }  // namespace cva
 
@@ -300,6 +425,7 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.thr = s.d_thr;
     args.expo = s.d_expo;
     args.mtm = s.d_mtm;
+    args.w_glob = reinterpret_cast<const float *>(s.d_const_img + sizeof(SimConsts));
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CVA_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
     const bool capturing = cap != cudaStreamCaptureStatusNone;
@@ -321,6 +447,15 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     sim_kernel<E, C, CS><<<(args.M + sb - 1) / sb, sb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
+    if (s.tune_price_pf == 0) {   // every portfolio per thread, weights in shared memory
+        constexpr int GP = (G + 1) / 2 * 2;
+        const int dpb = 8;
+        const dim3 sgrid((args.M + 255u) / 256u, (unsigned)((s.n + 1 + dpb - 1) / dpb));
+        price_smem_kernel<E, C, CS, G, NPF><<<sgrid, 128, (size_t)NPF * C * E * GP * sizeof(float2), st>>>(args, dpb);
+        CVA_CUDA_TRY(cudaGetLastError());
+        if (!capturing) CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
+        return CVA_OK;
+    }
     const int ppb = ((s.tune_price_pf == 2 || s.tune_price_pf == 3) && NPF % s.tune_price_pf == 0) ? s.tune_price_pf : 1;
     const dim3 pgrid((args.M + pb - 1) / pb, (unsigned)s.n + 1u, (unsigned)(NPF / ppb));
     if constexpr (NPF % 3 == 0) {

@@ -174,6 +174,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// `bytes` (a multiple of 16) from this CTA's 16-byte aligned shared address `src` to
+// the 16-byte aligned shared::cluster address `dst` (another CTA's shared memory, from
+// map_rank); completes `bytes` transactions on the mbarrier at shared::cluster address
+// `bar` (in the CTA that owns `dst`)
+__device__ __forceinline__ void bulk_s2c(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "r"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // 2-D tiled TMA load: the box of the tensor map at coordinates (x, y) (x innermost;
 // x * element size a multiple of 16 bytes) into 128-byte aligned shared address
 // `dst`; completes the box's bytes on `bar`. `tmap` is the generic address of a

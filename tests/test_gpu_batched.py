@@ -79,7 +79,7 @@ def test_autotune_keeps_results(api):
     choice = sim.autotune(wl.seed, "linear")
     assert choice["sim_block"] in (64, 128) and choice["price_block"] in (128, 256)
     assert choice["inner_paths_per_block"] in (2, 4, 8)
-    assert choice["portfolios_per_price_block"] in (1, 2, 3)
+    assert choice["portfolios_per_price_block"] in (0, 1, 2, 3)
     sim.run(wl.seed)
     p, _ = sim.regress_portfolios("linear")
     torch.cuda.synchronize()
@@ -91,20 +91,26 @@ def test_autotune_keeps_results(api):
     sim.close()
 
 
-@pytest.mark.parametrize("ppb", [1, 2, 3])
-def test_pricing_portfolio_groups_bit_identical(api, ppb):
-    """Pricing 1, 2 or 3 portfolios per block changes no exposure, MtM or target bit."""
-    wl = W.make("batched", M=8192, N=32, n_steps=20)
-    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N)
+@pytest.mark.parametrize("name,M,ppb", [("batched", 8192, 0), ("batched", 8192, 1), ("batched", 8192, 2),
+                                        ("batched", 8192, 3), ("batched", 8191, 0), ("paper", 4099, 0),
+                                        ("small", 1001, 0)])
+def test_pricing_portfolio_groups_bit_identical(api, name, M, ppb):
+    """Pricing 1, 2 or 3 portfolios per block (weights in constant memory), or every
+    portfolio per thread for two paths (weights in shared memory, ppb = 0), changes no
+    exposure, MtM or target bit; ragged M leaves the last thread with one path."""
+    wl = W.make(name, M=M, N=32, n_steps=20 if name != "small" else 50)
+    sim = api.Simulation(wl.model, wl.portfolios, wl.grid, wl.M, wl.N, keep_exposures=True)
     sim.set_tiles(128, 256, 0, 2432, 1)
     sim.run(wl.seed)
     torch.cuda.synchronize()
-    ref_t = sim.targets().clone()
+    ref = [v.clone() for v in (sim.targets(), sim.exposures(), sim.mtm())]
     sim.set_tiles(64, 128, 4, 1216, ppb)
-    sim.targets().zero_()
+    for v in (sim.targets(), sim.exposures(), sim.mtm()):
+        v.fill_(float("nan"))
     sim.run(wl.seed)
     torch.cuda.synchronize()
-    assert torch.equal(sim.targets(), ref_t)
+    for got, want in zip((sim.targets(), sim.exposures(), sim.mtm()), ref):
+        assert torch.equal(got, want)
     with pytest.raises(RuntimeError):
-        sim.set_tiles(64, 128, 4, 1216, 4)          # not one of 1, 2, 3
+        sim.set_tiles(64, 128, 4, 1216, 4)          # not one of 0, 1, 2, 3
     sim.close()

@@ -123,3 +123,29 @@ def test_backward_learning_on_simulated_targets(api, u):
         # predictions miss it by several percent)
         assert abs(pred[i].mean() - targs[i].mean()) < 0.05 * scale, (i, pred[i].mean(), targs[i].mean())
     sim.close()
+
+
+def test_grid_barrier_timeout_is_reported_and_the_next_call_is_clean(api):
+    """Failure detection without a GPU fault: with the width-128 trainer's grid-barrier
+    wait limit at 0 polls, the first CTA to reach a barrier gives up, every CTA leaves
+    its remaining waits (each wait bounded; tensor-core and copy waits keep their full
+    limits), and the call returns CVA_ETIMEOUT. The status word is cleared at the next
+    call, which then gives the same first-step gradient as before the failure."""
+    from paper_2211_17005_gb300 import _native as nat
+    M, u, nb = 4096 * 4, 128, 32
+    Y, xi = _problem(M, seed=4)
+    yd, xd = torch.from_numpy(Y).cuda(), torch.from_numpy(xi).cuda()
+    p0 = W.mlp_init(27, u, seed=21)
+    assert api.mlp_plan(M, hidden=u, n_batches=nb)["ctas"] >= 2   # a barrier has someone to wait for
+    ref = api.mlp_first_gradient(xd, yd, api.mlp_pack(p0, u), hidden=u, n_batches=nb).cpu().numpy()
+    nat.lib().cva_mlp_set_wait_limit(0)
+    try:
+        with pytest.raises(nat.CvaError) as ei:
+            api.mlp_fit(xd, yd, api.mlp_pack(p0, u), hidden=u, n_batches=nb, epochs=2)
+        assert ei.value.status == nat.CVA_ETIMEOUT
+        assert "bounded device wait" in str(ei.value)
+    finally:
+        nat.lib().cva_mlp_set_wait_limit(0xFFFFFFFF)
+    again = api.mlp_first_gradient(xd, yd, api.mlp_pack(p0, u), hidden=u, n_batches=nb).cpu().numpy()
+    np.testing.assert_array_equal(again, ref)
+    torch.cuda.synchronize()
