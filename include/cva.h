@@ -98,6 +98,8 @@ typedef struct cva_sim cva_sim;   /* opaque: tables and device buffers of one ru
 #define CVA_KEEP_DEFAULTS  1u   /* also keep default step indices (validation)     */
 #define CVA_KEEP_EXPOSURES 2u   /* also keep the MtM per counterparty and date     */
 #define CVA_PROFILE        4u   /* record CUDA events around each kernel launch    */
+#define CVA_GENERIC_KERNELS 8u  /* run-time-shape kernels even where a compiled
+                                   instantiation exists (validation)               */
 
 /* Prepare a simulation of M outer paths x N inner default draws for n_pf
  * portfolios sharing one model and grid. Validates every input (returns
@@ -247,6 +249,42 @@ CVA_API cva_status cva_cva0(const float *xi0_dev, uint64_t M, double *out2_host,
 CVA_API cva_status cva_regress(const float *targets_dev, const float *features_dev, int F,
                        uint64_t M, int basis, float *pred_dev, double *coef_host,
                        void *stream);
+
+/* Least squares of eq. (e:forw) over outer paths split into ranges, one per process
+ * (and GPU), with one exchange: every range computes its part of the normal
+ * equations, the parts are summed (in a fixed order, on the host or by a
+ * collective), solved once, and every range predicts its own paths. Outer paths
+ * are independent and the generator's counters are keyed by the global path
+ * index (cva_simulate's k0), so a split run simulates exactly the paths of one
+ * large run, and the summed normal matrix is the whole sample's.
+ *
+ * cva_regress_partial: the augmented normal matrix [phi, xi]^T [phi, xi] (host
+ * double [(m+1) x (m+1)], row-major, symmetric; m = F+1 linear, 3 poly2) of the
+ * basis centred on centre_dev (device float [F], poly2 [1]: a state every range
+ * agrees on, e.g. path 0's), accumulated as cva_regress does (FP32 products in
+ * runs, FP64 sums in a fixed order). Synchronises `stream`.
+ * cva_regress_solve: host only. The summed matrix solved as cva_regress does
+ * (Jacobi scaling, Cholesky in FP64, a vanishing pivot's column dropped with
+ * coefficient 0): coef_centred_host (double [m], nullable) in the centred basis,
+ * coef_raw_host (double [m], nullable) in the raw basis for centre_host (host
+ * double copy of the centre), dropped_host (nullable) the number of dropped columns.
+ * cva_regress_predict: pred_dev (device float [M]) receives phi(Y_k) . w for the
+ * centred coefficients of cva_regress_solve. Synchronises `stream`. */
+CVA_API cva_status cva_regress_partial(const float *targets_dev, const float *features_dev, int F, uint64_t M,
+                                       int basis, const float *centre_dev, double *gram_host, void *stream);
+CVA_API cva_status cva_regress_solve(const double *gram_host, int F, int basis, const double *centre_host,
+                                     double *coef_centred_host, double *coef_raw_host, int *dropped_host);
+CVA_API cva_status cva_regress_predict(const float *features_dev, int F, uint64_t M, int basis,
+                                       const float *centre_dev, const double *coef_centred_host, float *pred_dev,
+                                       void *stream);
+
+/* CVA_0 over outer paths split into ranges (eq. (eq:CVA_portfolio) at i = 0):
+ * cva_cva0_partials writes out3_host = (M, sum of xi0, sum of xi0^2) of one range,
+ * FP64 in a fixed order (synchronises `stream`); cva_cva0_combine (host only) adds
+ * n_parts such triples (host double [n_parts][3]) in their order and writes
+ * out2_host = (CVA_0, its Monte Carlo standard error), by the formula of cva_cva0. */
+CVA_API cva_status cva_cva0_partials(const float *xi0_dev, uint64_t M, double *out3_host, void *stream);
+CVA_API cva_status cva_cva0_combine(const double *parts_host, int n_parts, double *out2_host);
 
 /* The same regression for every date i = 1..n-1 of a simulation and portfolio
  * pf, all dates in one grouped launch: features of date i, targets of date i.

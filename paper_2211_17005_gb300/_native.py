@@ -17,7 +17,7 @@ _lib = None
 CVA_OK, CVA_EINVAL, CVA_ENOMEM, CVA_ECUDA, CVA_ETIMEOUT, CVA_ENOTSUP, CVA_ENUMERIC = range(7)
 STATUS_NAMES = {0: "CVA_OK", 1: "CVA_EINVAL", 2: "CVA_ENOMEM", 3: "CVA_ECUDA", 4: "CVA_ETIMEOUT",
                 5: "CVA_ENOTSUP", 6: "CVA_ENUMERIC"}
-KEEP_DEFAULTS, KEEP_EXPOSURES, PROFILE = 1, 2, 4
+KEEP_DEFAULTS, KEEP_EXPOSURES, PROFILE, GENERIC_KERNELS = 1, 2, 4, 8
 VIEW_FEATURES, VIEW_TARGETS, VIEW_DISCOUNT, VIEW_THRESHOLD, VIEW_EXPOSURE, VIEW_MTM, VIEW_DEFAULTS = range(7)
 BASIS_LINEAR, BASIS_POLY2 = 0, 1
 
@@ -67,6 +67,14 @@ SIGNATURES = {
     "cva_cva0": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _dp, ctypes.c_void_p]),
     "cva_regress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
                                    ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_void_p]),
+    "cva_regress_partial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_void_p]),
+    "cva_regress_solve": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "cva_regress_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                           ctypes.c_void_p, _dp, ctypes.c_void_p, ctypes.c_void_p]),
+    "cva_cva0_partials": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _dp, ctypes.c_void_p]),
+    "cva_cva0_combine": (ctypes.c_int, [_dp, ctypes.c_int, _dp]),
     "cva_regress_all": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, _dp,
                                        ctypes.c_void_p]),
     "cva_regress_portfolios": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_void_p]),

@@ -66,14 +66,15 @@ class Simulation:
     model, grid and up to 6 portfolios; device buffers are allocated once."""
 
     def __init__(self, model, portfolios: Sequence, grid, M: int, N: int,
-                 keep_defaults: bool = False, keep_exposures: bool = False, profile: bool = False):
+                 keep_defaults: bool = False, keep_exposures: bool = False, profile: bool = False,
+                 generic: bool = False):
         L = N_lib()
         keep = _Keep()
         md = model_desc(model, keep)
         pds = (nat.PortfolioDesc * len(portfolios))(*[portfolio_desc(p, keep) for p in portfolios])
         gd = nat.GridDesc(float(grid.horizon), int(grid.n_steps), int(grid.substeps))
         flags = ((nat.KEEP_DEFAULTS if keep_defaults else 0) | (nat.KEEP_EXPOSURES if keep_exposures else 0)
-                 | (nat.PROFILE if profile else 0))
+                 | (nat.PROFILE if profile else 0) | (nat.GENERIC_KERNELS if generic else 0))
         h = ctypes.c_void_p()
         nat.check(L.cva_sim_create(ctypes.byref(md), pds, len(portfolios), ctypes.byref(gd), int(M), int(N),
                                  flags, ctypes.byref(h)), "cva_sim_create")

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libcva.so")
-SOURCES = ["api.cu", "sim.cu", "reduce.cu", "lsq.cu", "alive.cu", "mlp.cu", "mlp_wide.cu", "outer_small.cu", "outer_paper.cu", "outer_batched.cu", "peaks.cu"]
+SOURCES = ["api.cu", "sim.cu", "reduce.cu", "lsq.cu", "alive.cu", "mlp.cu", "mlp_wide.cu", "outer_small.cu", "outer_paper.cu", "outer_batched.cu", "outer_generic.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -199,14 +199,20 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
             G = std::max(G, (int)d.n_periods[s]);
         }
     }
+    // the compiled instantiation of this shape if there is one (and its stochastic
+    // intensities are the first counterparties), else the run-time-shape kernels
+    bool cir_first = true;
+    for (int c = 0; c < C; ++c)
+        if ((model->cir_nu[c] > 0.0) != (c < CS)) cir_first = false;
     int Ginst = 0;
-    if (!outer_supported(E, C, CS, G, n_pf, &Ginst))
-        return fail(CVA_ENOTSUP, "no compiled outer kernel for E=" + std::to_string(E) + " C=" +
-                                     std::to_string(C) + " stochastic C=" + std::to_string(CS) +
-                                     " portfolios=" + std::to_string(n_pf));
-    if ((size_t)n_pf * C * E * Ginst > (size_t)kMaxW) return fail(CVA_ENOTSUP, "portfolio weights exceed constant memory");
+    const bool generic = (flags & CVA_GENERIC_KERNELS) || !cir_first || !outer_supported(E, C, CS, G, n_pf, &Ginst);
+    if (generic) Ginst = G;
+    if ((size_t)n_pf * C * E * Ginst > (size_t)kMaxW)
+        return fail(CVA_ENOTSUP, "portfolio weights exceed constant memory: n_pf C E (longest schedule) must be <= " +
+                                     std::to_string(kMaxW));
 
     Sim *s = new Sim();
+    s->generic = generic;
     s->E = E; s->C = C; s->CS = CS; s->F = F; s->G = G; s->Ginst = Ginst; s->NPF = n_pf;
     s->n = n; s->S = S; s->ppp = (int)ppp; s->M = M; s->N = N; s->flags = flags;
     s->horizon = grid->horizon; s->delta = delta;
@@ -232,8 +238,9 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
         k.lchi0[e] = e ? (float)std::log(model->fx0[e]) : 0.f;
         k.fix0_m1[e] = (float)std::expm1(model->curve[e] * delta);   // 1/ZC_0(delta) - 1
     }
-    for (int c = 0; c < C; ++c) {
+    for (int c = 0, pos = 2 * E - 1; c < C; ++c) {
         const bool stoch = model->cir_nu[c] > 0.0;
+        k.gpos[c] = stoch ? pos++ : -1;
         k.cir_kds[c] = stoch ? (float)(model->cir_kappa[c] * ds) : 0.f;
         k.cir_ktds[c] = stoch ? (float)(model->cir_kappa[c] * model->cir_theta[c] * ds) : 0.f;
         k.cir_nu_sqds[c] = stoch ? (float)(model->cir_nu[c] * std::sqrt(ds)) : 0.f;
@@ -406,6 +413,52 @@ cva_status cva_nested_reference(cva_sim *sim, uint64_t seed, uint64_t k0, int pf
 cva_status cva_relative_rmse(const float *phi_dev, const float *ref_dev, uint64_t M, double *out2, void *stream)
 {
     return relative_rmse_fp64(phi_dev, ref_dev, M, out2, reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_cva0_partials(const float *xi0_dev, uint64_t M, double *out3_host, void *stream)
+{
+    if (!out3_host) return fail(CVA_EINVAL, "cva0_partials: NULL output");
+    double h[2];
+    cva_status r = sums_fp64(xi0_dev, M, h, reinterpret_cast<cudaStream_t>(stream));
+    if (r != CVA_OK) return r;
+    out3_host[0] = (double)M;
+    out3_host[1] = h[0];
+    out3_host[2] = h[1];
+    return CVA_OK;
+}
+
+cva_status cva_cva0_combine(const double *parts_host, int n_parts, double *out2_host)
+{
+    if (!parts_host || !out2_host || n_parts < 1) return fail(CVA_EINVAL, "cva0_combine: bad arguments");
+    double m = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = 0; i < n_parts; ++i) {   // in part order
+        m += parts_host[3 * i];
+        s1 += parts_host[3 * i + 1];
+        s2 += parts_host[3 * i + 2];
+    }
+    if (!(m > 0.0)) return fail(CVA_EINVAL, "cva0_combine: no paths");
+    mean_se_from_sums(m, s1, s2, out2_host);
+    return CVA_OK;
+}
+
+cva_status cva_regress_partial(const float *targets_dev, const float *features_dev, int F, uint64_t M, int basis,
+                               const float *centre_dev, double *gram_host, void *stream)
+{
+    return lsq_normal_partial(targets_dev, features_dev, F, M, basis, centre_dev, gram_host,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
+cva_status cva_regress_solve(const double *gram_host, int F, int basis, const double *centre_host,
+                             double *coef_centred_host, double *coef_raw_host, int *dropped_host)
+{
+    return lsq_solve_normal_host(gram_host, F, basis, centre_host, coef_centred_host, coef_raw_host, dropped_host);
+}
+
+cva_status cva_regress_predict(const float *features_dev, int F, uint64_t M, int basis, const float *centre_dev,
+                               const double *coef_centred_host, float *pred_dev, void *stream)
+{
+    return lsq_predict_centred(features_dev, F, M, basis, centre_dev, coef_centred_host, pred_dev,
+                               reinterpret_cast<cudaStream_t>(stream));
 }
 
 cva_status cva_inner_cost_ratio(double t1, uint32_t N1, double t2, uint32_t N2, double *kappa_out)

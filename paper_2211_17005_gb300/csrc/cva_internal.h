@@ -44,6 +44,7 @@ struct SimConsts {
     float fix0_m1[kMaxE];                  // 1/ZC_0(delta) - 1 (first fixing)
     float cir_kds[kMaxC], cir_ktds[kMaxC], cir_nu_sqds[kMaxC];
     float gamma0[kMaxC], lgd[kMaxC];
+    int gpos[kMaxC];                       // state factor of gamma^c (CIR), -1 for a constant intensity
 };
 
 // Date-bucketed portfolio weights, [pf][c][e][g] with compile-time strides
@@ -63,6 +64,7 @@ struct Sim {
     uint64_t M;
     uint32_t N;
     uint32_t flags;
+    bool generic = false;          // the run-time-shape kernels (outer_generic.cu)
     double horizon, delta;
     // host tables
     SimConsts consts;
@@ -193,6 +195,16 @@ cva_status alive_regress(Sim &s, int pf, float *pred_dev, double *coef_host, int
 // CVA_0 reduction (reduce.cu).
 cva_status philox_blocks(const uint32_t *ctr, uint32_t *out, uint64_t n, uint64_t seed, cudaStream_t st);
 cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st);
+cva_status sums_fp64(const float *x, uint64_t M, double *sum2_host, cudaStream_t st);
+void mean_se_from_sums(double M, double s1, double s2, double *out2);
+// Least squares split over path ranges (lsq.cu): the augmented normal matrix of one
+// range with a given centring, its solution on the host, the predictions of a range.
+cva_status lsq_normal_partial(const float *targ, const float *feat, int F, uint64_t M, int basis, const float *centre,
+                              double *gram_host, cudaStream_t st);
+cva_status lsq_solve_normal_host(const double *gram, int F, int basis, const double *centre, double *coef_centred,
+                                 double *coef_raw, int *dropped);
+cva_status lsq_predict_centred(const float *feat, int F, uint64_t M, int basis, const float *centre,
+                               const double *coef_centred_host, float *pred, cudaStream_t st);
 cva_status twin_l2_fp64(const float *phi, const float *xi1, const float *xi2, uint64_t M, double *out2,
                         cudaStream_t st);
 cva_status accumulate_mean(float *acc, const float *x, uint64_t M, int first, int last, int copies, cudaStream_t st);

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <vector>
 
 #include "cva_internal.h"
 
@@ -36,7 +37,14 @@ struct LsqArgs {
     int nt = 1;                 // target columns sharing one normal matrix
     size_t targ_tstride = 0;    // floats between a group's targets
     size_t pred_tstride = 0;    // floats between a group's predictions
+    const float *centre = nullptr;   // [F] (poly2: [1]) centring state; null: path 0 of the group
 };
+
+// the centring state of the basis: the given one, else path 0 of the group's features
+__device__ __forceinline__ float centre_of(const LsqArgs &a, const float *feat, int f)
+{
+    return a.centre ? __ldg(a.centre + f) : __ldg(feat + (size_t)f * a.M);
+}
 
 // value of augmented column `col` at row k (columns m..m+nt-1 are the targets);
 // c0[f] is path 0's value of factor f (the centring of the basis)
@@ -81,7 +89,7 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram(LsqArgs a)
         }
     }
     __shared__ float c0[40];
-    for (int f = tid; f < (a.basis == CVA_BASIS_POLY2 ? 1 : a.F); f += kGramThreads) c0[f] = __ldg(feat + (size_t)f * a.M);
+    for (int f = tid; f < (a.basis == CVA_BASIS_POLY2 ? 1 : a.F); f += kGramThreads) c0[f] = centre_of(a, feat, f);
     double dacc[16];
     float acc[16];
 #pragma unroll
@@ -175,7 +183,7 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
         }
     }
     __shared__ float c0[40];
-    for (int f = tid; f < F; f += kGramThreads) c0[f] = __ldg(feat + (size_t)f * a.M);
+    for (int f = tid; f < F; f += kGramThreads) c0[f] = centre_of(a, feat, f);
     for (int e = tid; e < 2 * TR; e += kGramThreads)       // padding columns stay zero
         for (int c = mA; c < MP; ++c) tiles[e * RS + c] = 0.f;
     __syncthreads();
@@ -361,14 +369,14 @@ __global__ void __launch_bounds__(256) lsq_solve(LsqArgs a)
     double *co = a.coef + ((size_t)g * a.nt + t) * m, *cr = a.coef_raw + ((size_t)g * a.nt + t) * m;
     for (int i = 0; i < m; ++i) co[i] = w[i];
     if (a.basis == CVA_BASIS_POLY2) {
-        const double c = (double)feat[0];
+        const double c = (double)centre_of(a, feat, 0);
         cr[0] = w[0] - w[1] * c + w[2] * c * c;
         cr[1] = w[1] - 2.0 * w[2] * c;
         cr[2] = w[2];
     } else {
         double w0 = w[0];
         for (int f = 0; f < a.F; ++f) {
-            const double c = (double)feat[(size_t)f * a.M];
+            const double c = (double)centre_of(a, feat, f);
             w0 -= w[1 + f] * c;
             cr[1 + f] = w[1 + f];
         }
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(256) lsq_predict(LsqArgs a)
     const float *feat = a.feat0 + (size_t)g * a.feat_stride;
     for (int i = threadIdx.x; i < nt * m; i += blockDim.x) cs[i] = (float)co[i];
     const int nf = a.basis == CVA_BASIS_POLY2 ? 1 : a.F;
-    for (int f = threadIdx.x; f < nf; f += blockDim.x) f0[f] = __ldg(feat + (size_t)f * a.M);
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) f0[f] = centre_of(a, feat, f);
     __syncthreads();
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.M) return;
@@ -427,7 +435,7 @@ __global__ void __launch_bounds__(256) lsq_predict4(LsqArgs a)
     const double *co = a.coef + (size_t)g * nt * m;
     const float *feat = a.feat0 + (size_t)g * a.feat_stride;
     for (int i = threadIdx.x; i < nt * m; i += blockDim.x) cs[i] = (float)co[i];
-    for (int f = threadIdx.x; f < a.F; f += blockDim.x) f0[f] = __ldg(feat + (size_t)f * a.M);
+    for (int f = threadIdx.x; f < a.F; f += blockDim.x) f0[f] = centre_of(a, feat, f);
     __syncthreads();
     const uint32_t k = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
     if (k >= a.M) return;
@@ -626,6 +634,224 @@ cva_status lsq_grouped_strided(const float *feat0, size_t feat_stride, const flo
     if (r != CVA_OK) return r;
     CVA_CUDA_TRY(cudaEventRecord(sc.done, st));
     return CVA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Least squares split over path ranges (one range per process and GPU). Every
+// range accumulates its augmented normal matrix with the same centring (a state
+// vector all ranges agree on), the host sums the ranges' matrices in a fixed order
+// and solves once; each range then predicts its own paths. The sum over ranges is
+// the normal matrix of all paths, so the fit is the one of the whole sample.
+
+// the library's regression scratch of the current device, grown to `need` doubles
+// (the previous user of a larger one has finished: callers synchronise)
+static cva_status lsq_scratch_get(size_t need, cudaStream_t st, double **out)
+{
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_lsq_mu);
+    LsqScratch &sc = g_lsq[dev];
+    if (!sc.done) CVA_CUDA_TRY(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming));
+    else CVA_CUDA_TRY(cudaStreamWaitEvent(st, sc.done, 0));
+    if (sc.cap < need) {
+        if (sc.buf) {
+            CVA_CUDA_TRY(cudaEventSynchronize(sc.done));
+            cudaFree(sc.buf);
+            sc.buf = nullptr;
+            sc.cap = 0;
+        }
+        if (cudaMalloc(&sc.buf, need * sizeof(double)) != cudaSuccess)
+            return fail(CVA_ENOMEM, "regress: scratch allocation failed");
+        sc.cap = need;
+    }
+    *out = sc.buf;
+    return CVA_OK;
+}
+
+static cva_status lsq_scratch_release(cudaStream_t st)
+{
+    int dev = 0;
+    CVA_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_lsq_mu);
+    CVA_CUDA_TRY(cudaEventRecord(g_lsq[dev].done, st));
+    return CVA_OK;
+}
+
+static cva_status lsq_split_check(const float *feat, uint64_t M, int F, int basis, const float *centre)
+{
+    if (!feat || !centre || M == 0) return fail(CVA_EINVAL, "regress: bad arguments");
+    if (M > 0x7fffffffull) return fail(CVA_EINVAL, "regress: M too large");
+    if (basis != CVA_BASIS_LINEAR && basis != CVA_BASIS_POLY2) return fail(CVA_EINVAL, "regress: unknown basis");
+    if (F < 1) return fail(CVA_EINVAL, "regress: need one factor");
+    if (basis == CVA_BASIS_LINEAR && F + 2 > 32) return fail(CVA_ENOTSUP, "regress: linear basis supports 1 <= F <= 30");
+    return CVA_OK;
+}
+
+cva_status lsq_normal_partial(const float *targ, const float *feat, int F, uint64_t M, int basis, const float *centre,
+                              double *gram_host, cudaStream_t st)
+{
+    cva_status r = lsq_split_check(feat, M, F, basis, centre);
+    if (r != CVA_OK) return r;
+    if (!targ || !gram_host) return fail(CVA_EINVAL, "regress: bad arguments");
+    const int m = (basis == CVA_BASIS_POLY2) ? 3 : F + 1, mA = m + 1;
+    const int MP = lsq_width(m, 1), NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2;
+    const uint64_t chunks = lsq_chunks(M, 1, 2432);
+    double *part = nullptr;
+    r = lsq_scratch_get((size_t)(chunks + 1) * NUT * 16, st, &part);
+    if (r != CVA_OK) return r;
+    LsqArgs a;
+    a.feat0 = feat;
+    a.feat_stride = (size_t)F * M;
+    a.targ0 = targ;
+    a.targ_stride = M;
+    a.pred0 = nullptr;
+    a.pred_stride = M;
+    a.F = F;
+    a.m = m;
+    a.basis = basis;
+    a.chunks = (int)chunks;
+    a.M = (uint32_t)M;
+    a.rows_per_chunk = (uint32_t)((M + chunks - 1) / chunks);
+    a.part = part;
+    a.coef = a.coef_raw = nullptr;
+    a.status = nullptr;
+    a.centre = centre;
+    const dim3 ggrid((unsigned)chunks, 1u);
+    switch (MP) {
+    case 4: r = launch_gram<4, 1024>(a, ggrid, st); break;
+    case 12: r = launch_gram<12, 512>(a, ggrid, st); break;
+    default: r = launch_gram<32, 256>(a, ggrid, st); break;
+    }
+    if (r == CVA_OK) r = sum_columns_fp64(part, (int)chunks, NUT * 16, part + (size_t)chunks * NUT * 16, st);
+    std::vector<double> blocks((size_t)NUT * 16);
+    if (r == CVA_OK) {
+        cudaError_t e = cudaMemcpyAsync(blocks.data(), part + (size_t)chunks * NUT * 16, sizeof(double) * NUT * 16,
+                                        cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) r = cuda_fail(e, "regress: copy of the normal matrix");
+    }
+    const cva_status rr = lsq_scratch_release(st);
+    if (r != CVA_OK) return r;
+    if (rr != CVA_OK) return rr;
+    // the upper-triangular 4x4 blocks -> the dense symmetric (m+1) x (m+1) matrix
+    for (int e = 0; e < NUT * 16; ++e) {
+        int t = e / 16, bi = 0;
+        while (t >= NBLK - bi) {
+            t -= NBLK - bi;
+            ++bi;
+        }
+        const int bj = bi + t, i = 4 * bi + (e % 16) / 4, j = 4 * bj + e % 4;
+        if (i < mA && j < mA) {
+            gram_host[(size_t)i * mA + j] = blocks[e];
+            gram_host[(size_t)j * mA + i] = blocks[e];
+        }
+    }
+    return CVA_OK;
+}
+
+// The solve of lsq_solve on the host: Jacobi scaling, Cholesky factorisation of the
+// scaled normal matrix with vanishing pivots dropped (coefficient 0), the two
+// triangular solves; coefficients in the centred basis and in the raw one.
+cva_status lsq_solve_normal_host(const double *gram, int F, int basis, const double *centre, double *coef_centred,
+                                 double *coef_raw, int *dropped)
+{
+    if (!gram || !centre || F < 1 || (basis != CVA_BASIS_LINEAR && basis != CVA_BASIS_POLY2))
+        return fail(CVA_EINVAL, "regress: bad arguments");
+    const int m = (basis == CVA_BASIS_POLY2) ? 3 : F + 1, mA = m + 1;
+    std::vector<double> A((size_t)m * m), sc(m), y(m), w(m);
+    std::vector<int> drop(m);
+    for (int r = 0; r < m; ++r) {
+        const double d = gram[(size_t)r * mA + r];
+        drop[r] = !(d > 0.0);
+        sc[r] = drop[r] ? 0.0 : 1.0 / sqrt(d);
+    }
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c <= r; ++c) A[(size_t)r * m + c] = gram[(size_t)r * mA + c] * sc[r] * sc[c];
+    for (int j = 0; j < m; ++j) {
+        const double s = A[(size_t)j * m + j];
+        if (drop[j] || !(s > 1e-12)) {
+            drop[j] = 1;
+            A[(size_t)j * m + j] = 1.0;
+        } else {
+            A[(size_t)j * m + j] = sqrt(s);
+        }
+        const double inv = drop[j] ? 0.0 : 1.0 / A[(size_t)j * m + j];
+        for (int r = j + 1; r < m; ++r) A[(size_t)r * m + j] *= inv;
+        for (int r = j + 1; r < m; ++r)
+            for (int c = j + 1; c <= r; ++c) A[(size_t)r * m + c] -= A[(size_t)r * m + j] * A[(size_t)c * m + j];
+    }
+    int nd = 0;
+    for (int r = 0; r < m; ++r) nd += drop[r];
+    for (int i = 0; i < m; ++i) {               // L y = D^{-1/2} b
+        double s = gram[(size_t)i * mA + m] * sc[i];
+        for (int p = 0; p < i; ++p) s -= A[(size_t)i * m + p] * y[p];
+        y[i] = drop[i] ? 0.0 : s / A[(size_t)i * m + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {         // L^T z = y, w = D^{-1/2} z
+        double s = y[i];
+        for (int p = i + 1; p < m; ++p) s -= A[(size_t)p * m + i] * w[p];
+        w[i] = drop[i] ? 0.0 : s / A[(size_t)i * m + i];
+    }
+    for (int i = 0; i < m; ++i) w[i] *= sc[i];
+    if (coef_centred)
+        for (int i = 0; i < m; ++i) coef_centred[i] = w[i];
+    if (coef_raw) {
+        if (basis == CVA_BASIS_POLY2) {
+            const double c = centre[0];
+            coef_raw[0] = w[0] - w[1] * c + w[2] * c * c;
+            coef_raw[1] = w[1] - 2.0 * w[2] * c;
+            coef_raw[2] = w[2];
+        } else {
+            double w0 = w[0];
+            for (int f = 0; f < F; ++f) {
+                w0 -= w[1 + f] * centre[f];
+                coef_raw[1 + f] = w[1 + f];
+            }
+            coef_raw[0] = w0;
+        }
+    }
+    if (dropped) *dropped = nd;
+    return CVA_OK;
+}
+
+cva_status lsq_predict_centred(const float *feat, int F, uint64_t M, int basis, const float *centre,
+                               const double *coef_centred_host, float *pred, cudaStream_t st)
+{
+    cva_status r = lsq_split_check(feat, M, F, basis, centre);
+    if (r != CVA_OK) return r;
+    if (!coef_centred_host || !pred) return fail(CVA_EINVAL, "regress: bad arguments");
+    const int m = (basis == CVA_BASIS_POLY2) ? 3 : F + 1;
+    double *coef = nullptr;
+    r = lsq_scratch_get((size_t)m, st, &coef);
+    if (r != CVA_OK) return r;
+    cudaError_t e = cudaMemcpyAsync(coef, coef_centred_host, sizeof(double) * m, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "regress: coefficients to the device");
+    LsqArgs a;
+    a.feat0 = feat;
+    a.feat_stride = (size_t)F * M;
+    a.targ0 = nullptr;
+    a.targ_stride = M;
+    a.pred0 = pred;
+    a.pred_stride = M;
+    a.F = F;
+    a.m = m;
+    a.basis = basis;
+    a.chunks = 1;
+    a.M = (uint32_t)M;
+    a.rows_per_chunk = (uint32_t)M;
+    a.part = nullptr;
+    a.coef = coef;
+    a.coef_raw = nullptr;
+    a.status = nullptr;
+    a.centre = centre;
+    r = lsq_predict_launch(a, 1, st);
+    // the host coefficients are read by the copy above before the call returns
+    e = cudaStreamSynchronize(st);
+    const cva_status rr = lsq_scratch_release(st);
+    if (r != CVA_OK) return r;
+    if (e != cudaSuccess) return cuda_fail(e, "regress: predictions");
+    return rr;
 }
 
 // ---------------------------------------------------------------------------

@@ -249,18 +249,19 @@ __global__ void __launch_bounds__(256) price_kernel(OuterArgs a)
         }
 }
 
-// Every portfolio of the simulation priced by one thread, for two outer paths of a
+// Every portfolio of the simulation priced by one thread, for PT outer paths of a
 // pricing date at a time, with the date-bucketed weights staged once per block in
 // shared memory: each (path, date) computes its bond prices once for all
-// portfolios, and each weight, read with one broadcast load, feeds both paths. The
-// FMA order per path is price_kernel's, so the outputs are the same bits.
-// Block: 128 threads = paths [256 b, 256 b + 256) (thread t takes t and t + 128),
-// dates [DPB y, DPB y + DPB). Shared memory: NPF C E GP float2 (wA, wK) pairs,
-// GP = G rounded up to even so that every row of pairs is 16-byte aligned.
-template <int E, int C, int CS, int G, int NPF>
-__global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_per_block)
+// portfolios, and each weight, read with one broadcast load, feeds the thread's PT
+// paths. The state of the next economy is requested while the current one is
+// priced. The FMA order per path is price_kernel's, so the outputs are the same bits.
+// Block: 256 / PT threads = paths [256 b, 256 b + 256) (thread t takes t + u 256/PT,
+// u < PT), dates [dpb y, dpb y + dpb). Shared memory: NPF C E GP float2 (wA, wK)
+// pairs, GP = G rounded up to even so that every row of pairs is 16-byte aligned.
+template <int E, int C, int CS, int G, int NPF, int PT>
+__global__ void __launch_bounds__(256 / PT, 2) price_smem_kernel(OuterArgs a, int dates_per_block)
 {
-    constexpr int F = 2 * E - 1 + CS, GP = (G + 1) / 2 * 2, NPAIR = NPF * C * E * GP;
+    constexpr int F = 2 * E - 1 + CS, GP = (G + 1) / 2 * 2, NPAIR = NPF * C * E * GP, NT = 256 / PT;
     extern __shared__ float4 price_smem[];
     float2 *wsm = reinterpret_cast<float2 *>(price_smem);
     for (int i = threadIdx.x; i < NPAIR; i += blockDim.x) {
@@ -271,10 +272,15 @@ __global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_
     __syncthreads();
     const size_t M = a.M;
     const int n = c_sim.n, ppp = c_sim.ppp;
-    const uint32_t k_a = blockIdx.x * 256u + threadIdx.x, k_b = k_a + 128u;
-    if (k_a >= a.M) return;
-    const bool has_b = k_b < a.M;
-    const uint32_t kk[2] = {k_a, has_b ? k_b : k_a};
+    uint32_t kk[PT];
+    bool has[PT];
+#pragma unroll
+    for (int t = 0; t < PT; ++t) {
+        const uint32_t k = blockIdx.x * 256u + (uint32_t)(t * NT) + threadIdx.x;
+        has[t] = k < a.M;
+        kk[t] = has[t] ? k : (blockIdx.x * 256u + threadIdx.x < a.M ? blockIdx.x * 256u + threadIdx.x : 0u);
+    }
+    if (!has[0]) return;
     const int j0 = (int)blockIdx.y * dates_per_block;
     for (int j = j0; j < j0 + dates_per_block && j <= n; ++j) {
         if (j == 0) {   // no default at t_0: exposures of date 0 are never used
@@ -283,8 +289,8 @@ __global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_
 #pragma unroll
                 for (int c = 0; c < C; ++c)
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        if (t == 1 && !has_b) continue;
+                    for (int t = 0; t < PT; ++t) {
+                        if (!has[t]) continue;
                         const size_t o = ((size_t)(pf * (n + 1)) * C + c) * M + kk[t];
                         a.expo[o] = 0.f;
                         if (a.mtm) a.mtm[o] = 0.f;
@@ -293,10 +299,16 @@ __global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_
         }
         const int p = __ldg(a.date_p + j);          // t_j in (p delta, (p+1) delta]
         const float2 *fx = a.fix + (size_t)p * E;
-        float beta[2], mt[2][NPF][C];
+        const float *fe = a.features + (size_t)j * F * M;
+        const float *ffix = a.features + (size_t)(p * ppp) * F * M;   // state at the last reset
+        float beta[PT], mt[PT][NPF][C];
+        float nre[PT], nfix[PT], nchi[PT];   // the next economy's state, requested one economy ahead
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < PT; ++t) {
             beta[t] = expf(-__ldg(a.disc + (size_t)j * M + kk[t]));
+            nre[t] = __ldg(fe + kk[t]);
+            nfix[t] = __ldg(ffix + kk[t]);
+            nchi[t] = 0.f;
 #pragma unroll
             for (int pf = 0; pf < NPF; ++pf)
 #pragma unroll
@@ -304,17 +316,26 @@ __global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_
         }
 #pragma unroll 1
         for (int e = 0; e < E; ++e) {
+            float re[PT], rfix[PT], lchi[PT];
+#pragma unroll
+            for (int t = 0; t < PT; ++t) {
+                re[t] = nre[t];
+                rfix[t] = nfix[t];
+                lchi[t] = nchi[t];
+                if (e + 1 < E) {
+                    nre[t] = __ldg(fe + (size_t)(e + 1) * M + kk[t]);
+                    nfix[t] = __ldg(ffix + (size_t)(e + 1) * M + kk[t]);
+                    nchi[t] = __ldg(fe + (size_t)(E + e) * M + kk[t]);   // log chi^{e+1}
+                }
+            }
             const float2 f2 = __ldg(fx + e);
             const float4 *tab = a.zc + ((size_t)j * E + e) * G;
             const float4 tp = __ldg(tab + (p < G ? p : G - 1));   // p >= G: every swap has matured
-            float Z[2][G], D[2][G], chi[2];
+            float Z[PT][G], D[PT][G], chi[PT];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const float *fe = a.features + (size_t)j * F * M + kk[t];
-                const float *ffix = a.features + (size_t)(p * ppp) * F * M + kk[t];
-                const float re = __ldg(fe + (size_t)e * M);
-                const float fixm1 = expm1f(fmaf(f2.y, __ldg(ffix + (size_t)e * M), -f2.x));
-                const float z_first = expf(fmaf(-tp.y, re, tp.x));
+            for (int t = 0; t < PT; ++t) {
+                const float fixm1 = expm1f(fmaf(f2.y, rfix[t], -f2.x));
+                const float z_first = expf(fmaf(-tp.y, re[t], tp.x));
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
                     if (g < p) {
@@ -326,12 +347,12 @@ __global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_
                     } else {
                         const float4 t4 = __ldg(tab + g);
                         const float zp = Z[t][g > 0 ? g - 1 : 0];
-                        const float em = expm1_small(fmaf(-t4.w, re, t4.z));
+                        const float em = expm1_small(fmaf(-t4.w, re[t], t4.z));
                         D[t][g] = -zp * em;
                         Z[t][g] = fmaf(zp, em, zp);
                     }
                 }
-                chi[t] = (e == 0) ? 1.f : expf(__ldg(fe + (size_t)(E - 1 + (e > 0 ? e : 1)) * M));
+                chi[t] = (e == 0) ? 1.f : expf(lchi[t]);
             }
 #pragma unroll
             for (int pf = 0; pf < NPF; ++pf)
@@ -348,7 +369,7 @@ __global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_
                         wk[2 * q + 1] = w4.w;
                     }
 #pragma unroll
-                    for (int t = 0; t < 2; ++t) {
+                    for (int t = 0; t < PT; ++t) {
                         float acc = 0.f;
 #pragma unroll
                         for (int h = 0; h < G; ++h) acc = fmaf(wa[h], D[t][h], acc);
@@ -359,8 +380,8 @@ __global__ void __launch_bounds__(128) price_smem_kernel(OuterArgs a, int dates_
                 }
         }
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            if (t == 1 && !has_b) continue;
+        for (int t = 0; t < PT; ++t) {
+            if (!has[t]) continue;
 #pragma unroll
             for (int pf = 0; pf < NPF; ++pf)
 #pragma unroll
@@ -449,9 +470,12 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
     if (s.tune_price_pf == 0) {   // every portfolio per thread, weights in shared memory
         constexpr int GP = (G + 1) / 2 * 2;
+        constexpr size_t smem = (size_t)NPF * C * E * GP * sizeof(float2);
+        static_assert(smem <= 48 * 1024, "portfolio weights exceed the default shared-memory limit");
         const int dpb = 8;
         const dim3 sgrid((args.M + 255u) / 256u, (unsigned)((s.n + 1 + dpb - 1) / dpb));
-        price_smem_kernel<E, C, CS, G, NPF><<<sgrid, 128, (size_t)NPF * C * E * GP * sizeof(float2), st>>>(args, dpb);
+        if (pb == 256) price_smem_kernel<E, C, CS, G, NPF, 1><<<sgrid, 256, smem, st>>>(args, dpb);
+        else price_smem_kernel<E, C, CS, G, NPF, 2><<<sgrid, 128, smem, st>>>(args, dpb);
         CVA_CUDA_TRY(cudaGetLastError());
         if (!capturing) CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
         return CVA_OK;

@@ -216,9 +216,10 @@ cva_status twin_l2_fp64(const float *phi, const float *xi1, const float *xi2, ui
     return CVA_OK;
 }
 
-cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st)
+// FP64 sums (sum x, sum x^2) of M floats, two stages in a fixed order: bit-reproducible.
+cva_status sums_fp64(const float *x, uint64_t M, double *sum2_host, cudaStream_t st)
 {
-    if (!x || !out2 || M == 0) return fail(CVA_EINVAL, "cva0: null pointer or M == 0");
+    if (!x || !sum2_host || M == 0) return fail(CVA_EINVAL, "cva0: null pointer or M == 0");
     int dev = 0;
     CVA_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
@@ -235,11 +236,27 @@ cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st)
     double2 h;
     CVA_CUDA_TRY(cudaMemcpyAsync(&h, part + kRedBlocks, sizeof(double2), cudaMemcpyDeviceToHost, st));
     CVA_CUDA_TRY(cudaStreamSynchronize(st));
-    const double mean = h.x / (double)M;
-    double var = (M > 1) ? (h.y - (double)M * mean * mean) / (double)(M - 1) : 0.0;
+    sum2_host[0] = h.x;
+    sum2_host[1] = h.y;
+    return CVA_OK;
+}
+
+// mean and Monte Carlo standard error from (count, sum x, sum x^2)
+void mean_se_from_sums(double M, double s1, double s2, double *out2)
+{
+    const double mean = s1 / M;
+    double var = (M > 1.0) ? (s2 - M * mean * mean) / (M - 1.0) : 0.0;
     if (var < 0.0) var = 0.0;
     out2[0] = mean;
-    out2[1] = sqrt(var / (double)M);
+    out2[1] = sqrt(var / M);
+}
+
+cva_status mean_fp64(const float *x, uint64_t M, double *out2, cudaStream_t st)
+{
+    double h[2];
+    cva_status r = sums_fp64(x, M, h, st);
+    if (r != CVA_OK) return r;
+    mean_se_from_sums((double)M, h[0], h[1], out2);
     return CVA_OK;
 }
 

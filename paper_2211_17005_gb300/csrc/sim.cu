@@ -249,14 +249,13 @@ cva_status launch_oversim(const Sim &s, int pf, const float *pred, uint64_t seed
     a.disc = s.d_disc;
     a.pred = pred;
     a.part = part;
-    switch (s.C) {
-    case 1: oversim_kernel<1><<<blocks, 256, 0, st>>>(a); break;
-    case 2: oversim_kernel<2><<<blocks, 256, 0, st>>>(a); break;
-    case 4: oversim_kernel<4><<<blocks, 256, 0, st>>>(a); break;
-    case 8: oversim_kernel<8><<<blocks, 256, 0, st>>>(a); break;
-    case 16: oversim_kernel<16><<<blocks, 256, 0, st>>>(a); break;
-    default: return fail(CVA_ENOTSUP, "oversimulation statistics compiled for C in {1, 2, 4, 8, 16}");
-    }
+    static constexpr void (*by_c[kMaxC])(OversimArgs) = {
+        oversim_kernel<1>,  oversim_kernel<2>,  oversim_kernel<3>,  oversim_kernel<4>,
+        oversim_kernel<5>,  oversim_kernel<6>,  oversim_kernel<7>,  oversim_kernel<8>,
+        oversim_kernel<9>,  oversim_kernel<10>, oversim_kernel<11>, oversim_kernel<12>,
+        oversim_kernel<13>, oversim_kernel<14>, oversim_kernel<15>, oversim_kernel<16>};
+    if (s.C < 1 || s.C > kMaxC) return fail(CVA_ENOTSUP, "oversimulation statistics: 1 <= C <= 16");
+    by_c[s.C - 1]<<<blocks, 256, 0, st>>>(a);
     CVA_CUDA_TRY(cudaGetLastError());
     return CVA_OK;
 }
@@ -265,6 +264,7 @@ cva_status launch_oversim(const Sim &s, int pf, const float *pred, uint64_t seed
 int outer_insts_small(const OuterInst **out);
 int outer_insts_paper(const OuterInst **out);
 int outer_insts_batched(const OuterInst **out);
+int outer_insts_generic(const OuterInst **out);
 
 static const OuterInst *find_outer(int E, int C, int CS, int G, int NPF)
 {
@@ -291,7 +291,8 @@ bool outer_supported(int E, int C, int CS, int G, int NPF, int *Ginst)
 
 void forget_const_owner(const Sim *s)
 {
-    int (*tables[])(const OuterInst **) = {outer_insts_small, outer_insts_paper, outer_insts_batched};
+    int (*tables[])(const OuterInst **) = {outer_insts_small, outer_insts_paper, outer_insts_batched,
+                                           outer_insts_generic};
     for (auto tab : tables) {
         const OuterInst *p = nullptr;
         const int cnt = tab(&p);
@@ -299,8 +300,16 @@ void forget_const_owner(const Sim *s)
     }
 }
 
+static const OuterInst *generic_outer()
+{
+    const OuterInst *p = nullptr;
+    outer_insts_generic(&p);
+    return p;
+}
+
 cva_status launch_adjoint(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st)
 {
+    if (s.generic) return fail(CVA_ENOTSUP, "no adjoint kernel for this model shape (compiled shapes only)");
     const OuterInst *o = find_outer(s.E, s.C, s.CS, s.G, s.NPF);
     if (!o || o->G != s.Ginst || !o->adjoint) return fail(CVA_ENOTSUP, "no adjoint kernel for this model shape");
     return o->adjoint(s, b, seed, k0, M, st);
@@ -308,6 +317,7 @@ cva_status launch_adjoint(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k
 
 cva_status launch_outer(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
 {
+    if (s.generic) return generic_outer()->launch(s, seed, k0, st);
     const OuterInst *o = find_outer(s.E, s.C, s.CS, s.G, s.NPF);
     if (!o || o->G != s.Ginst) return fail(CVA_ENOTSUP, "no outer kernel for this model shape");
     return o->launch(s, seed, k0, st);
@@ -350,15 +360,13 @@ cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.targets = s.d_targets;
     args.idx = s.d_idx;
     const size_t smem = inner_smem(P, s.C, s.n);
-    cudaError_t e;
-    switch (s.C) {
-    case 1: e = launch_inner_t<1>(args, smem, st); break;
-    case 2: e = launch_inner_t<2>(args, smem, st); break;
-    case 4: e = launch_inner_t<4>(args, smem, st); break;
-    case 8: e = launch_inner_t<8>(args, smem, st); break;
-    case 16: e = launch_inner_t<16>(args, smem, st); break;
-    default: return fail(CVA_ENOTSUP, "inner kernel compiled for C in {1, 2, 4, 8, 16}");
-    }
+    static constexpr cudaError_t (*by_c[kMaxC])(const InnerArgs &, size_t, cudaStream_t) = {
+        launch_inner_t<1>,  launch_inner_t<2>,  launch_inner_t<3>,  launch_inner_t<4>,
+        launch_inner_t<5>,  launch_inner_t<6>,  launch_inner_t<7>,  launch_inner_t<8>,
+        launch_inner_t<9>,  launch_inner_t<10>, launch_inner_t<11>, launch_inner_t<12>,
+        launch_inner_t<13>, launch_inner_t<14>, launch_inner_t<15>, launch_inner_t<16>};
+    if (s.C < 1 || s.C > kMaxC) return fail(CVA_ENOTSUP, "inner kernel: 1 <= C <= 16");
+    const cudaError_t e = by_c[s.C - 1](args, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "inner_kernel launch");
     return CVA_OK;
 }

@@ -20,6 +20,11 @@ Workload recipes (Sec. 4.3 of the paper describes the case study: 10 economies,
 * ``precision`` the ``paper`` model at M=2^20, N=128, MLP 27->128->128->1.
 * ``batched``   the ``paper`` model with 6 portfolios (50..2000 swaps), 120 steps over
                 10y, M=2^20, N=256, linear least squares on [1, Y_t].
+* ``mixed``     a shape with no compiled instantiation: 3 economies (paper ranges), 5
+                counterparties with constant and CIR intensities interleaved (nu = 0,
+                0.05, 0, 0.05, 0.05; the constant ones gamma = 0.02, 0.04), 4
+                portfolios of 20, 60, 150, 300 swaps, 40 steps over 10y (quarterly
+                pricing, annual resets), M=4096, N=16, linear least squares.
 
 Swap terms: notional ~ LogNormal(0, 0.5); payer (omega=+1) or receiver (-1) with
 probability 1/2; currency and counterparty uniform; maturity U[lo, hi] years rounded
@@ -153,6 +158,24 @@ def paper_model(rng: np.random.Generator, E: int = 10, C: int = 8) -> Model:
                  recovery=np.full(C, 0.4), corr=corr, corr_shrink=lam)
 
 
+def mixed_model(rng: np.random.Generator) -> Model:
+    """3 economies, 5 counterparties: constant intensities at 0 and 2, CIR at 1, 3, 4."""
+    E, C = 3, 5
+    hw_a = rng.uniform(0.05, 0.2, size=E)
+    hw_sigma = rng.uniform(0.005, 0.015, size=E)
+    curve = rng.uniform(0.01, 0.03, size=E)
+    fx_vol = np.concatenate([[0.0], rng.uniform(0.05, 0.15, size=E - 1)])
+    theta = rng.uniform(0.01, 0.05, size=C)
+    stoch = np.array([False, True, False, True, True])
+    const = np.array([0.02, 0.0, 0.04, 0.0, 0.0])
+    F = E + (E - 1) + int(stoch.sum())
+    corr, lam = _shrunk_correlation(rng, F)
+    return Model(E=E, C=C, hw_a=hw_a, hw_sigma=hw_sigma, curve=curve, fx_vol=fx_vol, fx0=np.ones(E),
+                 cir_kappa=np.where(stoch, 0.5, 0.0), cir_theta=np.where(stoch, theta, const),
+                 cir_nu=np.where(stoch, 0.05, 0.0), gamma0=np.where(stoch, theta, const),
+                 recovery=np.full(C, 0.4), corr=corr, corr_shrink=lam)
+
+
 def make(name: str, M: Optional[int] = None, N: Optional[int] = None,
          n_steps: Optional[int] = None, substeps: int = 1, seed: int = 1,
          n_swaps: Optional[int] = None) -> Workload:
@@ -184,6 +207,12 @@ def make(name: str, M: Optional[int] = None, N: Optional[int] = None,
         grid = Grid(10.0, n_steps or 120, substeps)
         return Workload(name, model, pfs, grid, M or (1 << 20), N or 256, "lsq-linear",
                         seed=seed)
+    if name == "mixed":
+        rng = np.random.default_rng(GENERATOR_SEED + 3)
+        model = mixed_model(rng)
+        pfs = [_swaps(rng, n_swaps or s, model.E, model.C, 1.0, 10.0) for s in (20, 60, 150, 300)]
+        grid = Grid(10.0, n_steps or 40, substeps)
+        return Workload(name, model, pfs, grid, M or 4096, N or 16, "lsq-linear", seed=seed)
     raise ValueError(f"unknown workload {name!r}")
 
 
