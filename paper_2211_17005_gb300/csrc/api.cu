@@ -738,7 +738,9 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
         // the first pass needs valid outputs of the earlier kernels: simulate once
         cva_status r = cva_simulate(sim, seed, 0, stream);
         if (r != CVA_OK) return r;
-        for (int w = 0; w < 5; ++w) {
+        // the pricing form (portfolios per block) before its block size: the best block
+        // size differs between the constant-memory and the shared-memory forms
+        for (int w : {0, 4, 1, 2, 3}) {
             float tb = 1e30f;
             for (int v : cand[w]) {
                 const float t = measure(w, v);

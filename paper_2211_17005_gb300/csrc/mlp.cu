@@ -437,12 +437,11 @@ struct Net {
         return mma([&] { gemm_rows(dcol(), offB(), 0, L::sW2, U, U, false); });
     }
 
-    // forward + backward of one tile; weight gradients accumulate in this slot's DW
-    __device__ bool train_tile(const TrainArgs &a, const CUtensorMap *tm, bool first, float inv_batch, bool has_next,
-                               uint32_t next_path, float *gsl)
+    // forward + backward of one tile whose inputs stage_x has placed (target y, staging
+    // status in_ok); weight gradients accumulate in this slot's DW
+    __device__ bool train_tile(const TrainArgs &a, const CUtensorMap *tm, float y, bool in_ok, bool first,
+                               float inv_batch, bool has_next, uint32_t next_path, float *gsl)
     {
-        float y;
-        const bool in_ok = stage_x(y);
         uint32_t m1[U / 32];
         if (!forward12(m1, in_ok, [&] {
                 if (has_next) prefetch(tm, a.targ, a.F, next_path);
@@ -614,14 +613,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
     const uint32_t xbar_part = umma::smem_u32(&s_xbar[0]), xbar_par = umma::smem_u32(&s_xbar[1]);
     uint32_t ph_part = 0, ph_par = 0;
 
-    bool ok = true;
+    // bias corrections 1 - beta^t of Adam, as running powers of beta
+    float b1t = powf(a.beta1, (float)a.step0), b2t = powf(a.beta2, (float)a.step0);
+    bool ok = true, staged = false, in_ok_next = true;
+    float y_next = 0.f;
     if (my_rounds > 0) n.prefetch(&tm, a.targ, a.F, path_of(0, 0));
     for (int st = 0; st < a.n_steps; ++st) {
         for (int rd = 0; rd < my_rounds && ok; ++rd) {
             const bool last = rd + 1 == my_rounds;
             const bool has_next = !last || st + 1 < a.n_steps;
             const uint32_t next = last ? path_of(st + 1, 0) : path_of(st, rd + 1);
-            ok = n.train_tile(a, &tm, rd == 0, inv_batch, has_next, next, my_gsl);
+            float y = y_next;
+            bool in_ok = in_ok_next;
+            if (!staged) in_ok = n.stage_x(y);   // else placed during the previous exchange
+            staged = false;
+            ok = n.train_tile(a, &tm, y, in_ok, rd == 0, inv_batch, has_next, next, my_gsl);
             if (!ok && n.row == 0) atomicExch(a.err, 2);
         }
         umma::fence_before_sync();
@@ -635,10 +641,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
                            part_s + (uint32_t)n.tid * slice_bytes, slice_bytes,
                            umma::map_rank(xbar_part, (uint32_t)n.tid));
 
+        // the next step's first tile: its inputs into the X columns of B (free since the
+        // weight-gradient GEMM completed) while the exchange runs
+        if (ok && my_rounds > 0 && st + 1 < a.n_steps) {
+            in_ok_next = n.stage_x(y_next);
+            staged = true;
+        }
+
         // the owned slice: Adam moments requested before the wait for the partials
         const int step = a.step0 + st + 1;
         const bool fresh = a.step0 == 0 && st == 0;   // the moments of a date start at zero
-        const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
+        b1t *= a.beta1;
+        b2t *= a.beta2;
+        const float inv_bc1 = 1.f / (1.f - b1t), inv_bc2 = 1.f / (1.f - b2t);
         const int q_first = lo + 4 * n.tid;
         float4 m4 = make_float4(0.f, 0.f, 0.f, 0.f), v4 = m4;
         if (q_first < hi && !fresh) {
@@ -656,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
             if (q >= L::NP || (q < L::ob1 && q / U >= a.F)) return 0.f;   // padding stays zero
             m = a.beta1 * m + (1.f - a.beta1) * g;
             v = a.beta2 * v + (1.f - a.beta2) * g * g;
-            return th[q] - a.lr * (m / bc1) / (sqrtf(v / bc2) + a.eps);
+            return th[q] - adam_delta(m, v, inv_bc1, inv_bc2, a.lr, a.eps);
         };
         for (int q0 = q_first; q0 < hi; q0 += 4 * kThreads) {
             if (q0 != q_first && !fresh) {

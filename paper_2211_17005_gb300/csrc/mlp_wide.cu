@@ -624,7 +624,8 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
         // new FP32 values and their BF16 images
         {
             const int step = a.step0 + st + 1;
-            const float bc1 = 1.f - powf(a.beta1, (float)step), bc2 = 1.f - powf(a.beta2, (float)step);
+            const float inv_bc1 = 1.f / (1.f - powf(a.beta1, (float)step)),
+                        inv_bc2 = 1.f / (1.f - powf(a.beta2, (float)step));
             const int NG = (hi - lo) / 4;
             const int nsub = NG >= kWThreads ? 1 : (NG > 0 ? kWThreads / NG : 1);
             const int Pg = kWThreads / nsub;
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
                         if (q < WL::NP && !(q < WL::ob1 && q / WL::U >= a.F)) {
                             mv[e] = a.beta1 * mv[e] + (1.f - a.beta1) * gv[e];
                             vv[e] = a.beta2 * vv[e] + (1.f - a.beta2) * gv[e] * gv[e];
-                            t = tv[e] - a.lr * (mv[e] / bc1) / (sqrtf(vv[e] / bc2) + a.eps);
+                            t = tv[e] - adam_delta(mv[e], vv[e], inv_bc1, inv_bc2, a.lr, a.eps);
                         }
                         tv[e] = t;
                         if (q < WL::ob1) {
