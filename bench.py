@@ -102,6 +102,21 @@ def price_instr_per_path_date(wl):
     return 20 * E + 12 * E * G + NPF * C * E * (2 * G + 1) + 3 * NPF * C + 6
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work from one
+# ncu capture of each kernel in its current form (profiles/), scaled to a launch by
+# the units it processes. The simulation kernels were captured at 32768 paths of the
+# paper workload (part of their writes still sat in the 129 MB L2 when they ended,
+# so the scaled figures are lower bounds); the trainer at the benchmark's 2^17 paths.
+NCU_TRAFFIC = {
+    "sim_kernel": {"bytes_per_unit": (0.12e6 + 415.28e6) / (32768 * 100), "unit": "path-step",
+                   "profile": "profiles/sim_price_inner_kernels_paper_32k.md"},
+    "price_kernel": {"bytes_per_unit": (263.78e6 + 81.86e6) / (32768 * 100), "unit": "path-date",
+                     "profile": "profiles/sim_price_inner_kernels_paper_32k.md"},
+    "inner_kernel": {"bytes_per_unit": (222.86e6 + 11.39e6) / 32768, "unit": "path",
+                     "profile": "profiles/sim_price_inner_kernels_paper_32k.md"},
+}
+
+
 def mlp_flops_per_date(M, d, u, epochs):
     """Algorithmic FLOPs of Algorithm 1 at one date for the NN+ network d -> u -> u -> 1:
     per sample and epoch a forward pass 2(d u + u^2) and a backward pass 2(u^2 + u^2 + d u)
@@ -495,8 +510,11 @@ def main():
     alu = {}
     for name, (per_unit, ms, unit) in kern.items():
         ach = per_unit * wl.M * n / (ms / 1e3)
+        tr = NCU_TRAFFIC.get(name) if wl.name == "paper" else None
         alu[name] = {"bound": "alu", "kernel": name, "achieved": ach / 1e12, "peak": peak_alu / 1e12,
-                     "unit": "T lane-instr/s", "frac": ach / peak_alu, "traffic": None,
+                     "unit": "T lane-instr/s", "frac": ach / peak_alu,
+                     "traffic": tr["bytes_per_unit"] * wl.M * n if tr else None,
+                     "traffic_source": tr["profile"] if tr else None,
                      "algorithmic_instr_per_unit": per_unit, "unit_of_work": unit, "ms": ms}
     dom = max(alu, key=lambda k: alu[k]["ms"])
     roof = dict(alu[dom])

@@ -103,12 +103,17 @@ typedef struct cva_sim cva_sim;   /* opaque: tables and device buffers of one ru
 
 /* Prepare a simulation of M outer paths x N inner default draws for n_pf
  * portfolios sharing one model and grid. Validates every input (returns
- * CVA_EINVAL on a bad one, CVA_ENOTSUP for model shapes the kernels are not
- * compiled for), builds the host tables (correlation Cholesky factor, Hull-White
- * drift and bond tables, date-bucketed portfolio weights, par rates) and
- * allocates the device buffers on the current device (CVA_ENOMEM if that
- * fails). Limits: 1 <= E <= 16, 1 <= C <= 16, n_steps <= 254, N <= 2^24,
- * M <= 2^31. Synchronous. */
+ * CVA_EINVAL on a bad one), builds the host tables (correlation Cholesky factor,
+ * Hull-White drift and bond tables, date-bucketed portfolio weights, par rates)
+ * and allocates the device buffers on the current device (CVA_ENOMEM if that
+ * fails). Limits: 1 <= E <= 16, 1 <= C <= 16, 1 <= n_pf <= 6, swaps of at most
+ * 10 periods, n_steps <= 254, N <= 2^24, M <= 2^31, and n_pf C E (longest
+ * schedule in periods) <= 5120 (the date-bucketed weights live in constant
+ * memory; CVA_ENOTSUP beyond). Compiled fast paths exist for (E, C, CIR
+ * counterparties first, n_pf) = (1, 2 constant, 1), (10, 8 CIR, 1) and (10, 8 CIR,
+ * 6); every other shape within the limits, including constant and CIR intensities
+ * in any order, runs on the run-time-shape kernels (flag CVA_GENERIC_KERNELS
+ * forces them for a compiled shape; the results are the same bits). Synchronous. */
 CVA_API cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc *pfs,
                           int n_pf, const cva_grid *grid, uint64_t M, uint32_t N,
                           uint32_t flags, cva_sim **out);
@@ -368,7 +373,9 @@ CVA_API cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, i
  * state every ckpt_every pricing dates (<= 16; sub-steps <= 4); the reverse sweep
  * recomputes each segment from its checkpoint. forward_only = 1 computes only
  * the smooth CVA_0 (grad_host may be NULL). Per-path adjoints are reduced in
- * FP64. Allocates and frees its buffers; synchronises `stream`. */
+ * FP64. The adjoint kernel is compiled for the fast-path shapes of cva_sim_create
+ * with one portfolio, (E, C) = (1, 2 constant) and (10, 8 CIR); other shapes return
+ * CVA_ENOTSUP. Allocates and frees its buffers; synchronises `stream`. */
 CVA_API cva_status cva_grad_cva0(const cva_model_desc *model, const cva_portfolio_desc *pf,
                                  const cva_grid *grid, uint64_t M, uint64_t seed, uint64_t k0,
                                  int ckpt_every, int forward_only, double *grad_host,
