@@ -224,7 +224,7 @@ def cpu_oracle_sample(wl, M_sample, use_mlp=None, n_threads=0):
     return dt, (n_threads or os.cpu_count()), o, reg
 
 
-def sim_errors(api, o, wl, M, pf=0, keep_sim=False):
+def sim_errors(api, o, wl, M, pf=0, keep_sim=False, tiles=None):
     """Errors of the GPU simulation (first M paths, the workload's seed, portfolio pf)
     against the oracle's outputs o on the same paths: CVA_0, every per-path target
     (against the oracle's targets rebuilt at the GPU's default step on tie-moved draws)
@@ -233,6 +233,9 @@ def sim_errors(api, o, wl, M, pf=0, keep_sim=False):
     import torch
     from oracle import compare
     sim = api.Simulation(wl.model, wl.portfolios, wl.grid, M, wl.N, keep_defaults=True)
+    if tiles:   # the tile shapes (and pricing form) of the measured run
+        sim.set_tiles(tiles["sim_block"], tiles["price_block"], tiles["inner_paths_per_block"],
+                      tiles["lsq_chunk_target"], tiles["portfolios_per_price_block"])
     sim.run(wl.seed)
     torch.cuda.synchronize()
     idx = sim.defaults().cpu().numpy()
@@ -577,7 +580,7 @@ def main():
         torch.cuda.synchronize()
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
-        reps = 3
+        reps = 5
         g0.record(stream)
         for _ in range(reps):
             graph.replay()
@@ -592,6 +595,25 @@ def main():
                    "tiles": tiles, "replays": reps, "l2": "working set 48 GB > L2"}
         bsim.close()
         del bpred, graph
+        # where a replay's time goes: the same launches run eagerly with per-kernel events
+        # (the tile choice is the cached one)
+        psim = api.Simulation(bwl.model, bwl.portfolios, bwl.grid, bwl.M, bwl.N, profile=True)
+        psim.autotune(bwl.seed, "linear")
+        ppred = torch.zeros((psim.n_pf, psim.n, psim.M), dtype=torch.float32, device="cuda")
+        parts = []
+        for _ in range(2):
+            psim.run(bwl.seed)
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            psim.regress_portfolios("linear", pred=ppred)
+            r1.record(stream)
+            torch.cuda.synchronize()
+            parts.append(list(psim.kernel_ms()) + [r0.elapsed_time(r1)])
+        k = np.min(np.array(parts), axis=0)
+        batched["eager_breakdown_ms"] = {"path_simulation": float(k[0]), "pricing": float(k[1]),
+                                         "inner_defaults": float(k[2]), "grouped_least_squares": float(k[3])}
+        psim.close()
+        del ppred
 
     # ---- least squares on (default indicators X, state Y) over the M N hierarchical sample (rank 0) ----
     alive = None
@@ -638,20 +660,26 @@ def main():
         psim.run(pwl.seed)
         api.mlp_regress_all(psim, pinit.clone(), hidden=pwl.hidden)   # warm-up
         torch.cuda.synchronize()
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        psim.run(pwl.seed)
-        e1.record(stream)
-        api.mlp_regress_all(psim, pinit.clone(), hidden=pwl.hidden)
-        e2.record(stream)
-        torch.cuda.synchronize()
-        p_sim, p_reg = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        sims, regs = [], []
+        for _ in range(3):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            psim.run(pwl.seed)
+            e1.record(stream)
+            api.mlp_regress_all(psim, pinit.clone(), hidden=pwl.hidden)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            sims.append(e0.elapsed_time(e1))
+            regs.append(e1.elapsed_time(e2))
+        p_sim, p_reg = float(np.median(sims)), float(np.median(regs))
         pflops = mlp_flops_per_date(pwl.M, pwl.model.F, pwl.hidden, epochs) * (pn - 1)
         ptf = pflops / (p_reg / 1e3) / 1e12
         peak_tf = pk.get("bf16_tflops_sustained", 1720.9)
         precision = {"workload": describe(pwl) + f", NN+ {pwl.model.F}->{pwl.hidden}->{pwl.hidden}->1, Algorithm 2 "
                                                  f"over {pn - 1} dates (E={epochs}, |B|={n_batches})",
-                     "sim_ms": p_sim, "regression_ms": p_reg, "step_ms": p_sim + p_reg,
+                     "sim_ms": p_sim, "regression_ms": p_reg, "step_ms": p_sim + p_reg, "repetitions": 3,
+                     "timing": "median of 3 (simulation, Algorithm 2) pairs after a warm-up, CUDA events",
+                     "trainer": api.mlp_plan(pwl.M, pwl.hidden, n_batches),
                      "value": pwl.M * pwl.N * pn / ((p_sim + p_reg) / 1e3), "unit": UNIT,
                      "regression_samples_per_s": pwl.M * (pn - 1) / (p_reg / 1e3),
                      "roofline": {"bound": "tensor", "kernel": "wide_train_kernel + wide_sweep_kernel",
@@ -721,11 +749,13 @@ def main():
             Mb, pb = 1024, len(bwl.portfolios) - 1      # the 2000-swap portfolio
             bo = oracle.simulate(bwl.model, bwl.portfolios[pb], bwl.grid, 0, Mb, bwl.N, bwl.seed,
                                  want=("features", "I0", "Lambda", "mtm", "idx", "xi_bar"))
-            e_b, bsim2, bc = sim_errors(api, bo, bwl, Mb, pf=pb, keep_sim=True)
+            e_b, bsim2, bc = sim_errors(api, bo, bwl, Mb, pf=pb, keep_sim=True,
+                                        tiles=batched["tiles"] if batched else None)
             bpred2, _ = bsim2.regress_portfolios("linear")
             e_b["least_squares"] = lsq_gap(bpred2[pb].cpu().numpy(), bo["features"], bo["xi_bar"],
                                            range(1, bwl.grid.n_steps), bc)
             e_b["portfolio"] = f"{pb} ({bwl.portfolios[pb].n_swaps} swaps) of the six, simulated together"
+            e_b["tiles"] = batched["tiles"] if batched else None
             bsim2.close()
             errors["batched"] = e_b
             del bo

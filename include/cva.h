@@ -323,8 +323,8 @@ CVA_API cva_status cva_regress_portfolios(cva_sim *sim, int basis, float *pred_d
  * draws where c has defaulted give the normal equations (FP64 accumulation), solved
  * by a Jacobi-scaled Cholesky factorisation in FP64; a column whose pivot vanishes
  * (no default of c by t_i in the whole sample) is dropped, with coefficient 0.
- * Needs a simulation created with CVA_KEEP_DEFAULTS after cva_simulate; C must be 2
- * or 8, 1 + F + C <= 40 and N (5C + 6) bytes of draw tables must fit 160 KB of shared
+ * Needs a simulation created with CVA_KEEP_DEFAULTS after cva_simulate; C <= 8 (one
+ * warp lane per counterparty pair), 1 + F + C <= 40 and N (5C + 6) bytes of draw tables must fit 160 KB of shared
  * memory (N <= 3400 at C = 8; else CVA_ENOTSUP).
  * pred_dev: float [n][M] (nullable; date 0 untouched) receives the fit at X_i = 0
  * (every counterparty alive). coef_host: double [n][1+F+C] (nullable; date 0
@@ -350,12 +350,15 @@ CVA_API cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *re
 /* Sets the tile shapes of a simulation directly (e.g. a choice cva_autotune made
  * in an earlier process): sim_block in {64, 128}, price_block in {128, 256},
  * inner_paths_per_block in {0 (automatic), 2, 4, 8}, lsq_chunk_target in
- * [152, 2^20], portfolios_per_price_block in {1, 2, 3} dividing the simulation's
- * number of portfolios (a pricing block prices that many portfolios, weights in
- * constant memory) or 0 (every thread prices every portfolio for two paths,
- * weights staged in shared memory; price_block is then unused). None of them
- * changes any result bit. Returns CVA_EINVAL (nothing changed) on a value outside
- * these sets. No GPU work. */
+ * [152, 2^20], and the pricing form portfolios_per_price_block: 1, 2 or 3 dividing
+ * the simulation's number of portfolios (a block prices that many portfolios,
+ * weights in constant memory; price_block threads), 0 (every thread prices every
+ * portfolio for 2 paths with price_block = 128 or 1 path with 256, weights staged in
+ * shared memory) or 4 (every portfolio of 128-path tiles on the tensor cores: the
+ * MtM as a TF32 product with each operand split into head and tail, FP32
+ * accumulation). None of the shapes and forms 0-3 changes any result bit; form 4
+ * rounds the MtM differently (within the oracle tolerances). Returns CVA_EINVAL
+ * (nothing changed) on a value outside these sets. No GPU work. */
 CVA_API cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner_paths_per_block,
                                  int lsq_chunk_target, int portfolios_per_price_block);
 

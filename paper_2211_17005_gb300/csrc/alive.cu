@@ -43,7 +43,7 @@ template <int C>
 struct Shape {
     static constexpr int NP = C * (C - 1) / 2;    // pairs c < d
     static constexpr int NQ = NP + C;             // block-summed statistics: P_cd, q_c
-    static_assert((C == 2 || C == 4 || C == 8) && NP <= 32, "counterparty count must be 2, 4 or 8");
+    static_assert(C >= 1 && C <= 8 && NP <= 32, "one lane per counterparty pair: at most 8 counterparties");
 };
 
 // A draw's C default steps (bytes) and C losses at those steps, vector loads.
@@ -66,12 +66,18 @@ __device__ __forceinline__ void load_draw(const uint8_t *jp, const float *ep, in
 #pragma unroll
         for (int c = 0; c < 4; ++c) j[c] = (v >> (8 * c)) & 255u;
         e[0] = a.x; e[1] = a.y; e[2] = a.z; e[3] = a.w;
-    } else {
+    } else if constexpr (C == 2) {
         const unsigned short v = *reinterpret_cast<const unsigned short *>(jp);
         const float2 a = *reinterpret_cast<const float2 *>(ep);
         j[0] = v & 255u;
         j[1] = v >> 8;
         e[0] = a.x; e[1] = a.y;
+    } else {   // other counts: byte and float loads
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            j[c] = jp[c];
+            e[c] = ep[c];
+        }
     }
 }
 
@@ -545,7 +551,7 @@ cva_status alive_regress(Sim &s, int pf, float *pred_dev, double *coef_host, int
     if (pf < 0 || pf >= s.NPF) return fail(CVA_EINVAL, "regress_alive: portfolio index out of range");
     if (s.n < 2) return fail(CVA_EINVAL, "regress_alive: need at least two pricing steps");
     if (!s.d_idx) return fail(CVA_EINVAL, "regress_alive: the simulation keeps no default steps (CVA_KEEP_DEFAULTS)");
-    if (s.C != 2 && s.C != 8) return fail(CVA_ENOTSUP, "regress_alive: compiled for 2 or 8 counterparties");
+    if (s.C < 1 || s.C > 8) return fail(CVA_ENOTSUP, "regress_alive: at most 8 counterparties");
     if (s.M > 0x7fffffffull) return fail(CVA_EINVAL, "regress_alive: M too large");
     const int C = s.C, NQ = C * (C - 1) / 2 + C, mY = s.F + 1, m = mY + C;
     if (m > kMaxUnknowns) return fail(CVA_ENOTSUP, "regress_alive: 1 + F + C must be <= 40");
@@ -618,7 +624,10 @@ cva_status alive_regress(Sim &s, int pf, float *pred_dev, double *coef_host, int
     a.status = reinterpret_cast<int *>(a.coef_raw + (size_t)groups * m);
     a.pred = pred_dev;
     const bool capturing = cap != cudaStreamCaptureStatusNone;
-    cva_status r = (C == 2) ? launch_stats<2>(a, W, capturing, st) : launch_stats<8>(a, W, capturing, st);
+    static constexpr cva_status (*by_c[8])(const AliveArgs &, int, bool, cudaStream_t) = {
+        launch_stats<1>, launch_stats<2>, launch_stats<3>, launch_stats<4>,
+        launch_stats<5>, launch_stats<6>, launch_stats<7>, launch_stats<8>};
+    cva_status r = by_c[C - 1](a, W, capturing, st);
     if (r != CVA_OK) return r;
     const size_t tile_bytes = 2 * (size_t)kTileRows * RS * sizeof(float);
     const size_t red_bytes = (size_t)(kGramThreads / NBLK) * NBLK * 16 * sizeof(double);

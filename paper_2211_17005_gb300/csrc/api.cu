@@ -731,7 +731,7 @@ cva_status cva_autotune(cva_sim *sim, uint64_t seed, int basis, char *report, si
         };
         // portfolios per pricing block: the divisors of n_pf among 1, 2, 3 (weights in
         // constant memory), or 0 (every portfolio per thread, weights in shared memory)
-        std::vector<int> ppf = {0, 1};
+        std::vector<int> ppf = {4, 0, 1};
         for (int v : {2, 3})
             if (s.NPF % v == 0) ppf.push_back(v);
         const std::vector<std::vector<int>> cand = {{64, 128}, {128, 256}, {2, 4, 8}, {1216, 2432, 4864, 9728}, ppf};
@@ -789,9 +789,11 @@ cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, int inner
         return fail(CVA_EINVAL, "inner_paths_per_block must be 0, 2, 4 or 8");
     if (lsq_chunk_target < 152 || lsq_chunk_target > (1 << 20))
         return fail(CVA_EINVAL, "lsq_chunk_target must lie in [152, 2^20]");
-    if (portfolios_per_price_block < 0 || portfolios_per_price_block > 3 ||
-        (portfolios_per_price_block > 0 && s.NPF % portfolios_per_price_block != 0))
-        return fail(CVA_EINVAL, "portfolios_per_price_block must be 0, or 1, 2 or 3 dividing the number of portfolios");
+    if (portfolios_per_price_block < 0 || portfolios_per_price_block > 4 ||
+        (portfolios_per_price_block >= 1 && portfolios_per_price_block <= 3 &&
+         s.NPF % portfolios_per_price_block != 0))
+        return fail(CVA_EINVAL, "pricing form must be 0 (shared memory), 1, 2 or 3 dividing the number of portfolios "
+                                "(constant memory) or 4 (tensor cores)");
     s.tune_sim_block = sim_block;
     s.tune_price_block = price_block;
     s.tune_inner_P = inner_paths_per_block;

@@ -19,10 +19,12 @@
 //
 // Outputs are structure-of-arrays with the path index fastest.
 #pragma once
+#include <algorithm>
 #include <mutex>
 
 #include "cva_internal.h"
 #include "rng.cuh"
+#include "umma.cuh"
 
 namespace cva {
 namespace {
@@ -394,6 +396,8 @@ __global__ void __launch_bounds__(256 / PT, 2) price_smem_kernel(OuterArgs a, in
     }
 }
 
+#include "price_tc.cuh"
+
 }  // namespace
 }  // namespace cva
 
@@ -468,6 +472,26 @@ cva_status outer_launch(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     sim_kernel<E, C, CS><<<(args.M + sb - 1) / sb, sb, 0, st>>>(args);
     CVA_CUDA_TRY(cudaGetLastError());
     if (s.ev[1]) CVA_CUDA_TRY(cudaEventRecord(s.ev[1], st));
+    if (s.tune_price_pf == 4) {   // every portfolio per 128-path tile on the tensor cores
+        using PT = PriceTc<E, G, NPF, C>;
+        static bool attr[64] = {};
+        if (!attr[dev]) {
+            if (capturing) return fail(CVA_EINVAL, "price: run once before capturing (kernel attribute)");
+            CVA_CUDA_TRY(cudaFuncSetAttribute(price_tc_kernel<E, C, CS, G, NPF>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, PT::bytes));
+            attr[dev] = true;
+        }
+        int sms = 0;
+        CVA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const uint32_t tiles = (args.M + 127u) / 128u;
+        const uint64_t items = (uint64_t)tiles * (uint64_t)(s.n + 1);
+        const unsigned grid =
+            (unsigned)std::min<uint64_t>((items + kPriceSlots - 1) / kPriceSlots, (uint64_t)sms);
+        price_tc_kernel<E, C, CS, G, NPF><<<grid, 128 * kPriceSlots, PT::bytes, st>>>(args, tiles);
+        CVA_CUDA_TRY(cudaGetLastError());
+        if (!capturing) CVA_CUDA_TRY(cudaEventRecord(t_last[dev], st));
+        return CVA_OK;
+    }
     if (s.tune_price_pf == 0) {   // every portfolio per thread, weights in shared memory
         constexpr int GP = (G + 1) / 2 * 2;
         constexpr size_t smem = (size_t)NPF * C * E * GP * sizeof(float2);

@@ -53,6 +53,27 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N)
 
 constexpr uint32_t kMnMajorA = 1u << 15, kMnMajorB = 1u << 16;
 
+// instruction descriptor: kind::tf32, A = B = TF32, D = FP32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// byte offset of 4-byte element (r, k) in an R x K canonical tile (core matrices of
+// 8 rows x 16 bytes = 4 elements along K)
+__host__ __device__ __forceinline__ uint32_t kmajor_offset32(uint32_t r, uint32_t k, uint32_t K)
+{
+    return (r >> 3) * (K >> 2) * 128u + (k >> 2) * 128u + (r & 7u) * 16u + (k & 3u) * 4u;
+}
+
+// x rounded to TF32 (10 explicit mantissa bits, nearest, ties away), in a 32-bit container
+__device__ __forceinline__ float tf32_round(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *smem_result, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(smem_result)),
@@ -77,6 +98,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T with TF32 operands, issued by one thread
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }

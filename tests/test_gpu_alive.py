@@ -65,6 +65,7 @@ def _check_against_oracle(wl, M, N, dates, pred, coef, dropped, feats):
 @pytest.mark.parametrize("name,M,N,n_steps,dates", [
     ("small", 4099, 40, 50, (1, 2, 10, 25, 48, 49)),
     ("paper", 1003, 24, 20, (1, 5, 10, 18, 19)),
+    ("mixed", 1531, 24, 40, (1, 7, 20, 38, 39)),   # C = 5, constant and CIR intensities interleaved
 ])
 def test_alive_regression_matches_oracle(api, name, M, N, n_steps, dates):
     wl = W.make(name, n_steps=n_steps)
