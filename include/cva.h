@@ -438,6 +438,17 @@ CVA_API cva_status cva_mlp_plan(uint64_t M, int hidden, int n_batches, int32_t *
  * every device; host-only, no device work. */
 CVA_API cva_status cva_mlp_set_wait_limit(uint32_t grid_polls);
 
+/* Kernel timing of the trainers (Algorithm 1's training epochs): while on, every
+ * launch of the training kernel by cva_mlp_fit, cva_mlp_first_gradient and
+ * cva_mlp_regress_all (one launch per epoch and date) is bracketed by a pair of
+ * CUDA events on the stream it runs on, and the call adds the launch's duration to
+ * a process-wide total once it has synchronised. This call stores the totals
+ * accumulated since its previous call (milliseconds, launches) in ms_host and
+ * launches_host (each nullable), clears them and switches timing on (on != 0) or
+ * off. The events break nothing but the overlap of one launch's start with the
+ * previous launch's end. Host-only, no device work. */
+CVA_API cva_status cva_mlp_kernel_timing(int on, double *ms_host, uint64_t *launches_host);
+
 /* Validation hook of cva_mlp_fit: one Adam step on the first batch; grad_dev
  * (float [cva_mlp_num_params]) receives that batch's gradient, params_dev the
  * updated parameters. */

@@ -94,6 +94,7 @@ SIGNATURES = {
                                    ctypes.c_void_p, ctypes.c_void_p]),
     "cva_mlp_num_params": (ctypes.c_int, [ctypes.c_int]),
     "cva_mlp_set_wait_limit": (ctypes.c_int, [ctypes.c_uint32]),
+    "cva_mlp_kernel_timing": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_uint64)]),
     "cva_mlp_plan": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
     "cva_mlp_first_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
                                               ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,

@@ -342,6 +342,15 @@ def mlp_plan(M: int, hidden: int = 64, n_batches: int = 32) -> dict:
     return {"ctas": int(out[0]), "cluster": int(out[1]), "tiles_per_batch": int(out[2]), "rounds": int(out[3])}
 
 
+def mlp_kernel_timing(on: bool) -> dict:
+    """Switch the trainers' per-launch event timing on or off; returns the totals
+    accumulated since the previous call (see cva_mlp_kernel_timing)."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_uint64(0)
+    nat.check(N_lib().cva_mlp_kernel_timing(1 if on else 0, ctypes.byref(ms), ctypes.byref(n)),
+              "cva_mlp_kernel_timing")
+    return {"ms": float(ms.value), "launches": int(n.value)}
+
+
 def mlp_pack(p, hidden: int) -> torch.Tensor:
     """Flat device parameter vector from a dict (W1 [u, d<=32], b1, W2, b2, w3, b3, mu)."""
     W1 = np.zeros((hidden, MLP_IN))

@@ -810,6 +810,12 @@ cva_status cva_mlp_set_wait_limit(uint32_t grid_polls)
     return CVA_OK;
 }
 
+cva_status cva_mlp_kernel_timing(int on, double *ms_host, uint64_t *launches_host)
+{
+    mlp_kernel_timing(on != 0, ms_host, launches_host);
+    return CVA_OK;
+}
+
 cva_status cva_mlp_plan(uint64_t M, int hidden, int n_batches, int32_t *out4_host)
 {
     if (!out4_host) return fail(CVA_EINVAL, "mlp_plan: NULL output");

@@ -178,6 +178,12 @@ cva_status mlp_wide_plan(int tiles_per_batch, int32_t out[4]);
 void mlp_wide_set_grid_polls(uint32_t polls);
 cva_status mlp_begin(cudaStream_t st);
 cva_status mlp_finish(cudaStream_t st);
+// Kernel timing of the train launches: mlp_kernel_timing returns and clears the
+// totals and switches timing on or off; mlp_timing_pair hands out the event pair
+// to record around one train launch (false when timing is off); mlp_finish adds
+// the durations of the pairs recorded since mlp_begin.
+void mlp_kernel_timing(bool on, double *ms, uint64_t *launches);
+bool mlp_timing_pair(int dev, cudaEvent_t *a, cudaEvent_t *b);
 cva_status mlp_fit_dates(const float *feat0, size_t feat_stride, const float *targ0, size_t targ_stride, int n_dates,
                          int F, uint64_t M, int U, int n_batches, int epochs, float lr, int max_steps,
                          float *params_dev, float *pred0, float *grad_out_dev, float *loss_out_dev, cudaStream_t st);

@@ -49,7 +49,9 @@
 #include <math.h>
 
 #include <climits>
+#include <atomic>
 #include <mutex>
+#include <vector>
 #include <string>
 
 #include "cva_internal.h"
@@ -848,9 +850,35 @@ struct MlpWork {
     int max_cluster = 0;     // 16 when a 16-CTA cluster of the train kernel fits, else 8
     cudaStream_t main = nullptr, side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_train = nullptr, ev_side = nullptr, ev_join = nullptr;
+    std::vector<cudaEvent_t> tev;   // timing events, a pair around each train launch
+    size_t tev_used = 0;
 };
 std::mutex g_mlp_mu;
 MlpWork g_mlp[64];
+
+// kernel timing of the train launches (cva_mlp_kernel_timing); totals under g_mlp_mu
+std::atomic<bool> g_mlp_timing{false};
+double g_train_ms = 0.0;
+uint64_t g_train_launches = 0;
+
+// the next pair of timing events of a device (created on first use), false when
+// timing is off or an event cannot be created; the caller holds g_mlp_mu
+bool timing_pair_locked(MlpWork &w, cudaEvent_t &a, cudaEvent_t &b)
+{
+    if (!g_mlp_timing.load()) return false;
+    while (w.tev.size() < w.tev_used + 2) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        w.tev.push_back(e);
+    }
+    a = w.tev[w.tev_used];
+    b = w.tev[w.tev_used + 1];
+    w.tev_used += 2;
+    return true;
+}
 
 struct MlpPlan {
     float *adam, *best[2], *stats, *snaps;
@@ -997,6 +1025,23 @@ cva_status mlp_plan(uint64_t M, int U, int n_batches, int32_t out[4])
     return CVA_OK;
 }
 
+bool mlp_timing_pair(int dev, cudaEvent_t *a, cudaEvent_t *b)
+{
+    if (dev < 0 || dev >= 64 || !g_mlp_timing.load()) return false;
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    return timing_pair_locked(g_mlp[dev], *a, *b);
+}
+
+void mlp_kernel_timing(bool on, double *ms, uint64_t *launches)
+{
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    if (ms) *ms = g_train_ms;
+    if (launches) *launches = g_train_launches;
+    g_train_ms = 0.0;
+    g_train_launches = 0;
+    g_mlp_timing.store(on);
+}
+
 cva_status mlp_begin(cudaStream_t st)
 {
     int dev = 0;
@@ -1004,6 +1049,7 @@ cva_status mlp_begin(cudaStream_t st)
     if (dev < 0 || dev >= 64) return fail(CVA_EINVAL, "device index out of range");
     std::lock_guard<std::mutex> lk(g_mlp_mu);
     MlpWork &w = g_mlp[dev];
+    w.tev_used = 0;
     if (!w.count) {
         if (cudaMalloc(&w.count, 4 * sizeof(unsigned)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: counters");
         if (cudaMalloc(&w.err, sizeof(int)) != cudaSuccess) return fail(CVA_ENOMEM, "mlp: status");
@@ -1026,6 +1072,20 @@ cva_status mlp_finish(cudaStream_t st)
     int herr = 0;
     if (err) CVA_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CVA_CUDA_TRY(cudaStreamSynchronize(st));
+    {   // every timed train launch has ended: add its duration
+        std::lock_guard<std::mutex> lk(g_mlp_mu);
+        MlpWork &w = g_mlp[dev];
+        for (size_t i = 0; i + 1 < w.tev_used; i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, w.tev[i], w.tev[i + 1]) == cudaSuccess) {
+                g_train_ms += ms;
+                ++g_train_launches;
+            } else {
+                (void)cudaGetLastError();
+            }
+        }
+        w.tev_used = 0;
+    }
     if (herr != 0) return fail(CVA_ETIMEOUT, "mlp: a bounded device wait gave up (status " + std::to_string(herr) + ")");
     return CVA_OK;
 }
@@ -1145,7 +1205,11 @@ cva_status mlp_fit_dates(const float *feat0, size_t feat_stride, const float *ta
             ta.n_steps = n_batches < steps_left ? n_batches : steps_left;
             ta.step0 = (e - 1) * n_batches;
             ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;   // on once the refit of epoch floor(E/2) ran
+            cudaEvent_t t0 = nullptr, t1 = nullptr;
+            const bool timed = timing_pair_locked(*w, t0, t1);
+            if (timed) CVA_CUDA_TRY(cudaEventRecord(t0, mst));
             CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, mlp_train_kernel<64>, ta, tm));
+            if (timed) CVA_CUDA_TRY(cudaEventRecord(t1, mst));
             steps_left -= ta.n_steps;
             if (max_steps > 0 && steps_left <= 0) {
                 stopped = true;

@@ -1012,7 +1012,11 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
             ta.step0 = (e - 1) * n_batches;
             ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;
             CVA_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), st));
+            cudaEvent_t t0 = nullptr, t1 = nullptr;
+            const bool timed = mlp_timing_pair(dev, &t0, &t1);
+            if (timed) CVA_CUDA_TRY(cudaEventRecord(t0, st));
             CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, wide_train_kernel, ta, tm));
+            if (timed) CVA_CUDA_TRY(cudaEventRecord(t1, st));
             steps_left -= ta.n_steps;
             if (max_steps > 0 && steps_left <= 0) return CVA_OK;
             if (e == epochs / 2) {

@@ -149,3 +149,23 @@ def test_grid_barrier_timeout_is_reported_and_the_next_call_is_clean(api):
     again = api.mlp_first_gradient(xd, yd, api.mlp_pack(p0, u), hidden=u, n_batches=nb).cpu().numpy()
     np.testing.assert_array_equal(again, ref)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("u", [64, 128])
+def test_kernel_timing_counts_every_train_launch(api, u):
+    """cva_mlp_kernel_timing: one event pair per training epoch, positive durations,
+    totals cleared by each call, and the same parameters with timing on as off."""
+    M, nb, E = 4096 * 4, 32, 4
+    Y, xi = _problem(M, seed=6)
+    yd, xd = torch.from_numpy(Y).cuda(), torch.from_numpy(xi).cuda()
+    p0 = W.mlp_init(27, u, seed=23)
+    p_off = api.mlp_pack(p0, u)
+    api.mlp_fit(xd, yd, p_off, hidden=u, n_batches=nb, epochs=E)
+    api.mlp_kernel_timing(True)
+    p_on = api.mlp_pack(p0, u)
+    api.mlp_fit(xd, yd, p_on, hidden=u, n_batches=nb, epochs=E)
+    t = api.mlp_kernel_timing(False)
+    assert t["launches"] == E and t["ms"] > 0.0
+    assert torch.equal(p_on, p_off)
+    api.mlp_fit(xd, yd, api.mlp_pack(p0, u), hidden=u, n_batches=nb, epochs=E)
+    assert api.mlp_kernel_timing(False) == {"ms": 0.0, "launches": 0}
