@@ -126,3 +126,49 @@ def test_planted_mlp_mistake_is_caught(name, old, new, pin, tmp_path):
     pin(mlp_pins.mlp)   # the unmodified oracle passes
     with pytest.raises(AssertionError):
         pin(mutant)
+
+
+from tests import test_oracle_dual as dual_pins  # noqa: E402
+
+DUAL_SRC = os.path.join(os.path.dirname(oracle.__file__), "dual.py")
+
+# plausible slips in the forward-mode gradient: each is caught by the value pin or by
+# the central-difference pin of tests/test_oracle_dual.py
+DUAL_PLANTS = [
+    ("product rule with a minus sign",
+     "self.d * o.v + o.d * self.v)", "self.d * o.v - o.d * self.v)",
+     dual_pins.pin_tangents_are_central_differences),
+    ("quotient rule with a plus sign",
+     "(self.d * o.v - o.d * self.v) / (o.v * o.v)", "(self.d * o.v + o.d * self.v) / (o.v * o.v)",
+     dual_pins.pin_tangents_are_central_differences),
+    ("square root derivative without the factor 1/2",
+     "x.d / (2.0 * safe)", "x.d / safe",
+     dual_pins.pin_tangents_are_central_differences),
+    ("positive part passing the tangent where x <= 0",
+     "np.where(x.v > 0.0, x.d, 0.0))", "x.d)",
+     dual_pins.pin_tangents_are_central_differences),
+    ("exponential without the chain factor",
+     "return Dual(e, x.d * e)", "return Dual(e, x.d)",
+     dual_pins.pin_tangents_are_central_differences),
+    ("quanto drift with the wrong sign",
+     "drift = drift - sx[e] * sr[e] * q_rho[e]", "drift = drift + sx[e] * sr[e] * q_rho[e]",
+     dual_pins.pin_value_is_the_oracle_smooth_cva0),
+    ("survival difference taken one date late",
+     "share[c] + V * (exp(-Lam_prev[c]) - exp(-Lam[c]))", "share[c] + V * (exp(-Lam[c]) - exp(-Lam[c]))",
+     dual_pins.pin_value_is_the_oracle_smooth_cva0),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", DUAL_PLANTS, ids=[p[0] for p in DUAL_PLANTS])
+def test_planted_dual_mistake_is_caught(name, old, new, pin, tmp_path):
+    import importlib.util
+    src = open(DUAL_SRC).read()
+    assert src.count(old) == 1, f"plant site for {name!r} not found exactly once"
+    path = tmp_path / "dual_mutant.py"
+    path.write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location("oracle._dual_mutant", str(path))
+    mutant = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mutant)
+    pin(dual_pins.dual)   # the unmodified oracle passes
+    with pytest.raises(AssertionError):
+        pin(mutant)
