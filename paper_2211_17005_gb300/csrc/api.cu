@@ -98,6 +98,7 @@ void free_sim(Sim *s)
     cudaFree(s->d_mtm);
     cudaFree(s->d_targets);
     cudaFree(s->d_idx);
+    cudaFree(s->d_cnt);
     cudaFree(s->d_const_img);
     cudaFree(s->d_lsq);
     cudaFree(s->d_alive_stats);
@@ -333,6 +334,15 @@ cva_status cva_sim_create(const cva_model_desc *model, const cva_portfolio_desc 
     if (flags & CVA_KEEP_EXPOSURES) TRY_ALLOC(s->d_mtm, (size_t)n_pf * (n + 1) * C * Mz);
     TRY_ALLOC(s->d_targets, (size_t)n_pf * n * Mz);
     if (flags & CVA_KEEP_DEFAULTS) TRY_ALLOC(s->d_idx, Mz * N * C);
+    if (N <= 65535u) {
+        uint16_t *cnt = nullptr;
+        TRY_ALLOC(cnt, (size_t)(n + 1) * C * Mz);
+        s->d_cnt = cnt;
+    } else {
+        uint32_t *cnt = nullptr;
+        TRY_ALLOC(cnt, (size_t)(n + 1) * C * Mz);
+        s->d_cnt = cnt;
+    }
     TRY_ALLOC(s->d_const_img, sizeof(SimConsts) + sizeof(SimWeights));
 #undef TRY_ALLOC
     cudaError_t e1 = cudaMemcpy(s->d_zc, zc.data(), zc.size() * sizeof(float4), cudaMemcpyHostToDevice);

@@ -83,6 +83,7 @@ struct Sim {
     float *d_mtm = nullptr;        // [NPF][n+1][C][M] (optional)
     float *d_targets = nullptr;    // [NPF][n][M]
     uint8_t *d_idx = nullptr;      // [M][N][C] (optional)
+    void *d_cnt = nullptr;         // [n+1][C][M] default counts per step: uint16 (N <= 65535) or uint32
     // device image of consts + weights (constant uploads are device-to-device, so
     // they can be captured in a CUDA graph)
     unsigned char *d_const_img = nullptr;

@@ -159,6 +159,14 @@ __global__ void __launch_bounds__(128 * kPriceSlots, 1) price_tc_kernel(OuterArg
         const float *ffix = a.features + (size_t)(p * ppp) * F * M + kr;   // state at the last reset
         const float beta = expf(-__ldg(a.disc + (size_t)j * M + kr));
         float x[GK];
+        // the state of economy 1 is requested before economy 0's bond prices are computed,
+        // and every later economy's one economy ahead (rates, FX log-level, rate at the fixing)
+        float n_r = 0.f, n_fix = 0.f, n_lchi = 0.f;
+        if (E > 1) {
+            n_r = __ldg(fe + M);
+            n_fix = __ldg(ffix + M);
+            n_lchi = __ldg(fe + (size_t)E * M);
+        }
         {
             const float2 f2 = __ldg(fx);
             price_row<G, GK>(x, a.zc + (size_t)j * E * G, p, __ldg(fe), expm1f(fmaf(f2.y, __ldg(ffix), -f2.x)), 1.f);
@@ -199,11 +207,16 @@ __global__ void __launch_bounds__(128 * kPriceSlots, 1) price_tc_kernel(OuterArg
                 umma::commit(mbar);
             }
             if (e + 1 < E) {   // the next economy's bond prices while the tensor core works
+                const float re = n_r, rfix = n_fix, lchi = n_lchi;   // economy e + 1, requested earlier
+                if (e + 2 < E) {
+                    n_r = __ldg(fe + (size_t)(e + 2) * M);
+                    n_fix = __ldg(ffix + (size_t)(e + 2) * M);
+                    n_lchi = __ldg(fe + (size_t)(E + e + 1) * M);   // log chi^{e+2}
+                }
                 const float2 f2 = __ldg(fx + e + 1);
-                const float fixm1 = expm1f(fmaf(f2.y, __ldg(ffix + (size_t)(e + 1) * M), -f2.x));
-                const float chi = expf(__ldg(fe + (size_t)(E + e) * M));   // chi^{e+1} from log chi^{e+1}
-                price_row<G, GK>(x, a.zc + ((size_t)j * E + e + 1) * G, p, __ldg(fe + (size_t)(e + 1) * M), fixm1,
-                                 chi);
+                const float fixm1 = expm1f(fmaf(f2.y, rfix, -f2.x));
+                const float chi = expf(lchi);   // chi^{e+1} from log chi^{e+1}
+                price_row<G, GK>(x, a.zc + ((size_t)j * E + e + 1) * G, p, re, fixm1, chi);
             }
             const bool done = umma::mbar_wait(mbar, ph, kPriceMbarPolls);
             ph ^= 1u;

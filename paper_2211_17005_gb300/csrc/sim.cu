@@ -1,14 +1,18 @@
 // Inner-default kernel of the hierarchical CVA simulation, and the dispatch
 // of the outer-path kernel instantiations (outer_*.cu).
 //
-// Inner kernel (one warp per outer path, Sec. 3.2 / eq. (e:tau)): N default
-// clocks per counterparty; tau^{k,l} falls in (t_{j-1}, t_j] when the uniform w
-// (epsilon = -log(1 - w)) satisfies T(j-1) < w <= T(j), T = 1 - e^{-Lambda};
-// the default step is the lower bound of w in the monotone thresholds. Counts
-// per (counterparty, step) are integers, so the averaged target of eq.
-// (eq:CVA_portfolio),
-//   xi_bar_i = beta_i^{-1} (1/N) sum_{j>i} sum_c V_c(j) count_c(j),
-// does not depend on the order of the draws.
+// Inner defaults (Sec. 3.2 / eq. (e:tau)), two kernels:
+//   inner_count_kernel   one warp per outer path: N default clocks per
+//     counterparty; tau^{k,l} falls in (t_{j-1}, t_j] when the uniform w
+//     (epsilon = -log(1 - w)) satisfies T(j-1) < w <= T(j), T = 1 - e^{-Lambda};
+//     the default step is the lower bound of w in the monotone thresholds, and
+//     the integer count of defaults per (counterparty, step) goes to global memory;
+//   inner_target_kernel  one thread per outer path: the averaged target of eq.
+//     (eq:CVA_portfolio) of every portfolio from the counts,
+//       xi_bar_i = beta_i^{-1} (1/N) sum_{j>i} sum_c V_c(j) count_c(j),
+//     as a running sum over the dates from the last, every load and store
+//     coalesced over consecutive paths.
+// The counts are integers, so the targets do not depend on the order of the draws.
 #include <mutex>
 
 #include "cva_internal.h"
@@ -27,16 +31,38 @@ struct InnerArgs {
     const float *__restrict__ disc;   // [n+1][M]
     float *targets;                   // [NPF][n][M]
     uint8_t *idx;                     // [M][N][C] or null
+    uint16_t *cnt16;                  // [n+1][C][M] default counts (N <= 65535) ...
+    uint32_t *cnt32;                  // ... or these (larger N)
 };
 
+// First j in [1, n] with T(j) >= w for nondecreasing thresholds T, else n + 1: the
+// lower bound by a fixed sequence of power-of-two steps from top, the largest power
+// of two <= n (every lane of a warp runs the same steps; the comparisons select).
+template <class Thr>
+__device__ __forceinline__ int lower_bound_pow2(Thr T, int n, int top, float w)
+{
+    int pos = 0;   // T(1..pos) < w
+    for (int step = top; step > 0; step >>= 1) {
+        const int q = pos + step;
+        if (q <= n && T(q) < w) pos = q;
+    }
+    return pos + 1;
+}
+
+__host__ __device__ __forceinline__ int pow2_floor(int n)
+{
+    int top = 1;
+    while (2 * top <= n) top *= 2;
+    return top;
+}
+
 template <int C>
-__global__ void __launch_bounds__(256) inner_kernel(InnerArgs a)
+__global__ void __launch_bounds__(256) inner_count_kernel(InnerArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int P = a.P, n = a.n, np1 = n + 1;
+    const int P = a.P, n = a.n, np1 = n + 1, top = pow2_floor(n);
     float *thr_s = reinterpret_cast<float *>(smem);                 // [P][C][n+1]
     uint32_t *cnt_s = reinterpret_cast<uint32_t *>(thr_s + P * C * np1);  // [P][C][n+1]
-    float *red_s = reinterpret_cast<float *>(cnt_s + P * C * np1);  // [P][n+1]
     const uint32_t M = a.M, tile0 = blockIdx.x * (uint32_t)P;
     const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
     const int nwarps = nthr >> 5;
@@ -65,16 +91,7 @@ __global__ void __launch_bounds__(256) inner_kernel(InnerArgs a)
                     if (c < C) {
                         const float w = uniform23(xs[i]);
                         const float *T = thr_s + (pk * C + c) * np1;
-                        int lo = 1, len = n;      // first j in [1, n] with T[j] >= w, else n+1
-                        while (len > 0) {
-                            const int half = len >> 1;
-                            if (T[lo + half] < w) {
-                                lo += half + 1;
-                                len -= half + 1;
-                            } else {
-                                len = half;
-                            }
-                        }
+                        const int lo = lower_bound_pow2([T](int j) { return T[j]; }, n, top, w);
                         if (a.idx) a.idx[((size_t)kl * a.N + l) * C + c] = (uint8_t)lo;
                         if (lo <= n) atomicAdd(&cnt_s[(pk * C + c) * np1 + lo], 1u);
                     }
@@ -83,57 +100,49 @@ __global__ void __launch_bounds__(256) inner_kernel(InnerArgs a)
         }
     }
     __syncthreads();
+    // the counts of steps 1..n, P consecutive paths per (step, counterparty) row
+    for (int i = tid; i < n * C * P; i += nthr) {
+        const int pk = i % P, jc = i / P, c = jc % C, j = 1 + jc / C;
+        const uint32_t kl = tile0 + pk;
+        if (kl < M) {
+            const uint32_t v = cnt_s[(pk * C + c) * np1 + j];
+            const size_t o = ((size_t)j * C + c) * M + kl;
+            if (a.cnt16) a.cnt16[o] = (uint16_t)v;
+            else a.cnt32[o] = v;
+        }
+    }
+}
 
+template <int C>
+__global__ void __launch_bounds__(256) inner_target_kernel(InnerArgs a)
+{
+    const uint32_t kl = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kl >= a.M) return;
+    const size_t M = a.M;
+    const int n = a.n, np1 = n + 1, NPF = a.NPF;
     const float invN = 1.0f / (float)a.N;
-    for (int pf = 0; pf < a.NPF; ++pf) {
-        // H[pk][j] = sum_c V_c(j) count_c(j); loads of 8 consecutive paths share a sector
-        for (int i = tid; i < n * P; i += nthr) {
-            const int pk = i % P, j = 1 + i / P;
-            const uint32_t kl = tile0 + pk;
-            float h = 0.f;
-            if (kl < M) {
+    float S[kMaxPF];   // sum_{j > i} sum_c V_c(j) count_c(j) of each portfolio
+#pragma unroll
+    for (int pf = 0; pf < kMaxPF; ++pf) S[pf] = 0.f;
+    for (int j = n; j >= 1; --j) {
+        float cnt[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const size_t o = ((size_t)j * C + c) * M + kl;
+            cnt[c] = a.cnt16 ? (float)__ldg(a.cnt16 + o) : (float)__ldg(a.cnt32 + o);
+        }
+        const float bi = expf(__ldg(a.disc + (size_t)(j - 1) * M + kl)) * invN;   // beta_{j-1}^{-1} / N
+#pragma unroll
+        for (int pf = 0; pf < kMaxPF; ++pf) {
+            if (pf < NPF) {
+                float h = 0.f;
 #pragma unroll
                 for (int c = 0; c < C; ++c)
-                    h = fmaf(__ldg(a.expo + ((size_t)(pf * np1 + j) * C + c) * M + kl),
-                             (float)cnt_s[(pk * C + c) * np1 + j], h);
-            }
-            red_s[pk * np1 + j] = h;
-        }
-        __syncthreads();
-        // suffix sums S(i) = sum_{j > i} H(j), stored at position i+1
-        const int per = (n + 31) / 32;
-        for (int pk = warp; pk < P; pk += nwarps) {
-            float loc = 0.f;
-            for (int t = 0; t < per; ++t) {
-                const int j = 1 + lane * per + t;
-                if (j <= n) loc += red_s[pk * np1 + j];
-            }
-            __syncwarp();
-            float suf = loc;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const float v = __shfl_down_sync(0xffffffffu, suf, off);
-                if (lane + off < 32) suf += v;
-            }
-            float acc = suf - loc;
-            for (int t = per - 1; t >= 0; --t) {
-                const int j = 1 + lane * per + t;
-                if (j <= n) {
-                    acc += red_s[pk * np1 + j];
-                    red_s[pk * np1 + j] = acc;    // = S(j-1)
-                }
+                    h = fmaf(__ldg(a.expo + ((size_t)(pf * np1 + j) * C + c) * M + kl), cnt[c], h);
+                S[pf] += h;
+                a.targets[((size_t)pf * n + j - 1) * M + kl] = S[pf] * bi;
             }
         }
-        __syncthreads();
-        for (int i2 = tid; i2 < n * P; i2 += nthr) {
-            const int pk = i2 % P, i = i2 / P;
-            const uint32_t kl = tile0 + pk;
-            if (kl < M) {
-                const float disc = __ldg(a.disc + (size_t)i * M + kl);
-                a.targets[((size_t)pf * n + i) * M + kl] = red_s[pk * np1 + i + 1] * expf(disc) * invN;
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(256) oversim_kernel(OversimArgs a)
     __shared__ double red[8][3];
     const uint32_t M = a.M, kl = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = kl < M;
-    const int n = a.n, np1 = n + 1, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = a.n, np1 = n + 1, top = pow2_floor(n), lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int idx[2][C];
     float vs[2][C];
 #pragma unroll
@@ -182,16 +191,9 @@ __global__ void __launch_bounds__(256) oversim_kernel(OversimArgs a)
                     const int c = 4 * cb + t;
                     if (c < C) {
                         const float w = uniform23(xs[t]);
-                        int lo = 1, len = n;   // first j in [1, n] with T(j) >= w, else n+1
-                        while (len > 0) {
-                            const int h = len >> 1;
-                            if (__ldg(a.thr + ((size_t)(lo + h) * C + c) * M + kl) < w) {
-                                lo += h + 1;
-                                len -= h + 1;
-                            } else {
-                                len = h;
-                            }
-                        }
+                        const float *Tc = a.thr + (size_t)c * M + kl;   // T(j) at Tc[j C M]
+                        const int lo = lower_bound_pow2([Tc, M](int j) { return __ldg(Tc + (size_t)j * C * M); },
+                                                        n, top, w);
                         idx[l][c] = lo;
                         if (lo <= n) vs[l][c] = __ldg(a.expo + ((size_t)(a.pf * np1 + lo) * C + c) * M + kl);
                     }
@@ -323,20 +325,23 @@ cva_status launch_outer(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     return o->launch(s, seed, k0, st);
 }
 
-static size_t inner_smem(int P, int C, int n) { return (size_t)P * (n + 1) * 4 * (2 * C + 1); }
+static size_t inner_smem(int P, int C, int n) { return (size_t)P * (n + 1) * 4 * (2 * C); }
 
 template <int C>
 static cudaError_t launch_inner_t(const InnerArgs &args, size_t smem, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(inner_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(inner_count_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const unsigned blocks = (args.M + args.P - 1) / args.P;
-    inner_kernel<C><<<blocks, 32 * args.P, smem, st>>>(args);
+    inner_count_kernel<C><<<blocks, 32 * args.P, smem, st>>>(args);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    inner_target_kernel<C><<<(args.M + 255) / 256, 256, 0, st>>>(args);
     return cudaGetLastError();
 }
 
@@ -359,6 +364,8 @@ cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.disc = s.d_disc;
     args.targets = s.d_targets;
     args.idx = s.d_idx;
+    args.cnt16 = s.N <= 65535u ? static_cast<uint16_t *>(s.d_cnt) : nullptr;
+    args.cnt32 = s.N <= 65535u ? nullptr : static_cast<uint32_t *>(s.d_cnt);
     const size_t smem = inner_smem(P, s.C, s.n);
     static constexpr cudaError_t (*by_c[kMaxC])(const InnerArgs &, size_t, cudaStream_t) = {
         launch_inner_t<1>,  launch_inner_t<2>,  launch_inner_t<3>,  launch_inner_t<4>,
@@ -367,7 +374,7 @@ cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
         launch_inner_t<13>, launch_inner_t<14>, launch_inner_t<15>, launch_inner_t<16>};
     if (s.C < 1 || s.C > kMaxC) return fail(CVA_ENOTSUP, "inner kernel: 1 <= C <= 16");
     const cudaError_t e = by_c[s.C - 1](args, smem, st);
-    if (e != cudaSuccess) return cuda_fail(e, "inner_kernel launch");
+    if (e != cudaSuccess) return cuda_fail(e, "inner kernels launch");
     return CVA_OK;
 }
 
