@@ -35,34 +35,32 @@ struct InnerArgs {
     uint32_t *cnt32;                  // ... or these (larger N)
 };
 
-// First j in [1, n] with T(j) >= w for nondecreasing thresholds T, else n + 1: the
-// lower bound by a fixed sequence of power-of-two steps from top, the largest power
-// of two <= n (every lane of a warp runs the same steps; the comparisons select).
+// First j in [1, n] with T(j) >= w for nondecreasing thresholds T, else n + 1
+// (n <= 255): the lower bound by the fixed power-of-two steps 128, 64, ..., 1 (every
+// lane of a warp runs the same unrolled steps, so that the searches of several
+// counterparties interleave; a step past n reads nothing).
 template <class Thr>
-__device__ __forceinline__ int lower_bound_pow2(Thr T, int n, int top, float w)
+__device__ __forceinline__ int lower_bound_pow2(Thr T, int n, float w)
 {
     int pos = 0;   // T(1..pos) < w
-    for (int step = top; step > 0; step >>= 1) {
+#pragma unroll
+    for (int step = 128; step > 0; step >>= 1) {
         const int q = pos + step;
         if (q <= n && T(q) < w) pos = q;
     }
     return pos + 1;
 }
 
-__host__ __device__ __forceinline__ int pow2_floor(int n)
-{
-    int top = 1;
-    while (2 * top <= n) top *= 2;
-    return top;
-}
-
 template <int C>
 __global__ void __launch_bounds__(256) inner_count_kernel(InnerArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int P = a.P, n = a.n, np1 = n + 1, top = pow2_floor(n);
+    const int P = a.P, n = a.n, np1 = n + 1;
     float *thr_s = reinterpret_cast<float *>(smem);                 // [P][C][n+1]
-    uint32_t *cnt_s = reinterpret_cast<uint32_t *>(thr_s + P * C * np1);  // [P][C][n+1]
+    // counters [P][C][n+1]: two 16-bit counters per word when every count fits (N <= 65535)
+    uint32_t *cnt_s = reinterpret_cast<uint32_t *>(thr_s + P * C * np1);
+    const bool packed = a.cnt16 != nullptr;
+    const int n_words = packed ? (P * C * np1 + 1) / 2 : P * C * np1;
     const uint32_t M = a.M, tile0 = blockIdx.x * (uint32_t)P;
     const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
     const int nwarps = nthr >> 5;
@@ -72,7 +70,7 @@ __global__ void __launch_bounds__(256) inner_count_kernel(InnerArgs a)
         const uint32_t kl = tile0 + pk;
         thr_s[(pk * C + c) * np1 + j] = (kl < M) ? __ldg(a.thr + ((size_t)j * C + c) * M + kl) : 2.f;
     }
-    for (int i = tid; i < P * C * np1; i += nthr) cnt_s[i] = 0u;
+    for (int i = tid; i < n_words; i += nthr) cnt_s[i] = 0u;
     __syncthreads();
 
     for (int pk = warp; pk < P; pk += nwarps) {
@@ -91,9 +89,13 @@ __global__ void __launch_bounds__(256) inner_count_kernel(InnerArgs a)
                     if (c < C) {
                         const float w = uniform23(xs[i]);
                         const float *T = thr_s + (pk * C + c) * np1;
-                        const int lo = lower_bound_pow2([T](int j) { return T[j]; }, n, top, w);
+                        const int lo = lower_bound_pow2([T](int j) { return T[j]; }, n, w);
                         if (a.idx) a.idx[((size_t)kl * a.N + l) * C + c] = (uint8_t)lo;
-                        if (lo <= n) atomicAdd(&cnt_s[(pk * C + c) * np1 + lo], 1u);
+                        if (lo <= n) {
+                            const int ci = (pk * C + c) * np1 + lo;
+                            if (packed) atomicAdd(&cnt_s[ci >> 1], 1u << (16 * (ci & 1)));
+                            else atomicAdd(&cnt_s[ci], 1u);
+                        }
                     }
                 }
             }
@@ -105,7 +107,8 @@ __global__ void __launch_bounds__(256) inner_count_kernel(InnerArgs a)
         const int pk = i % P, jc = i / P, c = jc % C, j = 1 + jc / C;
         const uint32_t kl = tile0 + pk;
         if (kl < M) {
-            const uint32_t v = cnt_s[(pk * C + c) * np1 + j];
+            const int ci = (pk * C + c) * np1 + j;
+            const uint32_t v = packed ? (cnt_s[ci >> 1] >> (16 * (ci & 1))) & 0xffffu : cnt_s[ci];
             const size_t o = ((size_t)j * C + c) * M + kl;
             if (a.cnt16) a.cnt16[o] = (uint16_t)v;
             else a.cnt32[o] = v;
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(256) oversim_kernel(OversimArgs a)
     __shared__ double red[8][3];
     const uint32_t M = a.M, kl = blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = kl < M;
-    const int n = a.n, np1 = n + 1, top = pow2_floor(n), lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = a.n, np1 = n + 1, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int idx[2][C];
     float vs[2][C];
 #pragma unroll
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(256) oversim_kernel(OversimArgs a)
                         const float w = uniform23(xs[t]);
                         const float *Tc = a.thr + (size_t)c * M + kl;   // T(j) at Tc[j C M]
                         const int lo = lower_bound_pow2([Tc, M](int j) { return __ldg(Tc + (size_t)j * C * M); },
-                                                        n, top, w);
+                                                        n, w);
                         idx[l][c] = lo;
                         if (lo <= n) vs[l][c] = __ldg(a.expo + ((size_t)(a.pf * np1 + lo) * C + c) * M + kl);
                     }
@@ -325,7 +328,12 @@ cva_status launch_outer(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     return o->launch(s, seed, k0, st);
 }
 
-static size_t inner_smem(int P, int C, int n) { return (size_t)P * (n + 1) * 4 * (2 * C); }
+// thresholds (FP32) and counters (16-bit pairs when packed) of P paths
+static size_t inner_smem(int P, int C, int n, bool packed)
+{
+    const size_t cells = (size_t)P * C * (n + 1);
+    return 4 * cells + 4 * (packed ? (cells + 1) / 2 : cells);
+}
 
 template <int C>
 static cudaError_t launch_inner_t(const InnerArgs &args, size_t smem, cudaStream_t st)
@@ -357,16 +365,17 @@ cva_status launch_inner(Sim &s, uint64_t seed, uint64_t k0, cudaStream_t st)
     args.n = s.n;
     args.NPF = s.NPF;
     int P = (s.tune_inner_P >= 1 && s.tune_inner_P <= 8) ? s.tune_inner_P : 8;
-    while (P > 1 && inner_smem(P, s.C, s.n) > 160 * 1024) P >>= 1;
+    const bool packed = s.N <= 65535u;
+    while (P > 1 && inner_smem(P, s.C, s.n, packed) > 160 * 1024) P >>= 1;
     args.P = P;
     args.thr = s.d_thr;
     args.expo = s.d_expo;
     args.disc = s.d_disc;
     args.targets = s.d_targets;
     args.idx = s.d_idx;
-    args.cnt16 = s.N <= 65535u ? static_cast<uint16_t *>(s.d_cnt) : nullptr;
-    args.cnt32 = s.N <= 65535u ? nullptr : static_cast<uint32_t *>(s.d_cnt);
-    const size_t smem = inner_smem(P, s.C, s.n);
+    args.cnt16 = packed ? static_cast<uint16_t *>(s.d_cnt) : nullptr;
+    args.cnt32 = packed ? nullptr : static_cast<uint32_t *>(s.d_cnt);
+    const size_t smem = inner_smem(P, s.C, s.n, packed);
     static constexpr cudaError_t (*by_c[kMaxC])(const InnerArgs &, size_t, cudaStream_t) = {
         launch_inner_t<1>,  launch_inner_t<2>,  launch_inner_t<3>,  launch_inner_t<4>,
         launch_inner_t<5>,  launch_inner_t<6>,  launch_inner_t<7>,  launch_inner_t<8>,
