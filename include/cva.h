@@ -376,9 +376,11 @@ CVA_API cva_status cva_set_tiles(cva_sim *sim, int sim_block, int price_block, i
  * state every ckpt_every pricing dates (<= 16; sub-steps <= 4); the reverse sweep
  * recomputes each segment from its checkpoint. forward_only = 1 computes only
  * the smooth CVA_0 (grad_host may be NULL). Per-path adjoints are reduced in
- * FP64. The adjoint kernel is compiled for the fast-path shapes of cva_sim_create
- * with one portfolio, (E, C) = (1, 2 constant) and (10, 8 CIR); other shapes return
- * CVA_ENOTSUP. Allocates and frees its buffers; synchronises `stream`. */
+ * FP64. The fast-path shapes of cva_sim_create with one portfolio, (E, C) = (1, 2
+ * constant) and (10, 8 CIR), have compiled adjoint kernels; every other shape within
+ * the limits of cva_sim_create runs the run-time-shape adjoint (same arithmetic,
+ * slower: its per-path arrays live in local memory). A constant intensity's kappa_c,
+ * theta_c and nu_c receive 0. Allocates and frees its buffers; synchronises `stream`. */
 CVA_API cva_status cva_grad_cva0(const cva_model_desc *model, const cva_portfolio_desc *pf,
                                  const cva_grid *grid, uint64_t M, uint64_t seed, uint64_t k0,
                                  int ckpt_every, int forward_only, double *grad_host,

@@ -314,7 +314,7 @@ static const OuterInst *generic_outer()
 
 cva_status launch_adjoint(Sim &s, const AdjBuffers &b, uint64_t seed, uint64_t k0, uint32_t M, cudaStream_t st)
 {
-    if (s.generic) return fail(CVA_ENOTSUP, "no adjoint kernel for this model shape (compiled shapes only)");
+    if (s.generic) return generic_outer()->adjoint(s, b, seed, k0, M, st);
     const OuterInst *o = find_outer(s.E, s.C, s.CS, s.G, s.NPF);
     if (!o || o->G != s.Ginst || !o->adjoint) return fail(CVA_ENOTSUP, "no adjoint kernel for this model shape");
     return o->adjoint(s, b, seed, k0, M, st);
