@@ -90,14 +90,19 @@ __device__ __forceinline__ float2 column_sums64(const float (&v)[64], int lane)
 
 // Refit of (w3, b3) at epoch floor(E/2) for hidden width U: block i sums row i
 // of the CTAs' Gram partials of Z = [h2 | 1 | y - mu] (fixed order); the last
-// block solves the Jacobi-scaled normal equations of [h2 | 1] (w3, b3) = y - mu by
-// FP64 Cholesky (right-looking, the trailing update spread over the block) and two
-// triangular solves. A numerically singular system keeps the old (w3, b3). The
-// new values go to params and, when not null, to params2. Dynamic shared memory:
-// refit_smem_bytes(U).
+// block solves the Jacobi-scaled normal equations of [h2 | 1] (w3, b3) = y - mu.
+// It factorises the scaled matrix in FP32 (right-looking Cholesky, the trailing
+// update spread over the block) and refines x by FP64 residuals r = b - A x with
+// FP32 triangular solves, until |r| <= 1e-12 (|b| + |x|) (at most 6 rounds): the
+// FP64 solution, with the factorisation at the FP32 rate (FP64 arithmetic runs at a
+// small fraction of it on this GPU). A pivot below 1e-5 of the unit diagonal or no
+// convergence falls back to the FP64 Cholesky and triangular solves. A numerically
+// singular system keeps the old (w3, b3). The new values go to params and, when not
+// null, to params2. Dynamic shared memory: refit_smem_bytes(U).
 __host__ __device__ constexpr size_t refit_smem_bytes(int U)
 {
-    return ((size_t)(U + 2) * (U + 2) + 3 * (size_t)(U + 1) + 256) * sizeof(double);
+    return ((size_t)(U + 2) * (U + 2) + 4 * (size_t)(U + 1) + 256) * sizeof(double) +
+           ((size_t)(U + 1) * (U + 1) + 2 * (size_t)(U + 1)) * sizeof(float);
 }
 
 template <int U>
@@ -107,8 +112,9 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
     constexpr int Z = U + 2, n1 = U + 1;
     constexpr int ow3 = 34 * U + U * U, ob3 = ow3 + U;
     extern __shared__ double refit_smem[];
-    double *A = refit_smem, *sc = A + Z * Z, *xv = sc + n1, *inv_d = xv + n1, *half = inv_d + n1;
-    __shared__ int s_last, s_singular;
+    double *A = refit_smem, *sc = A + Z * Z, *xv = sc + n1, *inv_d = xv + n1, *half = inv_d + n1, *rv = half + 256;
+    float *Lf = reinterpret_cast<float *>(rv + n1), *invf = Lf + n1 * n1, *yf = invf + n1;
+    __shared__ int s_last, s_singular, s_conv;
     const int tid = threadIdx.x, lane = tid & 31;
     const int i = blockIdx.x;
     {   // row i of the total Gram matrix: nh fixed ranges of the partials per column,
@@ -146,6 +152,87 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
         A[r * Z + c] *= sc[r] * (c < n1 ? sc[c] : 1.0);
     }
     __syncthreads();
+
+    // ---- FP32 factor of the scaled matrix, FP64 iterative refinement ----
+    for (int e = tid; e < n1 * n1; e += blockDim.x) Lf[e] = (float)A[(e / n1) * Z + e % n1];
+    __syncthreads();
+    bool fb = false;   // the same in every thread: each decision reads the same shared values
+    for (int j = 0; j < n1; ++j) {
+        const float d = Lf[j * n1 + j];
+        if (!(d > 1e-5f)) {
+            fb = true;
+            break;
+        }
+        const float y = rsqrtf(d);
+        if (tid == 0) invf[j] = y;
+        if (j > 0)
+            for (int r = j + tid; r < n1; r += blockDim.x) Lf[r * n1 + j - 1] *= invf[j - 1];
+        const float id = 1.f / d;
+        const int c = j + 1 + (tid % U);
+        if (c < n1) {
+            const float lcj = Lf[c * n1 + j] * id;
+            for (int r = c + tid / U; r < n1; r += (int)blockDim.x / U) Lf[r * n1 + c] -= Lf[r * n1 + j] * lcj;
+        }
+        __syncthreads();
+    }
+    if (!fb) {
+        for (int r = tid; r < n1; r += blockDim.x) {
+            xv[r] = 0.0;
+            rv[r] = A[r * Z + n1];
+        }
+        __syncthreads();
+        bool conv = false;
+        for (int it = 0; it < 6 && !conv; ++it) {
+            if (tid < 32) {   // Lf Lf^T y = r in FP32 (column-oriented, one warp), x += y
+                for (int r = lane; r < n1; r += 32) yf[r] = (float)rv[r];
+                __syncwarp();
+                for (int j = 0; j < n1; ++j) {
+                    const float yj = yf[j] * invf[j];
+                    __syncwarp();
+                    if (lane == 0) yf[j] = yj;
+                    for (int r = j + 1 + lane; r < n1; r += 32) yf[r] -= Lf[r * n1 + j] * yj;
+                    __syncwarp();
+                }
+                for (int j = n1 - 1; j >= 0; --j) {
+                    const float xj = yf[j] * invf[j];
+                    __syncwarp();
+                    if (lane == 0) yf[j] = xj;
+                    for (int r = lane; r < j; r += 32) yf[r] -= Lf[j * n1 + r] * xj;
+                    __syncwarp();
+                }
+                for (int r = lane; r < n1; r += 32) xv[r] += (double)yf[r];
+            }
+            __syncthreads();
+            for (int r = tid; r < n1; r += blockDim.x) {   // r = b - A x in FP64
+                double acc = A[r * Z + n1];
+                for (int c2 = 0; c2 < n1; ++c2) acc -= A[r * Z + c2] * xv[c2];
+                rv[r] = acc;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double rmax = 0.0, bmax = 0.0, xmax = 0.0;
+                for (int r = 0; r < n1; ++r) {
+                    rmax = fmax(rmax, fabs(rv[r]));
+                    bmax = fmax(bmax, fabs(A[r * Z + n1]));
+                    xmax = fmax(xmax, fabs(xv[r]));
+                }
+                s_conv = rmax <= 1e-12 * (bmax + xmax);
+            }
+            __syncthreads();
+            conv = s_conv != 0;
+        }
+        if (conv) {
+            for (int r = tid; r < n1; r += blockDim.x) {
+                const float v = (float)(xv[r] * sc[r]);
+                const int p = r < U ? ow3 + r : ob3;
+                params[p] = v;
+                if (params2) params2[p] = v;
+            }
+            return;
+        }
+    }
+
+    // ---- FP64 Cholesky and triangular solves (the fallback) ----
     // lower Cholesky factor in place, one barrier per column. Every thread takes
     // column j's pivot d and 1/sqrt(d) by two Newton-Raphson steps
     // y <- y (3 - d y^2) / 2 from an FP32 seed (relative error 2^-22 -> 2^-44 ->
