@@ -156,11 +156,38 @@ __device__ __forceinline__ void cp_async4_zfill(uint32_t saddr, const void *g, b
 // per thread in the same order, the same flushes), its tiles copied by cp.async into
 // two buffers so that the copies of the next tile run during the products of this
 // one; the state columns are centred on path 0 in place once a tile has landed.
+// Work blocks of lsq_gram_async per row group: for MP <= 12 the 4 x 4 blocks (bi <= bj)
+// of the upper triangle; for MP = 32 and 40 the 4 x 8 blocks (bi, bj8) that touch it
+// (2 bj8 + 1 >= bi), each a pair of 4 x 4 output blocks: three 16-byte operand reads
+// per row for 32 FMAs instead of two for 16, so that a row costs a quarter of the
+// issue slots.
+template <int MP>
+struct GramWork {
+    static constexpr int NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2;
+    static constexpr bool wide = MP >= 32;
+    static constexpr int count8()
+    {
+        int n = 0;
+        for (int bi = 0; bi < NBLK; ++bi) n += MP / 8 - bi / 2;
+        return n;
+    }
+    static constexpr int NW = wide ? count8() : NUT;          // work blocks
+    static constexpr int NRG = kGramThreads / NW;             // row groups
+    static constexpr int NA = wide ? 32 : 16;                 // accumulators per thread
+};
+
+// index of the 4 x 4 output block (bi <= bj) in the partial's block order
+__host__ __device__ constexpr int gram_blk(int NBLK, int bi, int bj)
+{
+    return bi * NBLK - bi * (bi - 1) / 2 + (bj - bi);
+}
+
 template <int MP, int TR>
 __global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
 {
+    using GW = GramWork<MP>;
     constexpr int NBLK = MP / 4, NUT = NBLK * (NBLK + 1) / 2, RS = MP + 4, TS = TR * RS;
-    constexpr int NRG = kGramThreads / NUT;
+    constexpr int NRG = GW::NRG, NW = GW::NW, NA = GW::NA;
     extern __shared__ __align__(16) unsigned char smem[];
     float *tiles = reinterpret_cast<float *>(smem);          // [2][TR][RS]
     const int g = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
@@ -169,17 +196,18 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
     const uint32_t r_begin = (uint32_t)chunk * a.rows_per_chunk;
     const uint32_t r_end = min(a.M, r_begin + a.rows_per_chunk);
     const int mA = a.m + a.nt, F = a.F, nload = a.F + a.nt;   // copied columns 1..F+nt: state, targets
-    const int b = tid % NUT, rg = tid / NUT;
-    int bi = 0, bj = 0;
+    const int b = tid % NW, rg = tid / NW;
+    int bi = 0, bj = 0;   // 4 x 4: block (bi, bj); 4 x 8: rows 4 bi.., columns 8 bj..
     {
         int t = b;
         for (int i = 0; i < NBLK; ++i) {
-            if (t < NBLK - i) {
+            const int w = GW::wide ? MP / 8 - i / 2 : NBLK - i;
+            if (t < w) {
                 bi = i;
-                bj = i + t;
+                bj = (GW::wide ? i / 2 : i) + t;
                 break;
             }
-            t -= NBLK - i;
+            t -= w;
         }
     }
     __shared__ float c0[40];
@@ -198,10 +226,10 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    double dacc[16];
-    float acc[16];
+    double dacc[NA];
+    float acc[NA];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < NA; ++i) {
         dacc[i] = 0.0;
         acc[i] = 0.f;
     }
@@ -224,15 +252,24 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
         if (rg < NRG) {
             for (int r = rg; r < TR; r += NRG) {
                 const float4 x = *reinterpret_cast<const float4 *>(tile + r * RS + 4 * bi);
-                const float4 y = *reinterpret_cast<const float4 *>(tile + r * RS + 4 * bj);
-                const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+                const float xv[4] = {x.x, x.y, x.z, x.w};
+                float yv[NA / 4];
+                if constexpr (GW::wide) {
+                    const float4 y0 = *reinterpret_cast<const float4 *>(tile + r * RS + 8 * bj);
+                    const float4 y1 = *reinterpret_cast<const float4 *>(tile + r * RS + 8 * bj + 4);
+                    yv[0] = y0.x; yv[1] = y0.y; yv[2] = y0.z; yv[3] = y0.w;
+                    yv[4] = y1.x; yv[5] = y1.y; yv[6] = y1.z; yv[7] = y1.w;
+                } else {
+                    const float4 y = *reinterpret_cast<const float4 *>(tile + r * RS + 4 * bj);
+                    yv[0] = y.x; yv[1] = y.y; yv[2] = y.z; yv[3] = y.w;
+                }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u * 4 + v] = fmaf(xv[u], yv[v], acc[u * 4 + v]);
+                    for (int v = 0; v < NA / 4; ++v) acc[u * (NA / 4) + v] = fmaf(xv[u], yv[v], acc[u * (NA / 4) + v]);
                 if (++since_flush == 512) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
+                    for (int i = 0; i < NA; ++i) {
                         dacc[i] += (double)acc[i];
                         acc[i] = 0.f;
                     }
@@ -242,12 +279,26 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
         }
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) dacc[i] += (double)acc[i];
+    for (int i = 0; i < NA; ++i) dacc[i] += (double)acc[i];
     __syncthreads();
     double *red = reinterpret_cast<double *>(smem);        // [NRG][NUT*16]
-    if (rg < NRG)
+    if (rg < NRG) {
+        if constexpr (GW::wide) {   // the halves of the 4 x 8 block on or above the diagonal
 #pragma unroll
-        for (int i = 0; i < 16; ++i) red[(size_t)rg * NUT * 16 + b * 16 + i] = dacc[i];
+            for (int h = 0; h < 2; ++h) {
+                const int bj4 = 2 * bj + h;
+                if (bj4 < bi) continue;
+                double *dst = red + (size_t)rg * NUT * 16 + gram_blk(NBLK, bi, bj4) * 16;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) dst[u * 4 + v] = dacc[u * 8 + 4 * h + v];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) red[(size_t)rg * NUT * 16 + b * 16 + i] = dacc[i];
+        }
+    }
     __syncthreads();
     double *out = a.part + ((size_t)g * a.chunks + chunk) * NUT * 16;
     for (int e = tid; e < NUT * 16; e += kGramThreads) {
@@ -263,7 +314,7 @@ __global__ void __launch_bounds__(kGramThreads) lsq_gram_async(LsqArgs a)
 template <int MP, int TR>
 cva_status launch_gram(const LsqArgs &a, dim3 grid, cudaStream_t st)
 {
-    constexpr int NUT = (MP / 4) * (MP / 4 + 1) / 2, NRG = kGramThreads / NUT;
+    constexpr int NUT = (MP / 4) * (MP / 4 + 1) / 2, NRG = GramWork<MP>::NRG;
     if (a.basis == CVA_BASIS_LINEAR) {
         const size_t tiles = 2 * (size_t)TR * (MP + 4) * sizeof(float), red = (size_t)NRG * NUT * 16 * sizeof(double);
         const size_t smem = tiles > red ? tiles : red;
@@ -885,7 +936,7 @@ PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
 template <int MP, int TR>
 cva_status static_gram_attr()
 {
-    constexpr int NUT = (MP / 4) * (MP / 4 + 1) / 2, NRG = kGramThreads / NUT;
+    constexpr int NUT = (MP / 4) * (MP / 4 + 1) / 2, NRG = GramWork<MP>::NRG;
     const size_t tiles = 2 * (size_t)TR * (MP + 4) * sizeof(float), red = (size_t)NRG * NUT * 16 * sizeof(double);
     CVA_CUDA_TRY(cudaFuncSetAttribute(lsq_gram_async<MP, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(tiles > red ? tiles : red)));
