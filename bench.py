@@ -48,6 +48,8 @@ def parse():
                    help="skip the 2^20-path width-128 network measurement")
     p.add_argument("--no-validation", action="store_true",
                    help="skip the twin, oversimulation and nested Monte Carlo measurements (profiling runs)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the simulation's cost against N and the S = 25 sub-step shape")
     p.add_argument("--tiles", default=None,
                    help="sim_block,price_block,inner_paths,lsq_chunks,portfolios_per_price_block for the timed "
                         "simulation (profiling runs; default: the library's defaults)")
@@ -471,6 +473,33 @@ def main():
                    "regression": "the step's" + (" NN+ network" if use_mlp else " least squares"),
                    "note": "kappa: cost of an outer path in inner draws from two simulations of the same M (eq. (l:ratio))"}
 
+    # ---- the simulation's cost against N at fixed M, and at the paper's S = 25 sub-steps ----
+    extras = None
+    if rank == 0 and not args.no_extras and wl.name == "paper":
+        def time_sim(grid, Nx, reps=5):
+            xs = api.Simulation(wl.model, wl.portfolios, grid, wl.M, Nx, profile=True)
+            xs.run(1, k0=k0)
+            torch.cuda.synchronize()
+            parts = []
+            for r in range(reps):
+                xs.run(2 + r, k0=k0)
+                torch.cuda.synchronize()
+                parts.append(xs.kernel_ms())
+            xs.close()
+            med = np.median(np.array(parts), axis=0)
+            return {"ms": float(med.sum()), "path_simulation_ms": float(med[0]), "pricing_ms": float(med[1]),
+                    "inner_defaults_ms": float(med[2])}
+        by_N = {f"N={Nx}": time_sim(wl.grid, Nx) for Nx in (1, 8, 64, 256, 1024)}
+        g25 = workload.Grid(wl.grid.horizon, wl.grid.n_steps, 25)
+        s25 = time_sim(g25, wl.N)
+        s25["value"] = wl.M * wl.N * n / (s25["ms"] / 1e3)
+        s25["unit"] = UNIT
+        extras = {"simulation_vs_N": by_N,
+                  "note_N": f"M = {wl.M}, n = {n}: the inner draws are the only part that grows with N",
+                  "substeps_25": s25,
+                  "note_S": "the paper's Euler grid (25 sub-steps per pricing step), N as configured",
+                  "timing": "median of 5 simulations after one warm-up, CUDA events of the library (profiling flag)"}
+
     # ---- nested Monte Carlo reference at the middle date (first 16384 paths, 1024 copies) ----
     nested = None
     if rank == 0 and not args.no_validation:
@@ -840,7 +869,7 @@ def main():
                "cva0": c0[0], "cva0_se": c0[1],
                "roofline": (mlp_roof if (mlp_roof and mlp_roof["ms"] > roof["ms"]) else roof),
                "mlp_roofline": mlp_roof, "twin_validation": twin, "oversimulation": oversim,
-               "nested_validation": nested,
+               "nested_validation": nested, "paper_shape_extras": extras,
                "adjoint_forward": adj, "batched": batched, "alive_regression": alive,
                "precision": precision,
                "cpu_baseline": cpu, "errors_vs_oracle": errors,
