@@ -114,8 +114,6 @@ NCU_TRAFFIC = {
                    "profile": "profiles/sim_price_inner_kernels_paper_32k.md"},
     "price_kernel": {"bytes_per_unit": (263.78e6 + 81.86e6) / (32768 * 100), "unit": "path-date",
                      "profile": "profiles/sim_price_inner_kernels_paper_32k.md"},
-    "inner_kernel": {"bytes_per_unit": (222.86e6 + 11.39e6) / 32768, "unit": "path",
-                     "profile": "profiles/sim_price_inner_kernels_paper_32k.md"},
     # one launch = one epoch at one date; captured at 65536 paths, scaled by the paths
     "mlp_train_kernel": {"bytes_per_unit": (7.532032e6 + 0.0) / 65536, "unit": "path",
                          "profile": "profiles/mlp_train_kernel_paper_64k.md"},
