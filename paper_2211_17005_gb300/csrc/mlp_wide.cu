@@ -862,6 +862,10 @@ struct WideWork {
     void *buf = nullptr;
     size_t cap = 0;
     bool attrs = false;
+    // the full-sample loss passes of epochs 1..E-1 and the predictions run on this
+    // low-priority stream, on the SMs the trainer's grid leaves free
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_train = nullptr, ev_side = nullptr;
 };
 std::mutex g_wide_mu;
 std::atomic<uint32_t> g_grid_polls{kGridPolls};
@@ -909,6 +913,11 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
         CVA_CUDA_TRY(cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WL::bytes));
         CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_refit_kernel<WL::U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)refit_smem_bytes(WL::U)));
+        int least = 0, greatest = 0;
+        CVA_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CVA_CUDA_TRY(cudaStreamCreateWithPriority(&w.side, cudaStreamNonBlocking, least));
+        CVA_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_train, cudaEventDisableTiming));
+        CVA_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_side, cudaEventDisableTiming));
         w.attrs = true;
     }
     int per_sm = 0;
@@ -917,6 +926,11 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     const int G = wide_grid(tiles_per_batch, sms);
     const uint64_t tiles = M / kRows;
     const int sweep_grid = (int)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
+    // passes that overlap the training take the SMs its grid leaves (one CTA per SM on
+    // either side); with fewer than 8 of them every pass stays on st with the whole GPU
+    const bool overlap = sms - G >= 8;
+    const int side_grid = overlap ? sms - G : sweep_grid;
+    const cudaStream_t sst = overlap ? w.side : st;
 
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_vec = al((size_t)WL::NPpad * 4), b_img = al((size_t)WL::img_elems * 2),
@@ -927,6 +941,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     const size_t need = 5 * b_vec + b_img + b_stats + b_snaps + b_part + b_flags + 2 * b_bl + b_G + b_pl + b_pg;
     if (w.cap < need) {
         CVA_CUDA_TRY(cudaStreamSynchronize(st));
+        CVA_CUDA_TRY(cudaStreamSynchronize(w.side));
         if (w.buf) cudaFree(w.buf);
         w.buf = nullptr;
         w.cap = 0;
@@ -1018,7 +1033,13 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
             CVA_CUDA_TRY(cudaLaunchKernelEx(&cfg, wide_train_kernel, ta, tm));
             if (timed) CVA_CUDA_TRY(cudaEventRecord(t1, st));
             steps_left -= ta.n_steps;
-            if (max_steps > 0 && steps_left <= 0) return CVA_OK;
+            if (max_steps > 0 && steps_left <= 0) {
+                if (overlap) {   // passes already requested finish before the caller's stream moves on
+                    CVA_CUDA_TRY(cudaEventRecord(w.ev_side, sst));
+                    CVA_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_side, 0));
+                }
+                return CVA_OK;
+            }
             if (e == epochs / 2) {
                 WSweepArgs g = sw;
                 g.mode = 1;
@@ -1031,22 +1052,38 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
                                                                                  params_dev, snap);
                 CVA_CUDA_TRY(cudaGetLastError());
             }
+            // the epoch's loss from its snapshot: beside the next epoch's training on the
+            // free SMs, the last epoch's with the whole GPU (the next date waits for it)
             sw.mode = 0;
             sw.theta = snap;
             sw.epoch = e;
-            wide_sweep_kernel<<<sweep_grid, kWThreads, WL::bytes, st>>>(sw, tm);
+            if (overlap) {
+                CVA_CUDA_TRY(cudaEventRecord(w.ev_train, st));
+                CVA_CUDA_TRY(cudaStreamWaitEvent(sst, w.ev_train, 0));
+            }
+            wide_sweep_kernel<<<e == epochs ? sweep_grid : side_grid, kWThreads, WL::bytes, sst>>>(sw, tm);
             CVA_CUDA_TRY(cudaGetLastError());
+        }
+        // the best parameters are known once the last loss pass ran: the next date (st)
+        // starts from them; the predictions (side) overlap its training
+        if (overlap) {
+            CVA_CUDA_TRY(cudaEventRecord(w.ev_side, sst));
+            CVA_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_side, 0));
         }
         if (pred0) {
             WSweepArgs pv = sw;
             pv.mode = 2;
             pv.theta = best[par];
             pv.pred = pred0 + (size_t)d * M;
-            wide_sweep_kernel<<<sweep_grid, kWThreads, WL::bytes, st>>>(pv, tm);
+            wide_sweep_kernel<<<side_grid, kWThreads, WL::bytes, sst>>>(pv, tm);
             CVA_CUDA_TRY(cudaGetLastError());
         }
         if (d == 0)
             CVA_CUDA_TRY(cudaMemcpyAsync(params_dev, best[par], WL::NP * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    if (overlap) {   // the caller's stream sees every pass
+        CVA_CUDA_TRY(cudaEventRecord(w.ev_side, sst));
+        CVA_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_side, 0));
     }
     return CVA_OK;
 }
