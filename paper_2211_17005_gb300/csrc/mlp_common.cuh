@@ -147,9 +147,12 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
     __syncthreads();
     for (int j = tid; j < n1; j += blockDim.x) sc[j] = A[j * Z + j] > 0.0 ? 1.0 / sqrt(A[j * Z + j]) : 0.0;
     __syncthreads();
+    // Jacobi scaling to a unit diagonal. A unit that is zero on every path (a ReLU dead
+    // on the whole sample) has a zero row and column: it gets a unit diagonal and a zero
+    // right-hand side, so its weight is 0, the minimum-norm least-squares choice.
     for (int e = tid; e < n1 * (n1 + 1); e += blockDim.x) {
         const int r = e / (n1 + 1), c = e % (n1 + 1);
-        A[r * Z + c] *= sc[r] * (c < n1 ? sc[c] : 1.0);
+        A[r * Z + c] = (r == c && sc[r] == 0.0) ? 1.0 : A[r * Z + c] * sc[r] * (c < n1 ? sc[c] : 1.0);
     }
     __syncthreads();
 
@@ -241,16 +244,23 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
     // 1/sqrt(d) during the next column's step, which does not read it. Thread t
     // updates column j + 1 + (t mod U), rows c + (t / U) + k (blockDim / U). The
     // diagonal of the factor is kept as its reciprocal inv_d.
+    // A pivot at or below 1e-12 of the unit diagonal means the column lies in the span
+    // of the columns kept before it: it is dropped (1/sqrt(d) taken as 0, so it updates
+    // nothing and its weight is 0). The fitted values, the projection of the targets on
+    // the span, are the least-squares ones. A pivot that is not finite leaves the
+    // parameters as they are.
     for (int j = 0; j < n1; ++j) {
-        double d = A[j * Z + j];
-        const bool bad = !(d > 1e-12);
-        if (bad) d = 1.0;
-        double y = (double)rsqrtf((float)d);
-        y = y * (1.5 - 0.5 * d * y * y);
-        y = y * (1.5 - 0.5 * d * y * y);
+        const double d = A[j * Z + j];
+        const bool drop = !(d > 1e-12);
+        double y = 0.0;
+        if (!drop) {
+            y = (double)rsqrtf((float)d);
+            y = y * (1.5 - 0.5 * d * y * y);
+            y = y * (1.5 - 0.5 * d * y * y);
+        }
         if (tid == 0) {
             inv_d[j] = y;
-            if (bad) s_singular = 1;
+            if (!isfinite(d)) s_singular = 1;
         }
         if (j > 0)
             for (int r = j + tid; r < n1; r += blockDim.x) A[r * Z + j - 1] *= inv_d[j - 1];

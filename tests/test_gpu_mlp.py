@@ -169,3 +169,38 @@ def test_kernel_timing_counts_every_train_launch(api, u):
     assert torch.equal(p_on, p_off)
     api.mlp_fit(xd, yd, api.mlp_pack(p0, u), hidden=u, n_batches=nb, epochs=E)
     assert api.mlp_kernel_timing(False) == {"ms": 0.0, "launches": 0}
+
+
+@pytest.mark.parametrize("u", [64, 128])
+@pytest.mark.parametrize("twins", [False, True])
+def test_refit_with_dead_and_duplicate_units(api, u, twins):
+    """The closed-form output-layer refit (Algorithm 1, epoch floor(E/2)) with ReLU units
+    that are zero on every path (bias -50) and, with twins, one unit duplicated. The
+    least-squares fit is unique in its fitted values, not in its weights: a dead unit's
+    weight is free (the minimum-norm choice, the oracle's lstsq, gives it 0) and only the
+    sum of the twins' weights is fixed. With a zero step size only the refit changes the
+    parameters, so the loss trace is flat but for one drop, at epoch 2 of 4, to the
+    oracle's refitted loss."""
+    M, nb, E = 4096 * 4, 32, 4
+    Y, xi = _problem(M, seed=3)
+    p0 = W.mlp_init(27, u, seed=14)
+    dead = [1, 7, 30]
+    p0["b2"][dead] = -50.0
+    if twins:
+        p0["W2"][12] = p0["W2"][11]
+        p0["b2"][12] = p0["b2"][11]
+    flat = api.mlp_pack(p0, u)
+    _, losses = api.mlp_fit(torch.from_numpy(xi).cuda(), torch.from_numpy(Y).cuda(), flat, hidden=u,
+                            n_batches=nb, epochs=E, lr=0.0, want_pred=False)
+    Z, _, _ = omlp.standardize(Y.astype(np.float64).T)
+    trace = []
+    best_p, _ = omlp.base_alg(p0, Z, xi.astype(np.float64), n_batches=nb, epochs=E, lr=0.0, trace=trace)
+    assert trace[1] < 0.5 * trace[0], trace                      # the refit matters here
+    assert losses[0] == pytest.approx(trace[0], rel=2e-2), (losses, trace)
+    assert losses[1] == pytest.approx(trace[1], rel=3e-2), (losses, trace)
+    assert np.all(np.abs(np.diff(losses[1:])) <= 1e-6 * losses[1]), losses
+    got = api.mlp_unpack(flat.cpu(), u, 27)
+    assert np.all(got["w3"][dead] == 0.0), got["w3"][dead]
+    if twins:
+        s_gpu, s_or = got["w3"][11] + got["w3"][12], best_p["w3"][11] + best_p["w3"][12]
+        assert abs(s_gpu - s_or) <= 0.05 * np.abs(best_p["w3"]).max(), (s_gpu, s_or)
