@@ -952,7 +952,7 @@ cva_status mlp_prepare(int dev, int sms, uint64_t M, int tiles_per_batch, int n_
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_adam = al(2 * (size_t)L::NPpad * 4), b_best = al((size_t)L::NPpad * 4),
                  b_stats = al((size_t)n_dates * 2 * kIn * 4), b_snaps = al((size_t)epochs * L::NPpad * 4), b_bl = al(8),
-                 b_G = al((size_t)Z * Z * 8), b_pl = al((size_t)pl.sweep_grid * 8),
+                 b_G = al(refit_g_bytes(64)), b_pl = al((size_t)pl.sweep_grid * 8),
                  b_pg = al((size_t)pl.sweep_grid * Z * Z * 8);
     const size_t need = b_adam + 2 * b_best + b_stats + b_snaps + 2 * b_bl + b_G + b_pl + b_pg;
     if (w.cap < need) {

@@ -88,21 +88,124 @@ __device__ __forceinline__ float2 column_sums64(const float (&v)[64], int lane)
     return make_float2(r[0], r[1]);
 }
 
-// Refit of (w3, b3) at epoch floor(E/2) for hidden width U: block i sums row i
-// of the CTAs' Gram partials of Z = [h2 | 1 | y - mu] (fixed order); the last
-// block solves the Jacobi-scaled normal equations of [h2 | 1] (w3, b3) = y - mu.
-// It factorises the scaled matrix in FP32 (right-looking Cholesky, the trailing
-// update spread over the block) and refines x by FP64 residuals r = b - A x with
-// FP32 triangular solves, until |r| <= 1e-12 (|b| + |x|) (at most 6 rounds): the
-// FP64 solution, with the factorisation at the FP32 rate (FP64 arithmetic runs at a
-// small fraction of it on this GPU). A pivot below 1e-5 of the unit diagonal or no
-// convergence falls back to the FP64 Cholesky and triangular solves. A numerically
-// singular system keeps the old (w3, b3). The new values go to params and, when not
-// null, to params2. Dynamic shared memory: refit_smem_bytes(U).
+// Refit of (w3, b3) at epoch floor(E/2) for hidden width U: block i sums row i of
+// the CTAs' Gram partials of Z = [h2 | 1 | y - mu] (fixed order) and stores it in FP64
+// (G) and FP32 (Gf, after G); the last block solves the normal equations of
+// [h2 | 1] (w3, b3) = y - mu Jacobi-scaled to a unit diagonal (S A S z = S b, x = S z;
+// any positive S gives the same x, so S is taken at FP32 accuracy). It factorises the
+// scaled matrix in FP32 (right-looking Cholesky over register tiles, one barrier per
+// column) and refines z by FP64 residuals of the unscaled system, r = b - A x, with
+// FP32 blocked triangular solves, until |S r| <= 1e-12 (|S b| + |z|) (at most 6
+// rounds): the FP64 solution, with the factorisation at the FP32 rate (FP64
+// arithmetic runs at a small fraction of it on this GPU). A pivot below 1e-5 of the
+// unit diagonal or no convergence falls back to the FP64 Cholesky and triangular
+// solves of the scaled system. A ReLU unit that is zero on every path has a zero row
+// and column: it gets a unit diagonal and the weight 0 (the minimum-norm choice). The
+// FP64 factor drops a column whose pivot is at or below 1e-12 (it lies in the span of
+// the columns before it); a pivot that is not finite keeps the old (w3, b3). The new
+// values go to params and, when not null, to params2. Dynamic shared memory:
+// refit_smem_bytes(U); G holds refit_g_bytes(U).
+
+// Register tiles of the FP32 factor: side T, NT tile rows over the U + 1 unknowns,
+// one tile of the lower triangle per thread.
+__host__ __device__ constexpr int refit_tile(int U) { return U >= 128 ? 8 : 4; }
+__host__ __device__ constexpr int refit_ntiles(int U) { return (U + 1 + refit_tile(U) - 1) / refit_tile(U); }
+__host__ __device__ constexpr size_t refit_g_bytes(int U)
+{
+    return (size_t)(U + 2) * (U + 2) * (sizeof(double) + sizeof(float));
+}
 __host__ __device__ constexpr size_t refit_smem_bytes(int U)
 {
-    return ((size_t)(U + 2) * (U + 2) + 4 * (size_t)(U + 1) + 256) * sizeof(double) +
-           ((size_t)(U + 1) * (U + 1) + 2 * (size_t)(U + 1)) * sizeof(float);
+    return ((size_t)(U + 2) * (U + 2) + 3 * (size_t)(U + 1) + 256) * sizeof(double) +
+           5 * (size_t)refit_ntiles(U) * refit_tile(U) * sizeof(float);
+}
+
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only), its group commit
+// and the wait for every copy of this thread.
+__device__ __forceinline__ void refit_cp16(void *s, const void *g)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(s)), "l"(g)
+                 : "memory");
+}
+__device__ __forceinline__ void refit_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void refit_cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Largest v over the warp, in every lane.
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// y <- (L L^T)^{-1} y in FP32 for the factor held in register tiles (the tile (R, C)
+// of side T in each owning thread, the reciprocal diagonal in invf): blocked
+// forward and back substitution over the NT tile columns, two barriers per tile
+// column. The thread of a diagonal tile solves its T x T triangle; the threads of
+// the tiles below it (forward) or left of it (backward) then update their own block
+// of y, a different block for each thread.
+template <int T, int NT>
+__device__ __forceinline__ void refit_tile_solve(const float (&a)[T][T], bool own, int R, int C, float *yf,
+                                                 const float *invf)
+{
+    for (int J = 0; J < NT; ++J) {
+        if (own && R == J && C == J) {
+            float y[T];
+#pragma unroll
+            for (int q = 0; q < T; ++q) y[q] = yf[J * T + q];
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                y[k] *= invf[J * T + k];
+#pragma unroll
+                for (int ii = k + 1; ii < T; ++ii) y[ii] = fmaf(-a[ii][k], y[k], y[ii]);
+            }
+#pragma unroll
+            for (int q = 0; q < T; ++q) yf[J * T + q] = y[q];
+        }
+        __syncthreads();
+        if (own && C == J && R > J) {
+            float yj[T];
+#pragma unroll
+            for (int k = 0; k < T; ++k) yj[k] = yf[J * T + k];
+#pragma unroll
+            for (int ii = 0; ii < T; ++ii) {
+                float s = 0.f;
+#pragma unroll
+                for (int k = 0; k < T; ++k) s = fmaf(a[ii][k], yj[k], s);
+                yf[R * T + ii] -= s;
+            }
+        }
+        __syncthreads();
+    }
+    for (int J = NT - 1; J >= 0; --J) {
+        if (own && R == J && C == J) {
+            float y[T];
+#pragma unroll
+            for (int q = 0; q < T; ++q) y[q] = yf[J * T + q];
+#pragma unroll
+            for (int k = T - 1; k >= 0; --k) {
+                y[k] *= invf[J * T + k];
+#pragma unroll
+                for (int ii = 0; ii < k; ++ii) y[ii] = fmaf(-a[k][ii], y[k], y[ii]);
+            }
+#pragma unroll
+            for (int q = 0; q < T; ++q) yf[J * T + q] = y[q];
+        }
+        __syncthreads();
+        if (own && R == J && C < J) {
+            float xj[T];
+#pragma unroll
+            for (int q = 0; q < T; ++q) xj[q] = yf[J * T + q];
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int ii = 0; ii < T; ++ii) s = fmaf(a[ii][k], xj[ii], s);
+                yf[C * T + k] -= s;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 template <int U>
@@ -110,20 +213,31 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
                                                         float *params, float *params2)
 {
     constexpr int Z = U + 2, n1 = U + 1;
+    constexpr int T = refit_tile(U), NT = refit_ntiles(U), P = NT * T;
+    static_assert(NT * (NT + 1) / 2 <= 256, "one register tile per thread");
     constexpr int ow3 = 34 * U + U * U, ob3 = ow3 + U;
     extern __shared__ double refit_smem[];
-    double *A = refit_smem, *sc = A + Z * Z, *xv = sc + n1, *inv_d = xv + n1, *half = inv_d + n1, *rv = half + 256;
-    float *Lf = reinterpret_cast<float *>(rv + n1), *invf = Lf + n1 * n1, *yf = invf + n1;
-    __shared__ int s_last, s_singular, s_conv;
-    const int tid = threadIdx.x, lane = tid & 31;
+    double *A = refit_smem, *sc = A + Z * Z, *xv = sc + n1, *inv_d = xv + n1, *half = inv_d + n1;
+    float *colbuf = reinterpret_cast<float *>(half + 256), *invf = colbuf + 2 * P, *yf = invf + P, *scf = yf + P;
+    __shared__ int s_last, s_singular;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = (int)blockDim.x >> 5;
     const int i = blockIdx.x;
+    float *Gf = reinterpret_cast<float *>(G + Z * Z);
     {   // row i of the total Gram matrix: nh fixed ranges of the partials per column,
-        // added in range order
+        // each added in order (the loads issued 32 at a time), the ranges added in order
         const int nh = (int)blockDim.x / Z > 0 ? (int)blockDim.x / Z : 1;
         for (int t = tid; t < nh * Z; t += blockDim.x) {
             const int c = t % Z, h = t / Z;
+            const int b0 = nparts * h / nh, b1 = nparts * (h + 1) / nh;
+            const double *src = part + (size_t)i * Z + c;
             double sum = 0.0;
-            for (int b = nparts * h / nh; b < nparts * (h + 1) / nh; ++b) sum += __ldg(part + (size_t)b * Z * Z + i * Z + c);
+            for (int b = b0; b < b1; b += 32) {
+                double v[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = b + q < b1 ? __ldg(src + (size_t)(b + q) * Z * Z) : 0.0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) sum += v[q];
+            }
             half[t] = sum;
         }
         __syncthreads();
@@ -131,6 +245,7 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
             double sum = 0.0;
             for (int h = 0; h < nh; ++h) sum += half[h * Z + c];
             G[i * Z + c] = sum;
+            Gf[i * Z + c] = (float)sum;
         }
     }
     __threadfence();
@@ -139,94 +254,166 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int e = tid; e < Z * Z; e += blockDim.x) A[e] = __ldcg(G + e);
+    // the FP64 matrix reaches shared memory by asynchronous copies while the FP32
+    // factor runs (waited for before the first residual or the fallback)
+    for (int e = tid; e < Z * Z / 2; e += blockDim.x) refit_cp16(A + 2 * e, G + 2 * e);
+    refit_cp_commit();
     if (tid == 0) {
         *count = 0u;
         s_singular = 0;
     }
-    __syncthreads();
-    for (int j = tid; j < n1; j += blockDim.x) sc[j] = A[j * Z + j] > 0.0 ? 1.0 / sqrt(A[j * Z + j]) : 0.0;
-    __syncthreads();
-    // Jacobi scaling to a unit diagonal. A unit that is zero on every path (a ReLU dead
-    // on the whole sample) has a zero row and column: it gets a unit diagonal and a zero
-    // right-hand side, so its weight is 0, the minimum-norm least-squares choice.
-    for (int e = tid; e < n1 * (n1 + 1); e += blockDim.x) {
-        const int r = e / (n1 + 1), c = e % (n1 + 1);
-        A[r * Z + c] = (r == c && sc[r] == 0.0) ? 1.0 : A[r * Z + c] * sc[r] * (c < n1 ? sc[c] : 1.0);
+    for (int j = tid; j < P; j += blockDim.x) {
+        double s = 0.0;
+        if (j < n1) {
+            const double d = __ldcg(G + j * Z + j);
+            const float df = (float)d;
+            s = d > 0.0 ? (df > 1e-30f && df < 1e30f ? (double)rsqrtf(df) : 1.0 / sqrt(d)) : 0.0;
+            sc[j] = s;
+        }
+        scf[j] = (float)s;
+        invf[j] = 0.f;
+        colbuf[j] = colbuf[P + j] = 0.f;
     }
     __syncthreads();
 
-    // ---- FP32 factor of the scaled matrix, FP64 iterative refinement ----
-    for (int e = tid; e < n1 * n1; e += blockDim.x) Lf[e] = (float)A[(e / n1) * Z + e % n1];
+    // ---- FP32 factor of the scaled matrix over register tiles ----
+    // Thread t owns the lower-triangle tile (R, C), R >= C, of side T; tiles are
+    // numbered column by column, so the threads of finished tile columns idle
+    // together. Rows and columns past U are zero. Column j of the trailing matrix is
+    // published in colbuf (two buffers, alternating): at step j every thread takes
+    // the pivot d = colbuf[j], writes l = colbuf / sqrt(d) into column j of its tile
+    // and subtracts l_r l_c from its entries (r, c), r >= c > j; the owners of column
+    // j + 1 then publish it. The factor's diagonal is kept as its reciprocal invf.
+    int R = NT, C = NT;
+    {
+        int rem = tid, c = 0;
+        while (c < NT && rem >= NT - c) {
+            rem -= NT - c;
+            ++c;
+        }
+        if (c < NT) {
+            C = c;
+            R = c + rem;
+        }
+    }
+    const bool own = C < NT;
+    float a[T][T];
+#pragma unroll
+    for (int ii = 0; ii < T; ++ii)
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            const int r = R * T + ii, c = C * T + k;
+            float v = 0.f;
+            if (own && r < n1 && c < n1 && r >= c)
+                v = (r == c && scf[r] == 0.f) ? 1.f : __ldcg(Gf + r * Z + c) * scf[r] * scf[c];
+            a[ii][k] = v;
+        }
+    if (own && C == 0)
+#pragma unroll
+        for (int ii = 0; ii < T; ++ii) colbuf[R * T + ii] = a[ii][0];
     __syncthreads();
     bool fb = false;   // the same in every thread: each decision reads the same shared values
     for (int j = 0; j < n1; ++j) {
-        const float d = Lf[j * n1 + j];
+        const float *cb = colbuf + (j & 1) * P;
+        const float d = cb[j];
         if (!(d > 1e-5f)) {
             fb = true;
             break;
         }
-        const float y = rsqrtf(d);
-        if (tid == 0) invf[j] = y;
-        if (j > 0)
-            for (int r = j + tid; r < n1; r += blockDim.x) Lf[r * n1 + j - 1] *= invf[j - 1];
-        const float id = 1.f / d;
-        const int c = j + 1 + (tid % U);
-        if (c < n1) {
-            const float lcj = Lf[c * n1 + j] * id;
-            for (int r = c + tid / U; r < n1; r += (int)blockDim.x / U) Lf[r * n1 + c] -= Lf[r * n1 + j] * lcj;
+        const float s = rsqrtf(d);
+        if (tid == 0) invf[j] = s;
+        if (own && C * T + T > j) {
+            // branch-free: rows r <= j and columns c <= j of the tile get zero factors
+            // (the entries above a diagonal tile's diagonal are never read)
+            const int kj = j - C * T;   // column j's place in this tile column, if in [0, T)
+            float lr[T], lc[T];
+#pragma unroll
+            for (int q = 0; q < T; ++q) {
+                const float vr = cb[R * T + q] * s, vc = cb[C * T + q] * s;
+                lr[q] = R * T + q > j ? vr : 0.f;
+                lc[q] = q > kj ? vc : 0.f;
+            }
+#pragma unroll
+            for (int ii = 0; ii < T; ++ii)
+#pragma unroll
+                for (int k = 0; k < T; ++k) a[ii][k] = fmaf(-lr[ii], lc[k], a[ii][k]);
+            if (kj >= 0 && kj < T)   // column j of the factor: l
+#pragma unroll
+                for (int ii = 0; ii < T; ++ii)
+#pragma unroll
+                    for (int k = 0; k < T; ++k) a[ii][k] = k == kj ? lr[ii] : a[ii][k];
+            const int k1 = kj + 1;
+            if (k1 >= 0 && k1 < T) {   // publish column j + 1 (rows > j)
+                float *nb = colbuf + ((j + 1) & 1) * P;
+#pragma unroll
+                for (int ii = 0; ii < T; ++ii) {
+                    float v = a[ii][0];
+#pragma unroll
+                    for (int k = 1; k < T; ++k) v = k == k1 ? a[ii][k] : v;
+                    if (R * T + ii > j) nb[R * T + ii] = v;
+                }
+            }
         }
         __syncthreads();
     }
     if (!fb) {
-        for (int r = tid; r < n1; r += blockDim.x) {
-            xv[r] = 0.0;
-            rv[r] = A[r * Z + n1];
+        // ---- FP64 iterative refinement: z += (L L^T)^{-1} S (b - A S z) ----
+        double bm = 0.0;
+        for (int r = tid; r < P; r += blockDim.x) {
+            double rs = 0.0;
+            if (r < n1) {
+                rs = sc[r] * __ldcg(G + r * Z + n1);
+                xv[r] = 0.0;
+                bm = fmax(bm, fabs(rs));
+            }
+            yf[r] = (float)rs;
         }
+        bm = warp_max(bm);
+        if (lane == 0) half[64 + warp] = bm;
+        refit_cp_wait();
         __syncthreads();
+        double bmax = 0.0;
+        for (int w = 0; w < nwarps; ++w) bmax = fmax(bmax, half[64 + w]);
         bool conv = false;
         for (int it = 0; it < 6 && !conv; ++it) {
-            if (tid < 32) {   // Lf Lf^T y = r in FP32 (column-oriented, one warp), x += y
-                for (int r = lane; r < n1; r += 32) yf[r] = (float)rv[r];
-                __syncwarp();
-                for (int j = 0; j < n1; ++j) {
-                    const float yj = yf[j] * invf[j];
-                    __syncwarp();
-                    if (lane == 0) yf[j] = yj;
-                    for (int r = j + 1 + lane; r < n1; r += 32) yf[r] -= Lf[r * n1 + j] * yj;
-                    __syncwarp();
-                }
-                for (int j = n1 - 1; j >= 0; --j) {
-                    const float xj = yf[j] * invf[j];
-                    __syncwarp();
-                    if (lane == 0) yf[j] = xj;
-                    for (int r = lane; r < j; r += 32) yf[r] -= Lf[j * n1 + r] * xj;
-                    __syncwarp();
-                }
-                for (int r = lane; r < n1; r += 32) xv[r] += (double)yf[r];
+            refit_tile_solve<T, NT>(a, own, R, C, yf, invf);
+            for (int r = tid; r < n1; r += blockDim.x) {   // z += y; x = S z into inv_d
+                const double z = xv[r] + (double)yf[r];
+                xv[r] = z;
+                inv_d[r] = sc[r] * z;
             }
             __syncthreads();
-            for (int r = tid; r < n1; r += blockDim.x) {   // r = b - A x in FP64
-                double acc = A[r * Z + n1];
-                for (int c2 = 0; c2 < n1; ++c2) acc -= A[r * Z + c2] * xv[c2];
-                rv[r] = acc;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double rmax = 0.0, bmax = 0.0, xmax = 0.0;
-                for (int r = 0; r < n1; ++r) {
-                    rmax = fmax(rmax, fabs(rv[r]));
-                    bmax = fmax(bmax, fabs(A[r * Z + n1]));
+            double rmax = 0.0, xmax = 0.0;
+            for (int r0 = 0; r0 < n1; r0 += (int)blockDim.x >> 1) {   // S (b - A x), two threads a row
+                const int r = r0 + (tid >> 1);   // the same trip count in every lane (the shuffle)
+                double acc = 0.0;
+                if (r < n1)
+                    for (int c = tid & 1; c < n1; c += 2) acc = fma(A[r * Z + c], inv_d[c], acc);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                if (r < n1 && (tid & 1) == 0) {
+                    const double rs = sc[r] * (A[r * Z + n1] - acc);
+                    yf[r] = (float)rs;
+                    rmax = fmax(rmax, fabs(rs));
                     xmax = fmax(xmax, fabs(xv[r]));
                 }
-                s_conv = rmax <= 1e-12 * (bmax + xmax);
+            }
+            rmax = warp_max(rmax);
+            xmax = warp_max(xmax);
+            if (lane == 0) {
+                half[2 * warp] = rmax;
+                half[2 * warp + 1] = xmax;
             }
             __syncthreads();
-            conv = s_conv != 0;
+            rmax = xmax = 0.0;
+            for (int w = 0; w < nwarps; ++w) {
+                rmax = fmax(rmax, half[2 * w]);
+                xmax = fmax(xmax, half[2 * w + 1]);
+            }
+            conv = rmax <= 1e-12 * (bmax + xmax);
         }
         if (conv) {
             for (int r = tid; r < n1; r += blockDim.x) {
-                const float v = (float)(xv[r] * sc[r]);
+                const float v = (float)inv_d[r];
                 const int p = r < U ? ow3 + r : ob3;
                 params[p] = v;
                 if (params2) params2[p] = v;
@@ -235,7 +422,14 @@ __global__ void __launch_bounds__(256) mlp_refit_kernel(const double *part, int 
         }
     }
 
-    // ---- FP64 Cholesky and triangular solves (the fallback) ----
+    // ---- FP64 Cholesky and triangular solves of the scaled system (the fallback) ----
+    refit_cp_wait();
+    __syncthreads();
+    for (int e = tid; e < n1 * (n1 + 1); e += blockDim.x) {
+        const int r = e / (n1 + 1), c = e % (n1 + 1);
+        A[r * Z + c] = (r == c && sc[r] == 0.0) ? 1.0 : A[r * Z + c] * sc[r] * (c < n1 ? sc[c] : 1.0);
+    }
+    __syncthreads();
     // lower Cholesky factor in place, one barrier per column. Every thread takes
     // column j's pivot d and 1/sqrt(d) by two Newton-Raphson steps
     // y <- y (3 - d y^2) / 2 from an FP32 seed (relative error 2^-22 -> 2^-44 ->

@@ -936,7 +936,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     const size_t b_vec = al((size_t)WL::NPpad * 4), b_img = al((size_t)WL::img_elems * 2),
                  b_stats = al((size_t)n_dates * 2 * kIn * 4), b_snaps = al((size_t)epochs * WL::NPpad * 4),
                  b_part = al((size_t)G * WL::NPpad * 4), b_flags = al(2 * 4), b_bl = al(8),
-                 b_G = al((size_t)Z * Z * 8), b_pl = al((size_t)sweep_grid * 8),
+                 b_G = al(refit_g_bytes(WL::U)), b_pl = al((size_t)sweep_grid * 8),
                  b_pg = al((size_t)sweep_grid * Z * Z * 8);
     const size_t need = 5 * b_vec + b_img + b_stats + b_snaps + b_part + b_flags + 2 * b_bl + b_G + b_pl + b_pg;
     if (w.cap < need) {
