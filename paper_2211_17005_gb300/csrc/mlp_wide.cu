@@ -7,9 +7,10 @@
 // Kernels of one date, in order on one stream:
 //   wide_train_kernel   one epoch of Adam steps on a cooperative grid (one CTA per
 //                       SM, at most one tile per CTA and round)
-//   wide_sweep_kernel   full-sample forward passes on all SMs: the epoch loss and
-//                       the best-parameter choice, the refit's Gram matrix, or the
-//                       predictions
+//   wide_sweep_kernel   full-sample forward passes: the refit's Gram matrix (the
+//                       trainer's layout, one CTA per SM), or the epoch loss with
+//                       the best-parameter choice and the predictions (a
+//                       forward-only layout, two CTAs per SM)
 //   mlp_refit_kernel    (shared) Gram sum, FP64 Cholesky, new (w3, b3)
 //
 // Every CTA owns one 128-row tile slot worked by its two warpgroups; warpgroup h
@@ -78,6 +79,7 @@ struct WL {
     static constexpr int img_elems = U * kIn + U * U;             // BF16 images of W1 | W2
     static constexpr uint32_t tmem_cols = 512;
     static constexpr uint32_t cD = 0, cW2 = 128, cW1 = 320;
+    static constexpr bool kGram = true;   // the layout holds the Gram pass's A buffer
     // vector offsets inside sVec
     static constexpr int vb1 = 0, vb2 = U, vw3 = 2 * U, vb3 = 3 * U, vmu = 3 * U + 1;
 
@@ -95,6 +97,27 @@ struct WL {
 };
 static_assert(WL::sStage % 128 == 0, "TMA destination must be 128-byte aligned");
 static_assert(WL::bytes <= 227 * 1024, "shared memory");
+
+// Forward-only layout of the loss and prediction passes: B, the weight images, the
+// vectors and the staging area, no A buffer; 107 KB of shared memory and 128 TMEM
+// columns (one accumulator for both layers), so two CTAs share an SM and one's
+// epilogues run beside the other's tensor-core work.
+struct WLF : WL {
+    static constexpr bool kGram = false;
+    static constexpr int sA = -1;
+    static constexpr int sB = 0;
+    static constexpr int sW1 = sB + kRows * wB * 2;
+    static constexpr int sW2 = sW1 + U * kIn * 2;
+    static constexpr int sVec = sW2 + U * U * 2;
+    static constexpr int sStage = sVec + 512 * 4;
+    static constexpr int sStats = sStage + (kIn + 1) * kRows * 4;
+    static constexpr int sGsl = sStats + 2 * kIn * 4;
+    static constexpr int sOut = sGsl + 8 * 66 * 4;
+    static constexpr int bytes = sOut + 2 * kRows * 4;
+    static constexpr uint32_t tmem_cols = 128;
+};
+static_assert(WLF::sStage % 128 == 0, "TMA destination must be 128-byte aligned");
+static_assert(2 * (WLF::bytes + 1024 + 256) <= 228 * 1024, "two CTAs per SM");
 
 // byte offset of element c of row r in a BF16 row buffer of width w (K-major core
 // matrices of 8 rows x 16 bytes)
@@ -181,7 +204,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, un
     return __syncthreads_and(ok) != 0;
 }
 
-struct WNet {
+template <class L>
+struct WNetT {
     unsigned char *smem;
     uint32_t tmem = 0;
     uint64_t *mbar, *sbar;
@@ -191,7 +215,7 @@ struct WNet {
     float *vec, *stage;
     const float *mean, *istd;
 
-    __device__ WNet(unsigned char *s, uint64_t *mbars) : smem(s)
+    __device__ WNetT(unsigned char *s, uint64_t *mbars) : smem(s)
     {
         tid = threadIdx.x;
         warp = tid >> 5;
@@ -200,9 +224,9 @@ struct WNet {
         half = tid >> 7;
         mbar = mbars;
         sbar = mbars + 1;
-        vec = reinterpret_cast<float *>(smem + WL::sVec);
-        stage = reinterpret_cast<float *>(smem + WL::sStage);
-        mean = reinterpret_cast<const float *>(smem + WL::sStats);
+        vec = reinterpret_cast<float *>(smem + L::sVec);
+        stage = reinterpret_cast<float *>(smem + L::sStage);
+        mean = reinterpret_cast<const float *>(smem + L::sStats);
         istd = mean + kIn;
     }
 
@@ -250,10 +274,10 @@ struct WNet {
     // D = dH2 W2: A = the dH2 columns of A (K = U), B = the W2 image read MN-major
     __device__ void gemm_w2t(uint32_t d) const
     {
-        const uint32_t id = umma::idesc_bf16_f32(kRows, WL::U) | umma::kMnMajorB;
-        const uint32_t a0 = saddr(WL::sA), b0 = saddr(WL::sW2), lbo = (WL::U / 8) * 128u;
-        const uint32_t asbo = (WL::wA / 8u) * 128u;
-        for (int kk = 0; kk < WL::U / 16; ++kk)
+        const uint32_t id = umma::idesc_bf16_f32(kRows, L::U) | umma::kMnMajorB;
+        const uint32_t a0 = saddr(L::sA), b0 = saddr(L::sW2), lbo = (L::U / 8) * 128u;
+        const uint32_t asbo = (L::wA / 8u) * 128u;
+        for (int kk = 0; kk < L::U / 16; ++kk)
             umma::mma_bf16(tmem + d, umma::smem_desc(a0 + kk * 256u, 128u, asbo),
                            umma::smem_desc(b0 + kk * 2u * lbo, lbo, 128u), id, kk > 0 ? 1u : 0u);
     }
@@ -304,9 +328,9 @@ struct WNet {
             x[4 * g + 2] = (stage[(f0 + 2) * kRows + row] - m.z) * r.z;
             x[4 * g + 3] = (stage[(f0 + 3) * kRows + row] - m.w) * r.w;
         }
-        unsigned char *b = smem + WL::sB;
-        *reinterpret_cast<uint4 *>(b + wrow_off(row, WL::cX + 16 * half, WL::wB)) = pack8(x);
-        *reinterpret_cast<uint4 *>(b + wrow_off(row, WL::cX + 16 * half + 8, WL::wB)) = pack8(x + 8);
+        unsigned char *b = smem + L::sB;
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, L::cX + 16 * half, L::wB)) = pack8(x);
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, L::cX + 16 * half + 8, L::wB)) = pack8(x + 8);
         y = stage[kIn * kRows + row];
         return ok;
     }
@@ -315,10 +339,10 @@ struct WNet {
     // H1 = relu(D + b1) into B; the mask of h1 > 0 in m1
     __device__ void epi1(uint32_t (&m1)[2]) const
     {
-        unsigned char *b = smem + WL::sB;
-        const float4 *b1 = reinterpret_cast<const float4 *>(vec + WL::vb1 + 64 * half);
+        unsigned char *b = smem + L::sB;
+        const float4 *b1 = reinterpret_cast<const float4 *>(vec + L::vb1 + 64 * half);
         float v[64];
-        umma::tmem_ld64(taddr(WL::cD + 64u * half), v);
+        umma::tmem_ld64(taddr(L::cD + 64u * half), v);
         m1[0] = m1[1] = 0u;
 #pragma unroll
         for (int g = 0; g < 16; ++g) {
@@ -331,16 +355,16 @@ struct WNet {
 #pragma unroll
         for (int i = 0; i < 64; ++i) m1[i / 32] |= (v[i] > 0.f ? 1u : 0u) << (i % 32);
 #pragma unroll
-        for (int g = 0; g < 8; ++g) *reinterpret_cast<uint4 *>(b + wrow_off(row, 64 * half + 8 * g, WL::wB)) = pack8(v + 8 * g);
+        for (int g = 0; g < 8; ++g) *reinterpret_cast<uint4 *>(b + wrow_off(row, 64 * half + 8 * g, L::wB)) = pack8(v + 8 * g);
     }
 
     // h2 = relu(D + b2) of this thread's 64 columns in place; returns their share of
     // w3 . h2 (four partial sums)
     __device__ float layer2(float (&v)[64]) const
     {
-        const float4 *b2 = reinterpret_cast<const float4 *>(vec + WL::vb2 + 64 * half),
-                     *w3 = reinterpret_cast<const float4 *>(vec + WL::vw3 + 64 * half);
-        umma::tmem_ld64(taddr(WL::cD + 64u * half), v);
+        const float4 *b2 = reinterpret_cast<const float4 *>(vec + L::vb2 + 64 * half),
+                     *w3 = reinterpret_cast<const float4 *>(vec + L::vw3 + 64 * half);
+        umma::tmem_ld64(taddr(L::cD + 64u * half), v);
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int g = 0; g < 16; ++g) {
@@ -360,10 +384,10 @@ struct WNet {
     // zeta = w3 . h2 + b3 of this thread's row: the two halves' shares added in order
     __device__ float zeta(float share) const
     {
-        float *so = reinterpret_cast<float *>(smem + WL::sOut);
+        float *so = reinterpret_cast<float *>(smem + L::sOut);
         so[half * kRows + row] = share;
         __syncthreads();
-        const float z = (so[row] + so[kRows + row]) + vec[WL::vb3];
+        const float z = (so[row] + so[kRows + row]) + vec[L::vb3];
         __syncthreads();
         return z;
     }
@@ -373,11 +397,11 @@ struct WNet {
     // (dw3) and, in the first warpgroup, of dout (db3) and dpred (dmu)
     __device__ void out_back2(int pos, float y, float inv_batch, float *gsl) const
     {
-        unsigned char *a = smem + WL::sA;
-        const float4 *w3 = reinterpret_cast<const float4 *>(vec + WL::vw3 + 64 * half);
+        unsigned char *a = smem + L::sA;
+        const float4 *w3 = reinterpret_cast<const float4 *>(vec + L::vw3 + 64 * half);
         float v[64];
         const float out = zeta(layer2(v));
-        const float pred = (pos ? fmaxf(out, 0.f) : out) + vec[WL::vmu];
+        const float pred = (pos ? fmaxf(out, 0.f) : out) + vec[L::vmu];
         const float dpred = 2.f * (pred - y) * inv_batch;
         const float dout = pos ? (out > 0.f ? dpred : 0.f) : dpred;
 #pragma unroll
@@ -387,7 +411,7 @@ struct WNet {
             float d[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) d[i] = v[8 * g + i] > 0.f ? dout * wv[i] : 0.f;
-            *reinterpret_cast<uint4 *>(a + wrow_off(row, 64 * half + 8 * g, WL::wA)) = pack8(d);
+            *reinterpret_cast<uint4 *>(a + wrow_off(row, 64 * half + 8 * g, L::wA)) = pack8(d);
         }
 #pragma unroll
         for (int i = 0; i < 64; ++i) v[i] *= dout;
@@ -406,42 +430,44 @@ struct WNet {
     // dH1 = D (h1 > 0) into A
     __device__ void back1(const uint32_t (&m1)[2]) const
     {
-        unsigned char *a = smem + WL::sA;
+        unsigned char *a = smem + L::sA;
         float v[64];
-        umma::tmem_ld64(taddr(WL::cD + 64u * half), v);
+        umma::tmem_ld64(taddr(L::cD + 64u * half), v);
 #pragma unroll
         for (int i = 0; i < 64; ++i) v[i] = ((m1[i / 32] >> (i % 32)) & 1u) ? v[i] : 0.f;
 #pragma unroll
         for (int g = 0; g < 8; ++g)
-            *reinterpret_cast<uint4 *>(a + wrow_off(row, WL::U + 64 * half + 8 * g, WL::wA)) = pack8(v + 8 * g);
+            *reinterpret_cast<uint4 *>(a + wrow_off(row, L::U + 64 * half + 8 * g, L::wA)) = pack8(v + 8 * g);
     }
 
     // first two layers of the staged tile; D holds the second-layer pre-activation
     template <class Side>
     __device__ bool forward12(uint32_t (&m1)[2], bool in_ok, Side side)
     {
-        if (!mma([&] { gemm_rows(WL::cD, WL::sB, WL::wB, WL::cX, WL::sW1, kIn, WL::U); }, in_ok, side)) return false;
+        if (!mma([&] { gemm_rows(L::cD, L::sB, L::wB, L::cX, L::sW1, kIn, L::U); }, in_ok, side)) return false;
         epi1(m1);
-        return mma([&] { gemm_rows(WL::cD, WL::sB, WL::wB, 0, WL::sW2, WL::U, WL::U); });
+        return mma([&] { gemm_rows(L::cD, L::sB, L::wB, 0, L::sW2, L::U, L::U); });
     }
 
     // constant columns of B: ones after H1 (first warpgroup) and after X (second)
     __device__ void init_constants()
     {
         const uint4 one = make_uint4((uint32_t)bf16_bits(1.f), 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
-        unsigned char *b = smem + WL::sB;
-        const int c = half ? WL::cOne2 : WL::cOne1;
-        *reinterpret_cast<uint4 *>(b + wrow_off(row, c, WL::wB)) = one;
-        *reinterpret_cast<uint4 *>(b + wrow_off(row, c + 8, WL::wB)) = zero;
+        unsigned char *b = smem + L::sB;
+        const int c = half ? L::cOne2 : L::cOne1;
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, c, L::wB)) = one;
+        *reinterpret_cast<uint4 *>(b + wrow_off(row, c + 8, L::wB)) = zero;
     }
 };
+using WNet = WNetT<WL>;
 
 // common start: TMEM, mbarriers, standardisation, zero staging rows >= F, the
 // constant columns of B, optionally a zeroed A
-__device__ void wide_setup(WNet &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *stats, int F, bool zero_a)
+template <class L>
+__device__ void wide_setup(WNetT<L> &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *stats, int F, bool zero_a)
 {
     if (n.warp == 0) {
-        umma::tmem_alloc(s_tmem, WL::tmem_cols);
+        umma::tmem_alloc(s_tmem, L::tmem_cols);
         umma::tmem_relinquish();
     }
     if (n.tid == 0) {
@@ -449,50 +475,52 @@ __device__ void wide_setup(WNet &n, uint32_t *s_tmem, uint64_t *s_mbar, const fl
         umma::mbar_init(&s_mbar[1], 1);
         umma::fence_mbar_init();
     }
-    float *st = reinterpret_cast<float *>(n.smem + WL::sStats);
+    float *st = reinterpret_cast<float *>(n.smem + L::sStats);
     if (n.tid < 2 * kIn) st[n.tid] = __ldg(stats + n.tid);
     for (int i = n.tid; i < (kIn + 1) * kRows; i += kWThreads) {
         const int f = i / kRows;
         if (f >= F && f < kIn) n.stage[i] = 0.f;
     }
-    float *gsl = reinterpret_cast<float *>(n.smem + WL::sGsl);
+    float *gsl = reinterpret_cast<float *>(n.smem + L::sGsl);
     for (int i = n.tid; i < 8 * 66; i += kWThreads) gsl[i] = 0.f;
-    if (zero_a) {
-        uint4 *a = reinterpret_cast<uint4 *>(n.smem + WL::sA);
-        for (int i = n.tid; i < kRows * WL::wA * 2 / 16; i += kWThreads) a[i] = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (L::sA >= 0) if (zero_a) {
+        uint4 *a = reinterpret_cast<uint4 *>(n.smem + L::sA);
+        for (int i = n.tid; i < kRows * L::wA * 2 / 16; i += kWThreads) a[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     n.init_constants();
 }
 
 // images and FP32 vectors of the parameters theta (global, row order)
-__device__ void wide_load_params(WNet &n, const float *theta)
+template <class L>
+__device__ void wide_load_params(WNetT<L> &n, const float *theta)
 {
-    for (int i = n.tid; i < WL::U * (kIn / 8); i += kWThreads) {   // W1: row o, 8 inputs from k
+    for (int i = n.tid; i < L::U * (kIn / 8); i += kWThreads) {   // W1: row o, 8 inputs from k
         const int o = i / (kIn / 8), k = (i % (kIn / 8)) * 8;
         float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = __ldg(theta + WL::oW1 + o * kIn + k + j);
-        *reinterpret_cast<uint4 *>(n.smem + WL::sW1 + umma::kmajor_offset(o, k, kIn)) = pack8(v);
+        for (int j = 0; j < 8; ++j) v[j] = __ldg(theta + L::oW1 + o * kIn + k + j);
+        *reinterpret_cast<uint4 *>(n.smem + L::sW1 + umma::kmajor_offset(o, k, kIn)) = pack8(v);
     }
-    for (int i = n.tid; i < WL::U * (WL::U / 8); i += kWThreads) {  // W2: row o, 8 inputs from k
-        const int o = i / (WL::U / 8), k = (i % (WL::U / 8)) * 8;
+    for (int i = n.tid; i < L::U * (L::U / 8); i += kWThreads) {  // W2: row o, 8 inputs from k
+        const int o = i / (L::U / 8), k = (i % (L::U / 8)) * 8;
         float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = __ldg(theta + WL::oW2 + o * WL::U + k + j);
-        *reinterpret_cast<uint4 *>(n.smem + WL::sW2 + umma::kmajor_offset(o, k, WL::U)) = pack8(v);
+        for (int j = 0; j < 8; ++j) v[j] = __ldg(theta + L::oW2 + o * L::U + k + j);
+        *reinterpret_cast<uint4 *>(n.smem + L::sW2 + umma::kmajor_offset(o, k, L::U)) = pack8(v);
     }
-    for (int i = n.tid; i < WL::U; i += kWThreads) {
-        n.vec[WL::vb1 + i] = __ldg(theta + WL::ob1 + i);
-        n.vec[WL::vb2 + i] = __ldg(theta + WL::ob2 + i);
-        n.vec[WL::vw3 + i] = __ldg(theta + WL::ow3 + i);
+    for (int i = n.tid; i < L::U; i += kWThreads) {
+        n.vec[L::vb1 + i] = __ldg(theta + L::ob1 + i);
+        n.vec[L::vb2 + i] = __ldg(theta + L::ob2 + i);
+        n.vec[L::vw3 + i] = __ldg(theta + L::ow3 + i);
     }
     if (n.tid == 0) {
-        n.vec[WL::vb3] = __ldg(theta + WL::ob3);
-        n.vec[WL::vmu] = __ldg(theta + WL::omu);
+        n.vec[L::vb3] = __ldg(theta + L::ob3);
+        n.vec[L::vmu] = __ldg(theta + L::omu);
     }
 }
 
-__device__ void wide_finish_setup(WNet &n, uint32_t *s_tmem)
+template <class L>
+__device__ void wide_finish_setup(WNetT<L> &n, uint32_t *s_tmem)
 {
     umma::fence_proxy_async();
     umma::fence_before_sync();
@@ -501,12 +529,13 @@ __device__ void wide_finish_setup(WNet &n, uint32_t *s_tmem)
     n.tmem = *s_tmem;
 }
 
-__device__ void wide_teardown(WNet &n)
+template <class L>
+__device__ void wide_teardown(WNetT<L> &n)
 {
     if (n.pending) (void)umma::mbar_wait(n.sbar, n.sphase, kMbarPolls);
     umma::fence_before_sync();
     __syncthreads();
-    if (n.warp == 0) umma::tmem_dealloc(n.tmem, WL::tmem_cols);
+    if (n.warp == 0) umma::tmem_dealloc(n.tmem, L::tmem_cols);
 }
 
 // One epoch (or its first n_steps batches) of Adam on a cooperative grid. Batch b
@@ -726,15 +755,17 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
 
 // Full-sample passes with fixed parameters, output ReLU on: the loss (mode 0), the
 // refit's Gram matrix of Z = [h2 | 1 | y - mu] (mode 1), the predictions (mode 2).
-__global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, const __grid_constant__ CUtensorMap tm)
+template <class L, int MinBlocks>
+__global__ void __launch_bounds__(kWThreads, MinBlocks) wide_sweep_kernel(WSweepArgs a,
+                                                                         const __grid_constant__ CUtensorMap tm)
 {
-    constexpr int Z = WL::Z;
+    constexpr int Z = L::Z;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ double s_red[8][3];
     __shared__ int s_flag[2];
-    WNet n(smem, s_mbar);
+    WNetT<L> n(smem, s_mbar);
     wide_setup(n, &s_tmem, s_mbar, a.stats, a.F, a.mode == 1);
     wide_load_params(n, a.theta);
     wide_finish_setup(n, &s_tmem);
@@ -756,7 +787,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, 
         float v[64];
         const float share = n.layer2(v);
         if (a.mode != 1) {
-            const float pred = fmaxf(n.zeta(share), 0.f) + n.vec[WL::vmu];
+            const float pred = fmaxf(n.zeta(share), 0.f) + n.vec[L::vmu];
             if (n.half == 0) {
                 if (a.mode == 2) {
                     if (a.pred) a.pred[t * kRows + n.row] = pred;
@@ -764,23 +795,23 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, 
                     acc[0] += (double)((pred - y) * (pred - y));
                 }
             }
-        } else {
+        } else if constexpr (L::kGram) {
             // row of Z into A: [h2 | 1 | y - mu | 0 ...]; the corner sums (1, y - mu,
             // (y - mu)^2 with y - mu rounded as the tensor core sees it) in FP64
-            unsigned char *ar = smem + WL::sA;
+            unsigned char *ar = smem + L::sA;
 #pragma unroll
             for (int g = 0; g < 8; ++g)
-                *reinterpret_cast<uint4 *>(ar + wrow_off(n.row, 64 * n.half + 8 * g, WL::wA)) = pack8(v + 8 * g);
+                *reinterpret_cast<uint4 *>(ar + wrow_off(n.row, 64 * n.half + 8 * g, L::wA)) = pack8(v + 8 * g);
             if (n.half == 1) {
-                const float d = y - n.vec[WL::vmu];
-                *reinterpret_cast<uint4 *>(ar + wrow_off(n.row, WL::U, WL::wA)) = make_uint4(pack2(1.f, d), 0u, 0u, 0u);
+                const float d = y - n.vec[L::vmu];
+                *reinterpret_cast<uint4 *>(ar + wrow_off(n.row, L::U, L::wA)) = make_uint4(pack2(1.f, d), 0u, 0u, 0u);
                 const double db = (double)__bfloat162float(__float2bfloat16_rn(d));
                 acc[0] += 1.0;
                 acc[1] += db;
                 acc[2] += db * db;
             }
             // G (+)= Z^T Z: M = the 128 h2 columns, N = the first 144 columns of the rows
-            ok = n.mma([&] { n.gemm_paths(WL::cW2, WL::sA, WL::wA, 0, WL::sA, WL::wA, 0, WL::U + 16, !first); });
+            ok = n.mma([&] { n.gemm_paths(L::cW2, L::sA, L::wA, 0, L::sA, L::wA, 0, L::U + 16, !first); });
         }
         if (!ok && n.tid == 0) atomicExch(a.err, 2);
         first = false;
@@ -820,9 +851,9 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, 
             }
             __syncthreads();
             if (s_flag[1])
-                for (int p = n.tid; p < WL::NP; p += kWThreads) a.best[p] = __ldg(a.theta + p);
+                for (int p = n.tid; p < L::NP; p += kWThreads) a.best[p] = __ldg(a.theta + p);
         }
-    } else if (a.mode == 1) {   // this CTA's Gram as FP64, [Z][Z]
+    } else if constexpr (L::kGram) {   // mode 1: this CTA's Gram as FP64, [Z][Z]
         double *P = a.part + (size_t)blockIdx.x * Z * Z;
         const bool have = blockIdx.x < tiles;
         const uint32_t lanes = (uint32_t)((n.warp & 3) * 32) << 16;
@@ -830,7 +861,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, 
         const int k0 = n.half ? 5 : 0, k1 = n.half ? 9 : 5;
         for (int k = k0; k < k1; ++k) {
             float v[16];
-            umma::tmem_ld16(n.tmem + lanes + WL::cW2 + 16u * k, v);
+            umma::tmem_ld16(n.tmem + lanes + L::cW2 + 16u * k, v);
             umma::tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
@@ -838,7 +869,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, 
                 if (c < Z) {
                     const double g = have ? (double)v[i] : 0.0;
                     P[r * Z + c] = g;
-                    if (c >= WL::U) P[c * Z + r] = g;   // rows U, U + 1 by symmetry
+                    if (c >= L::U) P[c * Z + r] = g;   // rows U, U + 1 by symmetry
                 }
             }
         }
@@ -849,9 +880,9 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_sweep_kernel(WSweepArgs a, 
                 c1 += s_red[w][1];
                 c2 += s_red[w][2];
             }
-            P[WL::U * Z + WL::U] = c0;
-            P[WL::U * Z + WL::U + 1] = P[(WL::U + 1) * Z + WL::U] = c1;
-            P[(WL::U + 1) * Z + WL::U + 1] = c2;
+            P[L::U * Z + L::U] = c0;
+            P[L::U * Z + L::U + 1] = P[(L::U + 1) * Z + L::U] = c1;
+            P[(L::U + 1) * Z + L::U + 1] = c2;
         }
     }
     wide_teardown(n);
@@ -910,7 +941,10 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     WideWork &w = g_wide[dev];
     if (!w.attrs) {
         CVA_CUDA_TRY(cudaFuncSetAttribute(wide_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WL::bytes));
-        CVA_CUDA_TRY(cudaFuncSetAttribute(wide_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WL::bytes));
+        CVA_CUDA_TRY(cudaFuncSetAttribute(wide_sweep_kernel<WL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          WL::bytes));
+        CVA_CUDA_TRY(cudaFuncSetAttribute(wide_sweep_kernel<WLF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          WLF::bytes));
         CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_refit_kernel<WL::U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)refit_smem_bytes(WL::U)));
         int least = 0, greatest = 0;
@@ -926,17 +960,25 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     const int G = wide_grid(tiles_per_batch, sms);
     const uint64_t tiles = M / kRows;
     const int sweep_grid = (int)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
-    // passes that overlap the training take the SMs its grid leaves (one CTA per SM on
-    // either side); with fewer than 8 of them every pass stays on st with the whole GPU
+    // the loss and prediction passes run the forward-only layout, fwd_per_sm CTAs an SM
+    int fwd_per_sm = 0;
+    CVA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fwd_per_sm, wide_sweep_kernel<WLF, 2>, kWThreads,
+                                                                WLF::bytes));
+    fwd_per_sm = fwd_per_sm < 1 ? 1 : (fwd_per_sm > 2 ? 2 : fwd_per_sm);
+    const uint64_t fwd_cap = (uint64_t)fwd_per_sm * (uint64_t)sms;
+    const int fwd_grid = (int)(tiles < fwd_cap ? tiles : fwd_cap);
+    // passes that overlap the training take the SMs its grid leaves (the trainer's CTA
+    // fills an SM); with fewer than 8 of them every pass stays on st with the whole GPU
     const bool overlap = sms - G >= 8;
-    const int side_grid = overlap ? sms - G : sweep_grid;
+    const uint64_t side_cap = (uint64_t)fwd_per_sm * (uint64_t)(sms - G);
+    const int side_grid = overlap ? (int)(tiles < side_cap ? tiles : side_cap) : fwd_grid;
     const cudaStream_t sst = overlap ? w.side : st;
 
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_vec = al((size_t)WL::NPpad * 4), b_img = al((size_t)WL::img_elems * 2),
                  b_stats = al((size_t)n_dates * 2 * kIn * 4), b_snaps = al((size_t)epochs * WL::NPpad * 4),
                  b_part = al((size_t)G * WL::NPpad * 4), b_flags = al(2 * 4), b_bl = al(8),
-                 b_G = al(refit_g_bytes(WL::U)), b_pl = al((size_t)sweep_grid * 8),
+                 b_G = al(refit_g_bytes(WL::U)), b_pl = al((size_t)(fwd_grid > sweep_grid ? fwd_grid : sweep_grid) * 8),
                  b_pg = al((size_t)sweep_grid * Z * Z * 8);
     const size_t need = 5 * b_vec + b_img + b_stats + b_snaps + b_part + b_flags + 2 * b_bl + b_G + b_pl + b_pg;
     if (w.cap < need) {
@@ -1046,7 +1088,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
                 g.theta = params_dev;
                 g.part = part_gram;
                 g.loss_out = nullptr;
-                wide_sweep_kernel<<<sweep_grid, kWThreads, WL::bytes, st>>>(g, tm);
+                wide_sweep_kernel<WL, 1><<<sweep_grid, kWThreads, WL::bytes, st>>>(g, tm);
                 CVA_CUDA_TRY(cudaGetLastError());
                 mlp_refit_kernel<WL::U><<<Z, 256, refit_smem_bytes(WL::U), st>>>(part_gram, sweep_grid, Gm, count + 2,
                                                                                  params_dev, snap);
@@ -1061,7 +1103,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
                 CVA_CUDA_TRY(cudaEventRecord(w.ev_train, st));
                 CVA_CUDA_TRY(cudaStreamWaitEvent(sst, w.ev_train, 0));
             }
-            wide_sweep_kernel<<<e == epochs ? sweep_grid : side_grid, kWThreads, WL::bytes, sst>>>(sw, tm);
+            wide_sweep_kernel<WLF, 2><<<e == epochs ? fwd_grid : side_grid, kWThreads, WLF::bytes, sst>>>(sw, tm);
             CVA_CUDA_TRY(cudaGetLastError());
         }
         // the best parameters are known once the last loss pass ran: the next date (st)
@@ -1075,7 +1117,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
             pv.mode = 2;
             pv.theta = best[par];
             pv.pred = pred0 + (size_t)d * M;
-            wide_sweep_kernel<<<side_grid, kWThreads, WL::bytes, sst>>>(pv, tm);
+            wide_sweep_kernel<WLF, 2><<<side_grid, kWThreads, WLF::bytes, sst>>>(pv, tm);
             CVA_CUDA_TRY(cudaGetLastError());
         }
         if (d == 0)
