@@ -430,14 +430,15 @@ CVA_API int cva_mlp_num_params(int hidden);
  * (CVA_ENOTSUP for another width) on the arguments cva_mlp_fit would reject. */
 CVA_API cva_status cva_mlp_plan(uint64_t M, int hidden, int n_batches, int32_t *out4_host);
 
-/* Failure-detection hook of the width-128 trainer: a CTA waiting at the trainer's
- * grid barrier gives up after grid_polls polls (about 32 ns apart; the default is
- * 2^22, over 0.1 s), sets the device status word and leaves its remaining waits at
- * once, so that every CTA ends its launch and the call returns CVA_ETIMEOUT (no
- * CTA outlives its tensor-core or copy operations: their own bounded waits are not
- * shortened). 0 makes every wait give up unless the barrier is already complete;
- * UINT32_MAX restores the default. Applies to the launches enqueued after it, on
- * every device; host-only, no device work. */
+/* Failure-detection hook of the width-128 trainer: a CTA waiting at one of the
+ * trainer's two grid barriers of an Adam step (gradient partials written; parameter
+ * slices updated) gives up after grid_polls polls of the barrier's arrival counter
+ * (about 32 ns apart; the default is 2^22, over 0.1 s), sets the device status word
+ * and leaves its remaining waits at once, so that every CTA ends its launch and the
+ * call returns CVA_ETIMEOUT (no CTA outlives its tensor-core or copy operations:
+ * their own bounded waits are not shortened). 0 makes every wait give up unless
+ * the barrier is already complete; UINT32_MAX restores the default. Applies to the
+ * launches enqueued after it, on every device; host-only, no device work. */
 CVA_API cva_status cva_mlp_set_wait_limit(uint32_t grid_polls);
 
 /* Kernel timing of the trainers (Algorithm 1's training epochs): while on, every

@@ -28,12 +28,12 @@
 //
 // One Adam step on the grid: every CTA writes its FP32 gradient partial to global
 // memory (column order q); after a grid barrier CTA c owns slice c of the
-// parameter vector: it sums the slice over all CTAs' partials (fixed order), applies
-// Adam (moments and FP32 master values in global memory) and writes the new FP32
-// values and their BF16 images; after a second grid barrier every CTA reloads the
-// images and the FP32 vectors. The grid barrier is an arrival counter and a
-// generation word with bounded waits (a wait that gives up sets the status word;
-// every other wait then ends at once).
+// parameter vector: it sums the slice over all CTAs' partials (fixed order, every
+// load of a thread in flight at once), applies Adam (moments and FP32 master values
+// in global memory) and writes the new FP32 values and their BF16 images; after a
+// second grid barrier every CTA fetches the images and the FP32 vectors by bulk
+// copies. The grid barrier is one arrival counter with bounded waits (a wait that
+// gives up sets the status word; every other wait then ends at once).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -141,7 +141,7 @@ struct WTrainArgs {
     float *gq;                     // [NPpad] q order: FP32 master parameters
     uint16_t *gimg;                // [img_elems] BF16 images of W1 | W2 (shared-memory layout)
     float *gpart;                  // [grid][NPpad] q order: gradient partials
-    unsigned *flags;               // [2] grid barrier: arrivals, generation (zero at launch)
+    unsigned *flags;               // [1] grid barrier: arrivals over the launch (zero at launch)
     uint32_t grid_polls;           // polls after which a grid-barrier wait gives up
     const float *stats;            // mean[32], 1/std[32]
     float *grad_out;               // [NP] row order: gradient of the first step (nullable)
@@ -165,32 +165,36 @@ struct WSweepArgs {
     int *err;
 };
 
+// make this thread's generic-proxy global writes visible to later bulk (async
+// proxy) reads of them, and order its async-proxy reads before later writes
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
 // Grid barrier of generation gen: bar[0] counts arrivals over the launch (one per
-// CTA and barrier), bar[1] holds the last completed generation. Thread 0 of every
-// CTA arrives with one atomic; the CTA completing the count publishes the
-// generation, the others poll that one word. Bounded: a wait that gives up (or sees
-// the status word set) sets the status word and returns false; all threads of the
-// CTA get the same answer. Every thread's global writes before the barrier are
-// visible to every thread of the grid after it.
+// CTA and barrier; zero at launch), so generation gen is complete once it reaches
+// gen * nblocks. After a block barrier, thread 0 of every CTA fences and arrives
+// with one atomic; the others of the generation poll the counter itself (relaxed
+// loads) and fence once they see it complete: the release and acquire halves of a
+// cooperative-groups grid barrier, with no second word for the last arrival to
+// publish and so one round trip through L2 fewer. Bounded: a wait that gives up
+// (or sees the status word set) sets the status word and returns false; all
+// threads of the CTA get the same answer. Every thread's global writes before the
+// barrier are visible to every thread of the grid after it.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, unsigned &gen, int *err,
                                              uint32_t max_polls)
 {
-    __threadfence();
     __syncthreads();
     gen += 1u;
     int ok = 1;
     if (threadIdx.x == 0) {
         __threadfence();
+        const unsigned target = gen * nblocks;
         const unsigned t = atomicAdd(bar, 1u);
-        if (t == gen * nblocks - 1u) {
-            __threadfence();
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen) : "memory");
-        } else {
+        if (t + 1u != target) {
             uint32_t it = 0;
             for (;;) {
                 unsigned v;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar + 1) : "memory");
-                if ((int)(v - gen) >= 0) break;
+                asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+                if ((int)(v - target) >= 0) break;
                 if (++it > max_polls || *(volatile int *)err) {
                     ok = 0;
                     atomicExch(err, 3);
@@ -545,7 +549,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ __align__(8) uint64_t s_mbar[3];   // tensor core, input staging, parameter reload
     WNet n(smem, s_mbar);
     const int G = (int)gridDim.x, cta = (int)blockIdx.x;
     // owned slice [lo, hi) of the padded parameter vector (multiples of 4 entries)
@@ -553,6 +557,10 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
     const int lo = min(WL::NPpad, cta * S), hi = min(WL::NPpad, lo + S);
 
     wide_setup(n, &s_tmem, s_mbar, a.stats, a.F, false);
+    if (n.tid == 0) {
+        umma::mbar_init(&s_mbar[2], 1);
+        umma::fence_mbar_init();
+    }
     wide_load_params(n, a.init);
     for (int q = lo + n.tid; q < hi; q += kWThreads) {
         a.gq[q] = q < WL::NP ? __ldg(a.init + WL::p_of(q)) : 0.f;
@@ -571,6 +579,9 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
     float *gsl = reinterpret_cast<float *>(smem + WL::sGsl);
     float *my_gsl = gsl + n.warp * 66;
     float4 *red = reinterpret_cast<float4 *>(smem + WL::sRed);
+    uint64_t *rbar = &s_mbar[2];
+    uint32_t rphase = 0;
+    bool rpending = false;
     unsigned gen = 0;
     bool ok = true;
 
@@ -610,32 +621,46 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
             const uint32_t lanes = (uint32_t)((n.warp & 3) * 32) << 16;
             const int r = (n.warp & 3) * 32 + n.lane;
             const bool have = my_rounds > 0;
-            const int k0 = n.half ? 5 : 0, k1 = n.half ? 9 : 5;   // DW2 | db2: 9 chunks of 16 columns
-            for (int k = k0; k < k1; ++k) {
-                float v[16];
-                umma::tmem_ld16(n.tmem + lanes + WL::cW2 + 16u * k, v);
-                umma::tmem_wait_ld();
+            // DW2 | db2 (9 chunks of 16 columns): chunks [0, 5) in the first half, [5, 9) in
+            // the second; DW1 | db1 (3 chunks): [0, 1) and [1, 3). Every load is issued
+            // before the one wait (the unused chunks read allocated, unused columns).
+            const int k0 = n.half ? 5 : 0, k1 = n.half ? 9 : 5, j0 = n.half ? 1 : 0, j1 = n.half ? 3 : 1;
+            float v2[5][16], v1[2][16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = 16 * k + i;
-                    const float g = have ? v[i] : 0.f;
-                    if (c < WL::U) P[WL::oW2 + c * WL::U + r] = g;
-                    else if (c == WL::U) P[WL::ob2 + r] = g;
-                }
-            }
-            const int j0 = n.half ? 1 : 0, j1 = n.half ? 3 : 1;   // DW1 | db1: 3 chunks
-            for (int k = j0; k < j1; ++k) {
-                float v[16];
-                umma::tmem_ld16(n.tmem + lanes + WL::cW1 + 16u * k, v);
-                umma::tmem_wait_ld();
+            for (int k = 0; k < 5; ++k) umma::tmem_ld16(n.tmem + lanes + WL::cW2 + 16u * (uint32_t)(k0 + k), v2[k]);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = 16 * k + i;
-                    const float g = have ? v[i] : 0.f;
-                    if (c < kIn) P[WL::oW1 + c * WL::U + r] = g;
-                    else if (c == kIn) P[WL::ob1 + r] = g;
+            for (int k = 0; k < 2; ++k) umma::tmem_ld16(n.tmem + lanes + WL::cW1 + 16u * (uint32_t)(j0 + k), v1[k]);
+            umma::tmem_wait_ld();
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(v2[k][i]));
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(v1[k][i]));
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k0 + k < k1) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int c = 16 * (k0 + k) + i;
+                        const float g = have ? v2[k][i] : 0.f;
+                        if (c < WL::U) P[WL::oW2 + c * WL::U + r] = g;
+                        else if (c == WL::U) P[WL::ob2 + r] = g;
+                    }
                 }
-            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (j0 + k < j1) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int c = 16 * (j0 + k) + i;
+                        const float g = have ? v1[k][i] : 0.f;
+                        if (c < kIn) P[WL::oW1 + c * WL::U + r] = g;
+                        else if (c == kIn) P[WL::ob1 + r] = g;
+                    }
+                }
             if (n.tid < WL::U + 2) {   // w3 from the warps of the column's half; b3, mu from the first half
                 const int j = n.tid;
                 const int h = j < WL::U ? j >> 6 : 0, c = j < WL::U ? (j & 63) : j - WL::U + 64;
@@ -646,6 +671,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
             __syncthreads();
             for (int i = n.tid; i < 8 * 66; i += kWThreads) gsl[i] = 0.f;
         }
+        fence_proxy_async_global();   // the last reload's bulk reads come before this step's writes
         if (!grid_barrier(a.flags, (unsigned)G, gen, a.err, a.grid_polls)) ok = false;
 
         // the owned slice: partials summed over the grid (nsub fixed interleaved
@@ -669,16 +695,16 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
                 }
                 float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (gi < NG && j < nsub)
-                    for (int c0 = j; c0 < G; c0 += 16 * nsub) {   // sixteen loads in flight, added in CTA order
-                        float4 v[16];
+                    for (int c0 = j; c0 < G; c0 += 32 * nsub) {   // 32 loads in flight, added in CTA order
+                        float4 v[32];
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
+                        for (int u = 0; u < 32; ++u) {
                             const int c = c0 + u * nsub;
                             v[u] = c < G ? __ldcg(reinterpret_cast<const float4 *>(a.gpart + (size_t)c * WL::NPpad + lo + 4 * gi))
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
+                        for (int u = 0; u < 32; ++u) {
                             acc.x += v[u].x;
                             acc.y += v[u].y;
                             acc.z += v[u].z;
@@ -724,24 +750,38 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
                 __syncthreads();
             }
         }
+        fence_proxy_async_global();   // the new slice is read by bulk copies
         if (!grid_barrier(a.flags, (unsigned)G, gen, a.err, a.grid_polls)) ok = false;
 
-        // every CTA: the new images and FP32 vectors
-        {
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.gimg);
-            uint4 *dst = reinterpret_cast<uint4 *>(smem + WL::sW1);
-            for (int i = n.tid; i < WL::img_elems * 2 / 16; i += kWThreads) dst[i] = __ldcg(src + i);
-            for (int i = n.tid; i < WL::U; i += kWThreads) {
-                n.vec[WL::vb1 + i] = __ldcg(a.gq + WL::ob1 + i);
-                n.vec[WL::vb2 + i] = __ldcg(a.gq + WL::ob2 + i);
-                n.vec[WL::vw3 + i] = __ldcg(a.gq + WL::ow3 + i);
-            }
+        // every CTA: the new images (W1 | W2, stored in the shared-memory layout) and the
+        // FP32 vectors b1 and b2 | w3 | b3 | mu (one padding word after them) by three
+        // bulk copies completing on the reload barrier (none is issued while an earlier
+        // one may still be in flight: after a wait that gave up the launch is failing)
+        if (!rpending) {
             if (n.tid == 0) {
-                n.vec[WL::vb3] = __ldcg(a.gq + WL::ob3);
-                n.vec[WL::vmu] = __ldcg(a.gq + WL::omu);
+                fence_proxy_async_global();
+                constexpr uint32_t img_bytes = WL::img_elems * 2u, b1_bytes = WL::U * 4u,
+                                   rest_bytes = (2 * WL::U + 4) * 4u;
+                static_assert(WL::sW2 == WL::sW1 + WL::U * kIn * 2 && img_bytes % 16 == 0, "images are one copy");
+                static_assert((WL::ob1 * 4) % 16 == 0 && (WL::ob2 * 4) % 16 == 0 && rest_bytes % 16 == 0,
+                              "bulk copy alignment");
+                static_assert(WL::vb2 + 2 * WL::U + 4 <= 512 && WL::ob2 + 2 * WL::U + 4 <= WL::NPpad,
+                              "vector copy bounds");
+                static_assert(WL::vw3 == WL::vb2 + (WL::ow3 - WL::ob2) && WL::vb3 == WL::vb2 + (WL::ob3 - WL::ob2) &&
+                                  WL::vmu == WL::vb2 + (WL::omu - WL::ob2),
+                              "b2 | w3 | b3 | mu keep their order");
+                umma::mbar_arrive_expect_tx(rbar, img_bytes + b1_bytes + rest_bytes);
+                umma::bulk_g2s(n.saddr(WL::sW1), a.gimg, img_bytes, rbar);
+                umma::bulk_g2s(n.saddr(WL::sVec + WL::vb1 * 4), a.gq + WL::ob1, b1_bytes, rbar);
+                umma::bulk_g2s(n.saddr(WL::sVec + WL::vb2 * 4), a.gq + WL::ob2, rest_bytes, rbar);
             }
-            umma::fence_proxy_async();
-            __syncthreads();
+            const bool got = umma::mbar_wait(rbar, rphase, kMbarPolls);
+            rphase ^= 1u;
+            rpending = __syncthreads_and(got) == 0;
+            if (rpending) {
+                ok = false;
+                if (n.tid == 0) atomicExch(a.err, 2);
+            }
         }
     }
     for (int q = lo + n.tid; q < hi; q += kWThreads)
@@ -750,6 +790,7 @@ __global__ void __launch_bounds__(kWThreads, 1) wide_train_kernel(WTrainArgs a, 
             a.params[WL::p_of(q)] = t;
             if (a.snap) a.snap[WL::p_of(q)] = t;
         }
+    if (rpending) (void)umma::mbar_wait(rbar, rphase ^ 1u, kMbarPolls);   // no copy outlives the CTA
     wide_teardown(n);
 }
 
@@ -977,7 +1018,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_vec = al((size_t)WL::NPpad * 4), b_img = al((size_t)WL::img_elems * 2),
                  b_stats = al((size_t)n_dates * 2 * kIn * 4), b_snaps = al((size_t)epochs * WL::NPpad * 4),
-                 b_part = al((size_t)G * WL::NPpad * 4), b_flags = al(2 * 4), b_bl = al(8),
+                 b_part = al((size_t)G * WL::NPpad * 4), b_flags = al(4), b_bl = al(8),
                  b_G = al(refit_g_bytes(WL::U)), b_pl = al((size_t)(fwd_grid > sweep_grid ? fwd_grid : sweep_grid) * 8),
                  b_pg = al((size_t)sweep_grid * Z * Z * 8);
     const size_t need = 5 * b_vec + b_img + b_stats + b_snaps + b_part + b_flags + 2 * b_bl + b_G + b_pl + b_pg;
@@ -1068,7 +1109,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
             ta.n_steps = n_batches < steps_left ? n_batches : steps_left;
             ta.step0 = (e - 1) * n_batches;
             ta.pos = (epochs / 2 >= 1 && e > epochs / 2) ? 1 : 0;
-            CVA_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), st));
+            CVA_CUDA_TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
             cudaEvent_t t0 = nullptr, t1 = nullptr;
             const bool timed = mlp_timing_pair(dev, &t0, &t1);
             if (timed) CVA_CUDA_TRY(cudaEventRecord(t0, st));
