@@ -117,6 +117,10 @@ NCU_TRAFFIC = {
     # one launch = one epoch at one date; captured at 65536 paths, scaled by the paths
     "mlp_train_kernel": {"bytes_per_unit": (7.532032e6 + 0.0) / 65536, "unit": "path",
                          "profile": "profiles/mlp_train_kernel_paper_64k.md"},
+    # width 128: one launch = one epoch at one date; captured at 131072 paths (second
+    # launch of the capture), scaled by the paths
+    "wide_train_kernel": {"bytes_per_unit": (15.038720e6 + 0.005120e6) / 131072, "unit": "path",
+                          "profile": "profiles/wide_train_kernel_precision_128k.md"},
 }
 
 
@@ -578,7 +582,8 @@ def main():
         per_launch = mlp_train_flops_per_launch(wl.M, wl.model.F, hidden)
         launch_ms = train_t["ms"] / max(train_t["launches"], 1)
         tf = per_launch / (launch_ms / 1e3) / 1e12
-        tr = NCU_TRAFFIC.get("mlp_train_kernel") if (wl.name == "paper" and hidden == 64) else None
+        tr = (NCU_TRAFFIC.get("mlp_train_kernel") if (wl.name == "paper" and hidden == 64) else
+              NCU_TRAFFIC.get("wide_train_kernel") if (wl.name == "precision" and hidden == 128) else None)
         mlp_roof = {"bound": "tensor", "kernel": "mlp_train_kernel" if hidden == 64 else "wide_train_kernel",
                     "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf,
                     "traffic": tr["bytes_per_unit"] * wl.M if tr else None,
@@ -747,7 +752,9 @@ def main():
                      "regression_samples_per_s": pwl.M * (pn - 1) / (p_reg / 1e3),
                      "roofline": {"bound": "tensor", "kernel": "wide_train_kernel",
                                   "achieved": p_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": p_tf / peak_tf,
-                                  "traffic": None, "algorithmic_flops_per_launch": p_launch,
+                                  "traffic": NCU_TRAFFIC["wide_train_kernel"]["bytes_per_unit"] * pwl.M,
+                                  "traffic_source": NCU_TRAFFIC["wide_train_kernel"]["profile"],
+                                  "algorithmic_flops_per_launch": p_launch,
                                   "launch_ms": p_launch_ms, "launches": p_train["launches"],
                                   "timing": "CUDA events around every train launch of a 4th repetition",
                                   "peak_source": "measured bf16 cuBLAS, sustained",

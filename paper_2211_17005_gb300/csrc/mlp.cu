@@ -460,38 +460,58 @@ struct Net {
     {
         const int q4 = warp & 3, wg = warp >> 2;
         const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
+        // every TMEM load of the thread is issued before the one wait; a chunk past the
+        // thread's range reads allocated columns whose values are not used
         if (q4 < 2) {   // rows o < U: dW2[o][:] at columns [0, U), db2[o] at column U
             const int o = q4 * 32 + lane;
             const int k0 = wg ? 3 : 0, k1 = wg ? 5 : 3;
-            for (int k = k0; k < k1; ++k) {
-                float v0[16], v1[16];
-                umma::tmem_ld16(tmem + lanes + 128u + 16u * k, v0);
-                umma::tmem_ld16(tmem + lanes + 256u + 16u * k, v1);
-                umma::tmem_wait_ld();
+            float v0[3][16], v1[3][16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = 16 * k + i;
-                    const float g = (h0 ? v0[i] : 0.f) + (h1 ? v1[i] : 0.f);
-                    if (col < U) P[L::oW2 + col * U + o] = g;
-                    else if (col == U) P[L::ob2 + o] = g;
-                }
+            for (int j = 0; j < 3; ++j) {
+                umma::tmem_ld16(tmem + lanes + 128u + 16u * (uint32_t)(k0 + j), v0[j]);
+                umma::tmem_ld16(tmem + lanes + 256u + 16u * (uint32_t)(k0 + j), v1[j]);
             }
+            umma::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(v0[j][i]), "+f"(v1[j][i]));
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (k0 + j < k1) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int col = 16 * (k0 + j) + i;
+                        const float g = (h0 ? v0[j][i] : 0.f) + (h1 ? v1[j][i] : 0.f);
+                        if (col < U) P[L::oW2 + col * U + o] = g;
+                        else if (col == U) P[L::ob2 + o] = g;
+                    }
+                }
         } else {        // rows U + i: dW1[i][:] at columns [cX, cX + 32), db1[i] at column cOne2
             const int i0 = (q4 - 2) * 32 + lane;
             const int k0 = wg ? 7 : 5, k1 = wg ? 8 : 7;
-            for (int k = k0; k < k1; ++k) {
-                float v0[16], v1[16];
-                umma::tmem_ld16(tmem + lanes + 128u + 16u * k, v0);
-                umma::tmem_ld16(tmem + lanes + 256u + 16u * k, v1);
-                umma::tmem_wait_ld();
+            float v0[2][16], v1[2][16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int f = 16 * k + i - L::cX;
-                    const float g = (h0 ? v0[i] : 0.f) + (h1 ? v1[i] : 0.f);
-                    if (f < kIn) P[L::oW1 + f * U + i0] = g;
-                    else if (f == kIn) P[L::ob1 + i0] = g;
-                }
+            for (int j = 0; j < 2; ++j) {
+                umma::tmem_ld16(tmem + lanes + 128u + 16u * (uint32_t)(k0 + j), v0[j]);
+                umma::tmem_ld16(tmem + lanes + 256u + 16u * (uint32_t)(k0 + j), v1[j]);
             }
+            umma::tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int i = 0; i < 16; ++i) asm volatile("" : "+f"(v0[j][i]), "+f"(v1[j][i]));
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (k0 + j < k1) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int f = 16 * (k0 + j) + i - L::cX;
+                        const float g = (h0 ? v0[j][i] : 0.f) + (h1 ? v1[j][i] : 0.f);
+                        if (f < kIn) P[L::oW1 + f * U + i0] = g;
+                        else if (f == kIn) P[L::ob1 + i0] = g;
+                    }
+                }
         }
         if (tid < U + 2) {
             float s = 0.f;

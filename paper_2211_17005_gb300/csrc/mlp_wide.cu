@@ -10,7 +10,7 @@
 //   wide_sweep_kernel   full-sample forward passes: the refit's Gram matrix (the
 //                       trainer's layout, one CTA per SM), or the epoch loss with
 //                       the best-parameter choice and the predictions (a
-//                       forward-only layout, two CTAs per SM)
+//                       forward-only layout, one CTA per SM)
 //   mlp_refit_kernel    (shared) Gram sum, FP64 Cholesky, new (w3, b3)
 //
 // Every CTA owns one 128-row tile slot worked by its two warpgroups; warpgroup h
@@ -100,8 +100,10 @@ static_assert(WL::bytes <= 227 * 1024, "shared memory");
 
 // Forward-only layout of the loss and prediction passes: B, the weight images, the
 // vectors and the staging area, no A buffer; 107 KB of shared memory and 128 TMEM
-// columns (one accumulator for both layers), so two CTAs share an SM and one's
-// epilogues run beside the other's tensor-core work.
+// columns (one accumulator for both layers). Two CTAs would fit an SM's shared
+// memory, registers and TMEM, and the launch asks the occupancy query for them, but
+// the query grants a kernel that uses tcgen05 instructions one CTA per SM, so each
+// pass runs one CTA per SM.
 struct WLF : WL {
     static constexpr bool kGram = false;
     static constexpr int sA = -1;
@@ -117,7 +119,7 @@ struct WLF : WL {
     static constexpr uint32_t tmem_cols = 128;
 };
 static_assert(WLF::sStage % 128 == 0, "TMA destination must be 128-byte aligned");
-static_assert(2 * (WLF::bytes + 1024 + 256) <= 228 * 1024, "two CTAs per SM");
+static_assert(2 * (WLF::bytes + 1024 + 256) <= 228 * 1024, "two CTAs fit an SM's shared memory");
 
 // byte offset of element c of row r in a BF16 row buffer of width w (K-major core
 // matrices of 8 rows x 16 bytes)
@@ -1002,6 +1004,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     const uint64_t tiles = M / kRows;
     const int sweep_grid = (int)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
     // the loss and prediction passes run the forward-only layout, fwd_per_sm CTAs an SM
+    // (at most 2; the occupancy query grants a tcgen05 kernel one)
     int fwd_per_sm = 0;
     CVA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fwd_per_sm, wide_sweep_kernel<WLF, 2>, kWThreads,
                                                                 WLF::bytes));
