@@ -7,10 +7,11 @@
 // Kernels of one date, in order on one stream:
 //   wide_train_kernel   one epoch of Adam steps on a cooperative grid (one CTA per
 //                       SM, at most one tile per CTA and round)
-//   wide_sweep_kernel   full-sample forward passes: the refit's Gram matrix (the
-//                       trainer's layout, one CTA per SM), or the epoch loss with
-//                       the best-parameter choice and the predictions (a
-//                       forward-only layout, one CTA per SM)
+//   wide_sweep_kernel   the refit's Gram matrix: a full-sample forward pass in the
+//                       trainer's layout (one CTA per SM)
+//   wide_fwd_kernel     full-sample forward passes: the epoch loss with the
+//                       best-parameter choice, or the predictions (two tiles of a
+//                       CTA in a pipeline, one CTA per SM)
 //   mlp_refit_kernel    (shared) Gram sum, FP64 Cholesky, new (w3, b3)
 //
 // Every CTA owns one 128-row tile slot worked by its two warpgroups; warpgroup h
@@ -98,28 +99,29 @@ struct WL {
 static_assert(WL::sStage % 128 == 0, "TMA destination must be 128-byte aligned");
 static_assert(WL::bytes <= 227 * 1024, "shared memory");
 
-// Forward-only layout of the loss and prediction passes: B, the weight images, the
-// vectors and the staging area, no A buffer; 107 KB of shared memory and 128 TMEM
-// columns (one accumulator for both layers). Two CTAs would fit an SM's shared
-// memory, registers and TMEM, and the launch asks the occupancy query for them, but
-// the query grants a kernel that uses tcgen05 instructions one CTA per SM, so each
-// pass runs one CTA per SM.
-struct WLF : WL {
-    static constexpr bool kGram = false;
+// Pipelined forward layout of the loss and prediction passes: two B buffers and two
+// TMEM accumulators, so that the first GEMM of a CTA's next tile runs while the
+// output layer of its current tile is evaluated, and kStages staging buffers, so that
+// the inputs of the next kStages tiles are in flight (one CTA per SM).
+struct WLP : WL {
+    static constexpr int kStages = 4;
+    static constexpr int stage_bytes = (kIn + 1) * kRows * 4;
     static constexpr int sA = -1;
     static constexpr int sB = 0;
-    static constexpr int sW1 = sB + kRows * wB * 2;
+    static constexpr int sB1 = sB + kRows * wB * 2;               // the second B buffer
+    static constexpr int sW1 = sB1 + kRows * wB * 2;
     static constexpr int sW2 = sW1 + U * kIn * 2;
     static constexpr int sVec = sW2 + U * U * 2;
-    static constexpr int sStage = sVec + 512 * 4;
-    static constexpr int sStats = sStage + (kIn + 1) * kRows * 4;
+    static constexpr int sStage = sVec + 512 * 4;                // [kStages][kIn + 1][128] FP32 inputs, target
+    static constexpr int sStats = sStage + kStages * stage_bytes;
     static constexpr int sGsl = sStats + 2 * kIn * 4;
     static constexpr int sOut = sGsl + 8 * 66 * 4;
     static constexpr int bytes = sOut + 2 * kRows * 4;
-    static constexpr uint32_t tmem_cols = 128;
+    static constexpr uint32_t tmem_cols = 256;                   // D of tile k at 128 (k & 1)
 };
-static_assert(WLF::sStage % 128 == 0, "TMA destination must be 128-byte aligned");
-static_assert(2 * (WLF::bytes + 1024 + 256) <= 228 * 1024, "two CTAs fit an SM's shared memory");
+static_assert(WLP::sStage % 128 == 0 && WLP::stage_bytes % 128 == 0 && WLP::sB1 % 1024 == 0,
+              "TMA destinations and operand alignment");
+static_assert(WLP::bytes <= 227 * 1024, "shared memory");
 
 // byte offset of element c of row r in a BF16 row buffer of width w (K-major core
 // matrices of 8 rows x 16 bytes)
@@ -931,6 +933,216 @@ __global__ void __launch_bounds__(kWThreads, MinBlocks) wide_sweep_kernel(WSweep
     wide_teardown(n);
 }
 
+// Loss (mode 0) and prediction (mode 2) passes: the forward pass of the trainer's
+// tiles (both warpgroups on one tile, 64 hidden columns each) in a two-stage
+// pipeline over the CTA's tiles k = 0, 1, ...:
+//   stage tile k into B[k & 1] and issue D[k & 1] = X W1^T;
+//   wait for tile k - 1's second GEMM, evaluate its output layer and loss;
+//   wait for tile k's first GEMM, H1 = relu(D + b1) into B[k & 1], issue
+//   D[k & 1] = H1 W2^T.
+// Every row's arithmetic is the trainer's forward pass, and a CTA adds its rows'
+// losses in tile order, so the result does not depend on the pipeline.
+__global__ void __launch_bounds__(kWThreads, 1) wide_fwd_kernel(WSweepArgs a, const __grid_constant__ CUtensorMap tm)
+{
+    using L = WLP;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[3];   // first GEMM, (unused staging), second GEMM
+    __shared__ __align__(8) uint64_t s_sbar[L::kStages];   // staging buffer s complete
+    __shared__ double s_red[8];
+    __shared__ int s_flag[2];
+    WNetT<L> n(smem, s_mbar);
+    wide_setup(n, &s_tmem, s_mbar, a.stats, a.F, false);
+    if (n.tid == 0) {
+        umma::mbar_init(&s_mbar[2], 1);
+        for (int q = 0; q < L::kStages; ++q) umma::mbar_init(&s_sbar[q], 1);
+        umma::fence_mbar_init();
+    }
+    // rows f >= F of every staging buffer stay zero (the copies fill rows < F)
+    for (int i = n.tid; i < L::kStages * (kIn + 1) * kRows; i += kWThreads) {
+        const int f = (i / kRows) % (kIn + 1);
+        if (f >= a.F && f < kIn) n.stage[i] = 0.f;
+    }
+    wide_load_params(n, a.theta);
+    wide_finish_setup(n, &s_tmem);
+    uint64_t *bar1 = &s_mbar[0], *bar2 = &s_mbar[2];
+    uint32_t ph1 = 0, ph2 = 0;
+
+    // tensor-core issue by thread 0 once every thread's operands are written
+    auto issue = [&](uint64_t *bar, auto f) {
+        umma::fence_proxy_async();
+        umma::fence_before_sync();
+        __syncthreads();
+        umma::fence_after_sync();
+        if (n.tid == 0) {
+            f();
+            umma::commit(bar);
+        }
+    };
+    auto wait = [&](uint64_t *bar, uint32_t &ph) {
+        const bool d = umma::mbar_wait(bar, ph, kMbarPolls);
+        ph ^= 1u;
+        umma::fence_after_sync();
+        return d;
+    };
+    // the inputs of the CTA's tile j (paths path0 ...) into staging buffer j % kStages
+    // (one thread issues; called once no thread reads that buffer any more)
+    auto request = [&](uint32_t j, uint32_t path0) {
+        if (n.tid == 32) {
+            uint64_t *sb = &s_sbar[j % L::kStages];
+            const uint32_t dst = n.saddr(L::sStage + (int)(j % L::kStages) * L::stage_bytes);
+            umma::mbar_arrive_expect_tx(sb, (uint32_t)(a.F + 1) * kRows * 4u);
+            umma::tma_load_2d(dst, &tm, (int32_t)path0, 0, sb);
+            umma::bulk_g2s(dst + kIn * kRows * 4u, a.targ + path0, kRows * 4u, sb);
+        }
+    };
+    // wait for tile j's inputs; this thread's 16 standardised inputs into the X columns
+    // of B[b]; y receives the target
+    auto stage_into = [&](uint32_t j, int b, float &y) {
+        const bool got = umma::mbar_wait(&s_sbar[j % L::kStages], (j / L::kStages) & 1u, kMbarPolls);
+        const float *stg = reinterpret_cast<const float *>(smem + L::sStage + (int)(j % L::kStages) * L::stage_bytes);
+        const float4 *mv = reinterpret_cast<const float4 *>(n.mean), *iv = reinterpret_cast<const float4 *>(n.istd);
+        float x[16];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int f0 = 16 * n.half + 4 * g;
+            const float4 m = mv[f0 / 4], r = iv[f0 / 4];
+            x[4 * g + 0] = (stg[(f0 + 0) * kRows + n.row] - m.x) * r.x;
+            x[4 * g + 1] = (stg[(f0 + 1) * kRows + n.row] - m.y) * r.y;
+            x[4 * g + 2] = (stg[(f0 + 2) * kRows + n.row] - m.z) * r.z;
+            x[4 * g + 3] = (stg[(f0 + 3) * kRows + n.row] - m.w) * r.w;
+        }
+        unsigned char *bp = smem + (b ? L::sB1 : L::sB);
+        *reinterpret_cast<uint4 *>(bp + wrow_off(n.row, L::cX + 16 * n.half, L::wB)) = pack8(x);
+        *reinterpret_cast<uint4 *>(bp + wrow_off(n.row, L::cX + 16 * n.half + 8, L::wB)) = pack8(x + 8);
+        y = stg[kIn * kRows + n.row];
+        return got;
+    };
+    // H1 = relu(D[b] + b1) of this thread's 64 columns into B[b]
+    auto epi1_into = [&](int b) {
+        unsigned char *bp = smem + (b ? L::sB1 : L::sB);
+        const float4 *b1 = reinterpret_cast<const float4 *>(n.vec + L::vb1 + 64 * n.half);
+        float v[64];
+        umma::tmem_ld64(n.taddr(128u * (uint32_t)b + 64u * (uint32_t)n.half), v);
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const float4 c = b1[g];
+            v[4 * g + 0] = fmaxf(v[4 * g + 0] + c.x, 0.f);
+            v[4 * g + 1] = fmaxf(v[4 * g + 1] + c.y, 0.f);
+            v[4 * g + 2] = fmaxf(v[4 * g + 2] + c.z, 0.f);
+            v[4 * g + 3] = fmaxf(v[4 * g + 3] + c.w, 0.f);
+        }
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            *reinterpret_cast<uint4 *>(bp + wrow_off(n.row, 64 * n.half + 8 * g, L::wB)) = pack8(v + 8 * g);
+    };
+    // this thread's share of w3 . relu(D[b] + b2) (four partial sums, the order of layer2)
+    auto share_of = [&](int b) {
+        const float4 *b2 = reinterpret_cast<const float4 *>(n.vec + L::vb2 + 64 * n.half),
+                     *w3 = reinterpret_cast<const float4 *>(n.vec + L::vw3 + 64 * n.half);
+        float v[64];
+        umma::tmem_ld64(n.taddr(128u * (uint32_t)b + 64u * (uint32_t)n.half), v);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const float4 c = b2[g], w = w3[g];
+            v[4 * g + 0] = fmaxf(v[4 * g + 0] + c.x, 0.f);
+            v[4 * g + 1] = fmaxf(v[4 * g + 1] + c.y, 0.f);
+            v[4 * g + 2] = fmaxf(v[4 * g + 2] + c.z, 0.f);
+            v[4 * g + 3] = fmaxf(v[4 * g + 3] + c.w, 0.f);
+            acc[0] = fmaf(v[4 * g + 0], w.x, acc[0]);
+            acc[1] = fmaf(v[4 * g + 1], w.y, acc[1]);
+            acc[2] = fmaf(v[4 * g + 2], w.z, acc[2]);
+            acc[3] = fmaf(v[4 * g + 3], w.w, acc[3]);
+        }
+        return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    };
+
+    const uint32_t tiles = a.M / kRows, stride = gridDim.x;
+    const uint32_t K = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / stride + 1 : 0;   // this CTA's tiles
+    double acc = 0.0;
+    bool ok = true, pend2 = false;   // pend2: a second GEMM issued and not yet waited for
+    float y_prev = 0.f, y = 0.f;
+    uint32_t requested = 0, consumed = 0;   // tiles whose inputs were requested / read
+    for (; requested < K && requested < (uint32_t)L::kStages; ++requested)
+        request(requested, (blockIdx.x + requested * stride) * kRows);
+    for (uint32_t k = 0; k <= K; ++k) {
+        const int b = (int)(k & 1u);
+        const uint32_t t = blockIdx.x + k * stride;
+        if (k < K) {
+            ok = stage_into(k, b, y) && ok;
+            ++consumed;
+            issue(bar1, [&] { n.gemm_rows(128u * (uint32_t)b, b ? L::sB1 : L::sB, L::wB, L::cX, L::sW1, kIn, L::U); });
+            if (requested < K) {   // every thread is past buffer k % kStages: tile k + kStages into it
+                request(requested, (blockIdx.x + requested * stride) * kRows);
+                ++requested;
+            }
+        }
+        if (k > 0) {   // the output layer of tile k - 1
+            ok = wait(bar2, ph2) && ok;
+            pend2 = false;
+            const float pred = fmaxf(n.zeta(share_of(b ^ 1)), 0.f) + n.vec[L::vmu];
+            if (n.half == 0) {
+                if (a.mode == 2) {
+                    if (a.pred) a.pred[(t - stride) * kRows + n.row] = pred;
+                } else {
+                    acc += (double)((pred - y_prev) * (pred - y_prev));
+                }
+            }
+        }
+        if (k < K) {
+            ok = wait(bar1, ph1) && ok;
+            epi1_into(b);
+            issue(bar2, [&] { n.gemm_rows(128u * (uint32_t)b, b ? L::sB1 : L::sB, L::wB, 0, L::sW2, L::U, L::U); });
+            pend2 = true;
+        }
+        y_prev = y;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+    }
+    if (pend2) (void)wait(bar2, ph2);   // a loop left early: no tensor-core work outlives the CTA
+    for (uint32_t j = consumed; j < requested; ++j)   // nor any input copy
+        (void)umma::mbar_wait(&s_sbar[j % L::kStages], (j / L::kStages) & 1u, kMbarPolls);
+    if (!ok && n.tid == 0) atomicExch(a.err, 2);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+
+    if (a.mode == 0) {
+        double sred = acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sred += __shfl_xor_sync(0xffffffffu, sred, o);
+        if (n.lane == 0) s_red[n.warp] = sred;
+        __syncthreads();
+        if (n.tid == 0) {
+            double bsum = 0.0;
+            for (int w = 0; w < 8; ++w) bsum += s_red[w];
+            a.part[blockIdx.x] = bsum;
+            __threadfence();
+            s_flag[0] = atomicAdd(a.count, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_flag[0]) {   // the last CTA: total loss, best parameters so far
+            __threadfence();
+            if (n.tid == 0) {
+                double tot = 0.0;
+                for (uint32_t bb = 0; bb < gridDim.x; ++bb) tot += __ldcg(a.part + bb);
+                tot /= (double)a.M;
+                if (a.loss_out) a.loss_out[a.epoch - 1] = (float)tot;
+                s_flag[1] = tot < *a.best_loss;
+                if (s_flag[1]) *a.best_loss = tot;
+                *a.count = 0u;
+            }
+            __syncthreads();
+            if (s_flag[1])
+                for (int p = n.tid; p < L::NP; p += kWThreads) a.best[p] = __ldg(a.theta + p);
+        }
+    }
+    wide_teardown(n);
+}
+
 // ---- host side ----
 struct WideWork {
     void *buf = nullptr;
@@ -986,8 +1198,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
         CVA_CUDA_TRY(cudaFuncSetAttribute(wide_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WL::bytes));
         CVA_CUDA_TRY(cudaFuncSetAttribute(wide_sweep_kernel<WL, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           WL::bytes));
-        CVA_CUDA_TRY(cudaFuncSetAttribute(wide_sweep_kernel<WLF, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          WLF::bytes));
+        CVA_CUDA_TRY(cudaFuncSetAttribute(wide_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WLP::bytes));
         CVA_CUDA_TRY(cudaFuncSetAttribute(mlp_refit_kernel<WL::U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)refit_smem_bytes(WL::U)));
         int least = 0, greatest = 0;
@@ -1003,19 +1214,12 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
     const int G = wide_grid(tiles_per_batch, sms);
     const uint64_t tiles = M / kRows;
     const int sweep_grid = (int)(tiles < (uint64_t)sms ? tiles : (uint64_t)sms);
-    // the loss and prediction passes run the forward-only layout, fwd_per_sm CTAs an SM
-    // (at most 2; the occupancy query grants a tcgen05 kernel one)
-    int fwd_per_sm = 0;
-    CVA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fwd_per_sm, wide_sweep_kernel<WLF, 2>, kWThreads,
-                                                                WLF::bytes));
-    fwd_per_sm = fwd_per_sm < 1 ? 1 : (fwd_per_sm > 2 ? 2 : fwd_per_sm);
-    const uint64_t fwd_cap = (uint64_t)fwd_per_sm * (uint64_t)sms;
-    const int fwd_grid = (int)(tiles < fwd_cap ? tiles : fwd_cap);
     // passes that overlap the training take the SMs its grid leaves (the trainer's CTA
-    // fills an SM); with fewer than 8 of them every pass stays on st with the whole GPU
+    // fills an SM, and so does a pass's); with fewer than 8 of them every pass stays on
+    // st with the whole GPU
     const bool overlap = sms - G >= 8;
-    const uint64_t side_cap = (uint64_t)fwd_per_sm * (uint64_t)(sms - G);
-    const int side_grid = overlap ? (int)(tiles < side_cap ? tiles : side_cap) : fwd_grid;
+    const int side_grid = overlap ? (int)(tiles < (uint64_t)(sms - G) ? tiles : (uint64_t)(sms - G)) : sweep_grid;
+    const int fwd_grid = sweep_grid;
     const cudaStream_t sst = overlap ? w.side : st;
 
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -1147,7 +1351,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
                 CVA_CUDA_TRY(cudaEventRecord(w.ev_train, st));
                 CVA_CUDA_TRY(cudaStreamWaitEvent(sst, w.ev_train, 0));
             }
-            wide_sweep_kernel<WLF, 2><<<e == epochs ? fwd_grid : side_grid, kWThreads, WLF::bytes, sst>>>(sw, tm);
+            wide_fwd_kernel<<<e == epochs ? fwd_grid : side_grid, kWThreads, WLP::bytes, sst>>>(sw, tm);
             CVA_CUDA_TRY(cudaGetLastError());
         }
         // the best parameters are known once the last loss pass ran: the next date (st)
@@ -1161,7 +1365,7 @@ cva_status mlp_wide_fit_dates(const float *feat0, size_t feat_stride, const floa
             pv.mode = 2;
             pv.theta = best[par];
             pv.pred = pred0 + (size_t)d * M;
-            wide_sweep_kernel<WLF, 2><<<side_grid, kWThreads, WLF::bytes, sst>>>(pv, tm);
+            wide_fwd_kernel<<<side_grid, kWThreads, WLP::bytes, sst>>>(pv, tm);
             CVA_CUDA_TRY(cudaGetLastError());
         }
         if (d == 0)
