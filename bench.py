@@ -115,7 +115,7 @@ NCU_TRAFFIC = {
     "price_kernel": {"bytes_per_unit": (263.78e6 + 81.86e6) / (32768 * 100), "unit": "path-date",
                      "profile": "profiles/sim_price_inner_kernels_paper_32k.md"},
     # one launch = one epoch at one date; captured at 65536 paths, scaled by the paths
-    "mlp_train_kernel": {"bytes_per_unit": (7.532032e6 + 0.0) / 65536, "unit": "path",
+    "mlp_train_kernel": {"bytes_per_unit": (7.506432e6 + 0.0) / 65536, "unit": "path",
                          "profile": "profiles/mlp_train_kernel_paper_64k.md"},
     # width 128: one launch = one epoch at one date; captured at 131072 paths (second
     # launch of the capture), scaled by the paths
