@@ -523,11 +523,11 @@ struct Net {
     }
 };
 
-// common start of the train and sweep kernels, the part that reads no parameters:
-// TMEM, mbarriers, standardisation, cleared gradient slots and staging rows,
-// constant operand columns (no block barrier)
+// common start of the train and sweep kernels: TMEM, mbarriers, parameters (q
+// order), standardisation, constant operand columns, weight images
 template <int U>
-__device__ void net_setup_fixed(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *stats, int F, bool zero_a)
+__device__ void net_setup(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *params, const float *stats,
+                          int F, bool zero_a)
 {
     using L = Layout<U>;
     if (n.warp == 0) {
@@ -538,6 +538,8 @@ __device__ void net_setup_fixed(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, c
         for (int i = 0; i < 4; ++i) umma::mbar_init(&s_mbar[i], 1);
         umma::fence_mbar_init();
     }
+    float *th = reinterpret_cast<float *>(n.smem + L::sTh);
+    for (int q = n.tid; q < L::NPpad; q += kThreads) th[q] = q < L::NP ? __ldg(params + L::p_of(q)) : 0.f;
     float *vec = reinterpret_cast<float *>(n.smem + L::sVec);
     if (n.tid < 2 * kIn) vec[n.tid] = __ldg(stats + n.tid);
     float *gsl = reinterpret_cast<float *>(n.smem + L::sGsl);
@@ -553,29 +555,6 @@ __device__ void net_setup_fixed(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, c
         for (int i = n.row; i < 32768 / 16; i += kRows) a[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     n.init_constants();
-}
-
-// the rest of the common start: the parameters (q order; every load of a thread in
-// flight at once, also handed to `also`, row order, when it is non-null) and their
-// weight images; ends with the block barrier that publishes the whole start
-template <int U>
-__device__ void net_setup_params(Net<U> &n, uint32_t *s_tmem, const float *params, float *also)
-{
-    using L = Layout<U>;
-    constexpr int kPer = (L::NPpad + kThreads - 1) / kThreads;
-    float *th = reinterpret_cast<float *>(n.smem + L::sTh);
-    float v[kPer];
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int q = n.tid + i * kThreads;
-        v[i] = q < L::NP ? __ldg(params + L::p_of(q)) : 0.f;
-    }
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int q = n.tid + i * kThreads;
-        if (q < L::NPpad) th[q] = v[i];
-        if (also && q < L::NP) also[L::p_of(q)] = v[i];
-    }
     __syncthreads();
     n.build_images();
     umma::fence_proxy_async();
@@ -583,14 +562,6 @@ __device__ void net_setup_params(Net<U> &n, uint32_t *s_tmem, const float *param
     __syncthreads();
     umma::fence_after_sync();
     n.tmem = *s_tmem;
-}
-
-template <int U>
-__device__ void net_setup(Net<U> &n, uint32_t *s_tmem, uint64_t *s_mbar, const float *params, const float *stats,
-                          int F, bool zero_a)
-{
-    net_setup_fixed<U>(n, s_tmem, s_mbar, stats, F, zero_a);
-    net_setup_params<U>(n, s_tmem, params, nullptr);
 }
 
 template <int U>
@@ -638,35 +609,26 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
     const int S = L::NPpad / (int)CL, lo = (int)rank * S, hi = lo + S;
     const uint32_t slice_bytes = (uint32_t)S * 4u;
 
+    // the previous kernel of the stream has completed and its writes are visible;
+    // from here on the next train launch may become resident
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (n.tid == 0) {
+        umma::mbar_init(&s_xbar[0], 1);
+        umma::mbar_init(&s_xbar[1], 1);
+    }
+    net_setup<U>(n, &s_tmem, s_mbar, a.init, a.stats, a.F, false);   // fences the barrier initialisation
+    if (a.step0 == 0 && rank == 0) {   // start of a date: the starting parameters are the best so far
+        for (int p = n.tid; p < L::NP; p += kThreads) a.best[p] = __ldg(a.init + p);
+        if (n.tid == 0) *a.best_loss = 1e300;
+    }
+    umma::cluster_sync();   // every CTA's exchange barriers exist before any copy targets them
+
     const uint32_t per_batch = (uint32_t)a.tiles_per_batch * kRows;
     const float inv_batch = 1.f / (float)per_batch;
     const int span = 2 * (int)CL, my = 2 * (int)rank + n.slot;
     const int my_rounds = my < a.tiles_per_batch ? (a.tiles_per_batch - 1 - my) / span + 1 : 0;
     auto path_of = [&](int st, int rd) { return (uint32_t)st * per_batch + (uint32_t)(rd * span + my) * kRows; };
-
-    // the start that reads nothing a train launch writes (TMEM, barriers, the date's
-    // standardisation, constant operand columns, the first tile's inputs) runs while
-    // the previous train launch of the stream may still be running; that launch
-    // becomes resident on other SMs only once the launch before it has completed, so
-    // everything earlier in the stream (the simulation, the standardisation) is done
-    if (n.tid == 0) {
-        umma::mbar_init(&s_xbar[0], 1);
-        umma::mbar_init(&s_xbar[1], 1);
-    }
-    net_setup_fixed<U>(n, &s_tmem, s_mbar, a.stats, a.F, false);   // fences the barrier initialisation
-    __syncthreads();   // the staging barriers exist before a copy completes on one
-    if (my_rounds > 0) n.prefetch(&tm, a.targ, a.F, path_of(0, 0));
-
-    // the previous kernel of the stream has completed and its writes are visible;
-    // from here on the next train launch may become resident
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    // the parameters; at the start of a date they are also the best so far
-    const bool date_start = a.step0 == 0 && rank == 0;
-    net_setup_params<U>(n, &s_tmem, a.init, date_start ? a.best : nullptr);
-    if (date_start && n.tid == 0) *a.best_loss = 1e300;
-    umma::cluster_sync();   // every CTA's exchange barriers exist before any copy targets them
-
     const bool h0 = 2 * (int)rank < a.tiles_per_batch, h1 = 2 * (int)rank + 1 < a.tiles_per_batch;
     float *my_gsl = gsl + n.warp * (U + 2);
     const uint32_t part_s = umma::smem_u32(part), th_s = umma::smem_u32(th), recv_s = umma::smem_u32(recv);
@@ -677,6 +639,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_train_kernel(TrainArgs a, con
     float b1t = powf(a.beta1, (float)a.step0), b2t = powf(a.beta2, (float)a.step0);
     bool ok = true, staged = false, in_ok_next = true;
     float y_next = 0.f;
+    if (my_rounds > 0) n.prefetch(&tm, a.targ, a.F, path_of(0, 0));
     for (int st = 0; st < a.n_steps; ++st) {
         for (int rd = 0; rd < my_rounds && ok; ++rd) {
             const bool last = rd + 1 == my_rounds;
