@@ -176,10 +176,10 @@ __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence
 // Grid barrier of generation gen: bar[0] counts arrivals over the launch (one per
 // CTA and barrier; zero at launch), so generation gen is complete once it reaches
 // gen * nblocks. After a block barrier, thread 0 of every CTA fences and arrives
-// with one atomic; the others of the generation poll the counter itself (relaxed
-// loads) and fence once they see it complete: the release and acquire halves of a
-// cooperative-groups grid barrier, with no second word for the last arrival to
-// publish and so one round trip through L2 fewer. Bounded: a wait that gives up
+// with one atomic (the release: fence, then the relaxed increment); the others of
+// the generation poll the counter itself with relaxed loads and fence once they see
+// it complete (the acquire). There is no second word for the last arrival to
+// publish, so a barrier takes one round trip through L2 fewer. Bounded: a wait that gives up
 // (or sees the status word set) sets the status word and returns false; all
 // threads of the CTA get the same answer. Every thread's global writes before the
 // barrier are visible to every thread of the grid after it.
